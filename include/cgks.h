@@ -1,0 +1,213 @@
+/*
+ * cgks.h -- C ABI of the B300 GMG-CGKS library: one pseudo-time iteration of
+ * the three-level geometric-multigrid compact gas-kinetic scheme on
+ * unstructured simplex meshes (Liu, Ji, Fu, Xu, "A Geometric Multigrid-
+ * Accelerated Compact Gas-Kinetic Scheme for Fast Convergence in High-Speed
+ * Flows on GPUs", arXiv 2509.06347).
+ *
+ * Conventions
+ *  - Every function returns an int status: CGKS_OK (0) or a negative code.
+ *    Nothing throws across the ABI.  cgks_last_error(h) returns a message that
+ *    stays valid until the next call on h.
+ *  - dim = 2 (triangles) or 3 (tetrahedra); nv = dim + 2 conservative
+ *    variables (rho, rho u, rho v, [rho w], rho E).
+ *  - Per-cell arrays exchanged through the ABI are in the ORIGINAL cell order
+ *    of the uploaded mesh, row-major: W [n][nv], slopes [n][nv][dim]
+ *    (d/dx_d of variable v), DF factor [n].  Internally cells are renumbered
+ *    colour by colour.
+ *  - Pointers flagged "on_device" are CUDA device pointers (e.g. a torch
+ *    tensor's data_ptr) borrowed for the duration of the call; otherwise host
+ *    pointers.  Inputs are copied; the library owns all of its state.
+ *  - All work is enqueued on the stream given to cgks_create (a borrowed
+ *    handle, e.g. torch.cuda.current_stream().cuda_stream).  If that handle is
+ *    0 (the legacy default stream) the library uses a private stream instead.
+ *    Calls that return host data synchronise that stream.
+ *  - Meshes are identified by a caller-chosen integer mesh_id; several meshes
+ *    can live in one context (batched solves).
+ */
+#ifndef CGKS_H
+#define CGKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CGKS_OK = 0,
+  CGKS_ERR_ARG = -1,         /* invalid argument, size or id */
+  CGKS_ERR_MESH = -2,        /* non-manifold / open / degenerate mesh or hierarchy */
+  CGKS_ERR_CUDA = -3,        /* a CUDA call failed (message in cgks_last_error) */
+  CGKS_ERR_DIVERGED = -4,    /* non-finite update or residual growth beyond the limit */
+  CGKS_ERR_NONPOSITIVE = -5, /* density or pressure could not be kept positive */
+  CGKS_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+  CGKS_ERR_STATE = -7        /* call out of order (e.g. no mesh or state yet) */
+};
+
+/* V-cycle precision modes */
+enum {
+  CGKS_PLAIN_FP64 = 0, /* everything in FP64 */
+  CGKS_MIXED = 1       /* LU-SGS sweeps and their corrections in FP32; residuals,
+                          DF factor and state updates in FP64 */
+};
+
+/* boundary tags */
+enum { CGKS_TAG_WALL = 1, CGKS_TAG_FARFIELD = 2 };
+
+typedef struct cgks_config {
+  double gamma;           /* ratio of specific heats (1.4) */
+  double cfl_imp;         /* CFL of the implicit (DF-weighted) part, Sec 4.3 (10) */
+  double cfl_exp;         /* CFL of the explicit part and of the flux time step (0.5) */
+  double tau_c1, tau_c2;  /* numerical collision time tau = c1 dt + c2 |dp|/(pl+pr) dt (0.01, 1) */
+  double weno_gamma_high; /* linear weight of the large HWENO stencil (0.95) */
+  double weno_eps;        /* WENO epsilon (1e-15) */
+  double r_safety;        /* spectral-radius factor of the LU-SGS splitting (1) */
+  int n_sweep_coarse;     /* LU-SGS smoothing steps per coarse level (6) */
+  int n_pre, n_post;      /* fine pre/post smoothing steps (1, 0; only these are supported) */
+  int check_every;        /* V-cycles between convergence checks in cgks_vcycle (10) */
+  double tol;             /* residual drop that stops cgks_vcycle (1e-10) */
+  double diverge_factor;  /* residual growth over the first cycle that aborts (1e6) */
+} cgks_config;
+
+typedef struct cgks_ctx cgks_t;
+
+/* Fills *cfg with the defaults listed above. */
+int cgks_default_config(cgks_config* cfg);
+
+/* Creates a context.  cfg is copied; stream is borrowed (see Conventions). */
+int cgks_create(cgks_t** h, const cgks_config* cfg, void* cuda_stream);
+/* Frees every library-owned resource of h.  h may be NULL. */
+int cgks_destroy(cgks_t* h);
+/* Message of the last failing call on h (borrowed; valid until the next call). */
+const char* cgks_last_error(cgks_t* h);
+
+/*
+ * Mesh upload (Sec 2.2: cells, faces, Gauss points; Sec 3.1: the per-cell
+ * constrained least-squares operator; Sec 4.1: colouring).  Host pointers,
+ * copied:
+ *   cell_nodes [n_cells][dim+1]       topological node ids (periodic images of
+ *                                     a node share one id so faces match)
+ *   cell_xyz   [n_cells][dim+1][dim]  each cell's own vertex coordinates (a
+ *                                     face shared across a periodic boundary
+ *                                     appears shifted by the period)
+ *   bface_nodes [n_bfaces][dim], bface_tag [n_bfaces] (CGKS_TAG_*)
+ * Face k of a cell is the face opposite its vertex k; that is the cell's
+ * stored face order used by the colouring.  Returns CGKS_ERR_MESH for a face
+ * shared by more than two cells, an open face missing from the boundary list
+ * or a degenerate cell.  Replaces any previous mesh with the same id.
+ */
+int cgks_upload_mesh(cgks_t* h, int mesh_id, int dim, int64_t n_cells, const int32_t* cell_nodes,
+                     const double* cell_xyz, int64_t n_bfaces, const int32_t* bface_nodes,
+                     const int32_t* bface_tag);
+
+/*
+ * Nested hierarchy (Sec 5.1-5.2).  parent[l-1][i] (host, copied) is the
+ * level-l agglomerate containing level-(l-1) cell i, both in their original
+ * numbering; n_levels counts the fine level (1..8).  Coarse volumes and
+ * centres are sums over children; coarse faces are unique neighbour pairs with
+ * summed area vectors; boundary faces are merged per (cell, tag).  Every level
+ * is coloured (a coarse cell's neighbours in ascending id order) and
+ * renumbered.  Allocates all solver buffers.
+ */
+int cgks_upload_hierarchy(cgks_t* h, int mesh_id, int n_levels, const int32_t* const* parent);
+
+/* Sizes: out[4*l + 0..3] = cells, colours, faces, boundary faces of level l
+ * (out must hold 4 * n_levels values); *n_levels receives the level count. */
+int cgks_mesh_info(cgks_t* h, int mesh_id, int* n_levels, int64_t* out);
+
+/* Colour (1..Nc) of every cell of a level, original order, host int32 [n]. */
+int cgks_get_coloring(cgks_t* h, int mesh_id, int level, int32_t* colors);
+
+/* Free-stream conservative state [nv] (host) used by far-field ghosts. */
+int cgks_set_freestream(cgks_t* h, int mesh_id, const double* w);
+
+/* Initial state: W [n][nv], slopes [n][nv][dim] (NULL = zero).  Sets the DF
+ * factor to 1 and clears the residual history and counters. */
+int cgks_init_state(cgks_t* h, int mesh_id, const double* W, const double* grad, int on_device);
+
+/* Checkpoint / resume of the fine state (W, slopes, DF factor); any pointer
+ * may be NULL.  get_state synchronises the stream when on_device == 0. */
+int cgks_get_state(cgks_t* h, int mesh_id, double* W, double* grad, double* alpha, int on_device);
+int cgks_set_state(cgks_t* h, int mesh_id, const double* W, const double* grad, const double* alpha,
+                   int on_device);
+
+/*
+ * Residual at the current state without changing it.
+ * level 0: third-order residual (Sec 2.2-2.4, Sec 3): R [n][nv] = total
+ *   outward time-averaged flux of each cell, grad_new [n][nv][dim] = slopes
+ *   from the time-evolved Gauss-point values (before the DF scaling), alpha
+ *   [n] = product of the Gauss-point DF factors.  The previous DF factor of
+ *   the state scales the Green-Gauss sub-stencil.
+ * level >= 1: first-order KFVS residual of W_in [n_l][nv] (required; the
+ *   outputs grad_new and alpha must be NULL).
+ * Any output may be NULL.
+ */
+int cgks_residual(cgks_t* h, int mesh_id, int level, const double* W_in, double* R_out, double* grad_new_out,
+                  double* alpha_out, int on_device);
+
+/* Reconstructed polynomials of every fine cell at the current state:
+ * out [n][nv][nc], nc = 6 (2-D) / 10 (3-D), P(X) = c0 + c_d X_d + sum_{d<=e}
+ * c_de X_d X_e about the cell centroid (quadratic terms xx, xy, yy or xx, xy,
+ * xz, yy, yz, zz).  Also returns the local time steps dt_exp, dt_imp [n]. */
+int cgks_reconstruct(cgks_t* h, int mesh_id, double* coef_out, double* dt_exp_out, double* dt_imp_out,
+                     int on_device);
+
+/*
+ * One multi-colour LU-SGS step with DF relaxation (Sec 4.2-4.3, Eqs.
+ * gpu-forward-relaxation and gpu-backward-relaxation) on level `level` for
+ * caller data: solves D dW + 1/2 alpha sum S [dT - r dW] = rhs forward over
+ * colours 1..Nc then backward, with D = alpha (V/dt_imp + 1/2 sum S r) +
+ * (1 - alpha) V/dt_exp, and applies W += dW with the positivity guard.
+ * W_inout [n][nv] is updated; dW_out [n][nv] may be NULL.  mode selects the
+ * sweep precision (CGKS_PLAIN_FP64 / CGKS_MIXED).
+ */
+int cgks_lusgs(cgks_t* h, int mesh_id, int level, int mode, double* W_inout, const double* rhs,
+               const double* alpha, const double* dt_exp, const double* dt_imp, double* dW_out, int on_device);
+
+/*
+ * Fine smoothing: n_sweeps x (third-order residual, DF-relaxed multi-colour
+ * LU-SGS driven by -R, slope update with DF) on the current fine state.  Only
+ * level 0 is accepted; coarse smoothing runs inside cgks_vcycle.
+ */
+int cgks_smooth(cgks_t* h, int mesh_id, int level, int n_sweeps);
+
+/*
+ * V-cycles (Sec 5.2; pre-smooth 1, post-smooth 0): residual and slope update,
+ * fine LU-SGS, residual, restriction, FAS forcing, n_sweep_coarse KFVS +
+ * LU-SGS steps per coarse level, DF-limited injection prolongation.  Runs up
+ * to n_cycles cycles on each mesh (captured once into a CUDA graph and
+ * replayed), stopping a mesh once its fine RMS density residual has dropped
+ * by cfg.tol relative to its first recorded cycle (checked every
+ * cfg.check_every cycles).  norms_out (host, nullable) receives
+ * [n_meshes][n_cycles][nv][2] fine-level (RMS, max) of R/V at the start of
+ * each cycle; entries of cycles not run are set to -1.  cycles_done (host,
+ * nullable) [n_meshes].
+ */
+int cgks_vcycle(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int mode, double* norms_out,
+                int* cycles_done);
+
+/* Residual norms of the last fine residual evaluation: out (host) [nv][2] =
+ * RMS and max over cells of R/V.  Level 0 only.  Synchronises the stream. */
+int cgks_residual_norms(cgks_t* h, int mesh_id, int level, double* out);
+
+/* Event counters since init_state (host uint64 [4]): reconstruction
+ * positivity fallbacks, halved updates, dropped updates, non-finite updates. */
+int cgks_counters(cgks_t* h, int mesh_id, uint64_t* out);
+
+/* Point evaluations for parity checks, device pointers, local frame (normal
+ * = first velocity component): Wl, Wr [n][nv]; Gl, Gr [n][dim][nv] derivatives
+ * along (n, t1, t2); dt [n].  Outputs F (time-averaged flux), Wt (point value
+ * at t = dt) [n][nv] and the DF point factor alpha [n]. */
+int cgks_gks_points(cgks_t* h, int dim, int64_t n, const double* Wl, const double* Gl, const double* Wr,
+                    const double* Gr, const double* dt, double* F, double* Wt, double* alpha);
+/* First-order KFVS flux of constant states, device pointers [n][nv]. */
+int cgks_kfvs_points(cgks_t* h, int dim, int64_t n, const double* Wl, const double* Wr, double* F);
+
+/* Waits for all work of h on its stream. */
+int cgks_synchronize(cgks_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGKS_H */

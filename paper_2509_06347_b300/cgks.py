@@ -1,0 +1,256 @@
+"""Thin Python binding of the CGKS C ABI (include/cgks.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+Device arrays are torch CUDA tensors (passed by data_ptr); host arrays are
+numpy arrays.  Importing works without a GPU; loading the library requires the
+built libcgks.so and raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcgks.so")
+
+CGKS_OK = 0
+ERRORS = {-1: "CGKS_ERR_ARG", -2: "CGKS_ERR_MESH", -3: "CGKS_ERR_CUDA", -4: "CGKS_ERR_DIVERGED",
+          -5: "CGKS_ERR_NONPOSITIVE", -6: "CGKS_ERR_TIMEOUT", -7: "CGKS_ERR_STATE"}
+PLAIN_FP64, MIXED = 0, 1
+TAG_WALL, TAG_FARFIELD = 1, 2
+
+# every entry point declared in include/cgks.h
+EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_error", "cgks_upload_mesh",
+           "cgks_upload_hierarchy", "cgks_mesh_info", "cgks_get_coloring", "cgks_set_freestream",
+           "cgks_init_state", "cgks_get_state", "cgks_set_state", "cgks_residual", "cgks_reconstruct",
+           "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
+           "cgks_gks_points", "cgks_kfvs_points", "cgks_synchronize"]
+
+
+class CgksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl_imp", C.c_double), ("cfl_exp", C.c_double),
+                ("tau_c1", C.c_double), ("tau_c2", C.c_double), ("weno_gamma_high", C.c_double),
+                ("weno_eps", C.c_double), ("r_safety", C.c_double), ("n_sweep_coarse", C.c_int),
+                ("n_pre", C.c_int), ("n_post", C.c_int), ("check_every", C.c_int), ("tol", C.c_double),
+                ("diverge_factor", C.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libcgks.so (raises FileNotFoundError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"CGKS CUDA library not built: {path} "
+                                "(run python -m paper_2509_06347_b300.build)")
+    L = C.CDLL(path)
+    P, I, I64, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    sig = {
+        "cgks_default_config": [C.POINTER(Config)],
+        "cgks_create": [C.POINTER(C.c_void_p), C.POINTER(Config), P],
+        "cgks_destroy": [P],
+        "cgks_upload_mesh": [P, I, I, I64, P, P, I64, P, P],
+        "cgks_upload_hierarchy": [P, I, I, P],
+        "cgks_mesh_info": [P, I, P, P],
+        "cgks_get_coloring": [P, I, I, P],
+        "cgks_set_freestream": [P, I, P],
+        "cgks_init_state": [P, I, P, P, I],
+        "cgks_get_state": [P, I, P, P, P, I],
+        "cgks_set_state": [P, I, P, P, P, I],
+        "cgks_residual": [P, I, I, P, P, P, P, I],
+        "cgks_reconstruct": [P, I, P, P, P, I],
+        "cgks_lusgs": [P, I, I, I, P, P, P, P, P, P, I],
+        "cgks_smooth": [P, I, I, I],
+        "cgks_vcycle": [P, P, I, I, I, P, P],
+        "cgks_residual_norms": [P, I, I, P],
+        "cgks_counters": [P, I, P],
+        "cgks_gks_points": [P, I, I64, P, P, P, P, P, P, P, P],
+        "cgks_kfvs_points": [P, I, I64, P, P, P],
+        "cgks_synchronize": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.cgks_last_error.argtypes = [P]
+    L.cgks_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def default_config(**over) -> Config:
+    cfg = Config()
+    load_library().cgks_default_config(C.byref(cfg))
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(a):
+    """Address of a torch tensor (device or host) or numpy array; None -> NULL."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _is_dev(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+class Context:
+    """One cgks_t handle bound to a CUDA stream (0 = library-private stream)."""
+
+    def __init__(self, config: Config | None = None, stream: int = 0, **over):
+        L = load_library()
+        self._L = L
+        cfg = config if config is not None else default_config(**over)
+        self.config = cfg
+        h = C.c_void_p()
+        rc = L.cgks_create(C.byref(h), C.byref(cfg), C.c_void_p(stream) if stream else None)
+        if rc != CGKS_OK:
+            raise CgksError(rc, "cgks_create failed")
+        self.h = h
+        self.meshes = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.cgks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != CGKS_OK:
+            raise CgksError(rc, self._L.cgks_last_error(self.h).decode())
+        return rc
+
+    # ---- mesh ----------------------------------------------------------------
+    def cgks_upload_mesh(self, mesh_id: int, mesh: dict):
+        cn = np.ascontiguousarray(mesh["cell_nodes"], np.int32)
+        cx = np.ascontiguousarray(mesh["cell_xyz"], np.float64)
+        bn = np.ascontiguousarray(mesh["bface_nodes"], np.int32)
+        bt = np.ascontiguousarray(mesh["bface_tag"], np.int32)
+        self._check(self._L.cgks_upload_mesh(self.h, mesh_id, int(mesh["dim"]), cn.shape[0], _ptr(cn), _ptr(cx),
+                                              bt.size, _ptr(bn) if bt.size else None, _ptr(bt) if bt.size else None))
+        self.meshes[mesh_id] = dict(dim=int(mesh["dim"]), n=cn.shape[0])
+
+    def cgks_upload_hierarchy(self, mesh_id: int, parents):
+        arrs = [np.ascontiguousarray(p, np.int32) for p in parents]
+        ptrs = (C.c_void_p * max(1, len(arrs)))(*[a.ctypes.data for a in arrs])
+        self._check(self._L.cgks_upload_hierarchy(self.h, mesh_id, len(arrs) + 1, ptrs))
+
+    def cgks_mesh_info(self, mesh_id: int):
+        nl = C.c_int()
+        out = np.zeros(32, np.int64)
+        self._check(self._L.cgks_mesh_info(self.h, mesh_id, C.byref(nl), _ptr(out)))
+        return [dict(cells=int(out[4 * l]), colors=int(out[4 * l + 1]), faces=int(out[4 * l + 2]),
+                     bfaces=int(out[4 * l + 3])) for l in range(nl.value)]
+
+    def cgks_get_coloring(self, mesh_id: int, level: int, n: int):
+        out = np.zeros(n, np.int32)
+        self._check(self._L.cgks_get_coloring(self.h, mesh_id, level, _ptr(out)))
+        return out
+
+    def cgks_set_freestream(self, mesh_id: int, w):
+        w = np.ascontiguousarray(w, np.float64)
+        self._check(self._L.cgks_set_freestream(self.h, mesh_id, _ptr(w)))
+
+    # ---- state -----------------------------------------------------------------
+    def cgks_init_state(self, mesh_id: int, W, grad=None):
+        dev = _is_dev(W)
+        if not dev:
+            W = np.ascontiguousarray(W, np.float64)
+            grad = None if grad is None else np.ascontiguousarray(grad, np.float64)
+        self._check(self._L.cgks_init_state(self.h, mesh_id, _ptr(W), _ptr(grad), int(dev)))
+
+    def cgks_set_state(self, mesh_id: int, W=None, grad=None, alpha=None):
+        arrs = [W, grad, alpha]
+        dev = any(_is_dev(a) for a in arrs if a is not None)
+        if not dev:
+            arrs = [None if a is None else np.ascontiguousarray(a, np.float64) for a in arrs]
+        self._check(self._L.cgks_set_state(self.h, mesh_id, *[_ptr(a) for a in arrs], int(dev)))
+
+    def cgks_get_state(self, mesh_id: int, W=None, grad=None, alpha=None):
+        """Fills the given arrays (all torch CUDA tensors, or all numpy arrays)."""
+        arrs = [W, grad, alpha]
+        dev = any(_is_dev(a) for a in arrs if a is not None)
+        self._check(self._L.cgks_get_state(self.h, mesh_id, *[_ptr(a) for a in arrs], int(dev)))
+        return W, grad, alpha
+
+    def cgks_residual(self, mesh_id: int, level: int = 0, W_in=None, R=None, grad_new=None, alpha=None):
+        arrs = [W_in, R, grad_new, alpha]
+        dev = any(_is_dev(a) for a in arrs if a is not None)
+        self._check(self._L.cgks_residual(self.h, mesh_id, level, *[_ptr(a) for a in arrs], int(dev)))
+        return R, grad_new, alpha
+
+    def cgks_reconstruct(self, mesh_id: int, coef=None, dt_exp=None, dt_imp=None):
+        arrs = [coef, dt_exp, dt_imp]
+        dev = any(_is_dev(a) for a in arrs if a is not None)
+        self._check(self._L.cgks_reconstruct(self.h, mesh_id, *[_ptr(a) for a in arrs], int(dev)))
+        return coef, dt_exp, dt_imp
+
+    def cgks_lusgs(self, mesh_id: int, level: int, mode: int, W, rhs, alpha, dt_exp, dt_imp, dW=None):
+        arrs = [W, rhs, alpha, dt_exp, dt_imp, dW]
+        dev = any(_is_dev(a) for a in arrs if a is not None)
+        self._check(self._L.cgks_lusgs(self.h, mesh_id, level, mode, *[_ptr(a) for a in arrs], int(dev)))
+        return W, dW
+
+    def cgks_smooth(self, mesh_id: int, level: int, n_sweeps: int):
+        self._check(self._L.cgks_smooth(self.h, mesh_id, level, n_sweeps))
+
+    def cgks_vcycle(self, mesh_ids, n_cycles: int, mode: int = PLAIN_FP64, norms=None, cycles_done=None,
+                    check: bool = True):
+        ids = np.ascontiguousarray(mesh_ids, np.int32)
+        rc = self._L.cgks_vcycle(self.h, _ptr(ids), ids.size, n_cycles, mode, _ptr(norms), _ptr(cycles_done))
+        if check:
+            self._check(rc)
+        return rc
+
+    def cgks_residual_norms(self, mesh_id: int, level: int = 0):
+        nv = self.meshes[mesh_id]["dim"] + 2
+        out = np.zeros((nv, 2))
+        self._check(self._L.cgks_residual_norms(self.h, mesh_id, level, _ptr(out)))
+        return out
+
+    def cgks_counters(self, mesh_id: int):
+        out = np.zeros(4, np.uint64)
+        self._check(self._L.cgks_counters(self.h, mesh_id, _ptr(out)))
+        return out
+
+    def cgks_gks_points(self, dim, Wl, Gl, Wr, Gr, dt, F, Wt, alpha):
+        self._check(self._L.cgks_gks_points(self.h, dim, Wl.shape[0], *[_ptr(a) for a in (Wl, Gl, Wr, Gr, dt, F, Wt,
+                                                                                          alpha)]))
+
+    def cgks_kfvs_points(self, dim, Wl, Wr, F):
+        self._check(self._L.cgks_kfvs_points(self.h, dim, Wl.shape[0], _ptr(Wl), _ptr(Wr), _ptr(F)))
+
+    def cgks_synchronize(self):
+        self._check(self._L.cgks_synchronize(self.h))
+
+    # ---- convenience -------------------------------------------------------------
+    def setup(self, mesh_id: int, mesh: dict, winf, W, grad=None, levels: int | None = None):
+        """Upload mesh + hierarchy, set the free stream and the initial state."""
+        self.cgks_upload_mesh(mesh_id, mesh)
+        parents = mesh.get("parents", [])
+        if levels is not None:
+            parents = parents[: levels - 1]
+        self.cgks_upload_hierarchy(mesh_id, parents)
+        self.cgks_set_freestream(mesh_id, winf)
+        self.cgks_init_state(mesh_id, W, grad)

@@ -1,0 +1,934 @@
+// C ABI of the CGKS library: device buffers, V-cycle orchestration on the
+// caller's stream, CUDA-graph capture and replay.  See include/cgks.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "cgks.h"
+#include "host_mesh.hpp"
+#include "kernels.cuh"
+
+namespace cgks {
+namespace {
+
+struct CudaError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct ArgError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct StateError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+#define CK(x)                                                                                     \
+  do {                                                                                            \
+    cudaError_t e_ = (x);                                                                         \
+    if (e_ != cudaSuccess) throw CudaError(std::string(#x) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+inline unsigned blocks_for(int64_t n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
+
+// owning device allocation
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() {
+    if (p) cudaFree(p);
+  }
+  void alloc(size_t b) {
+    if (p) { cudaFree(p); p = nullptr; }
+    bytes = b;
+    if (b) CK(cudaMalloc(&p, b));
+  }
+  template <class T>
+  T* as() const { return (T*)p; }
+};
+
+template <class T>
+T* upload(std::vector<std::unique_ptr<DBuf>>& pool, const std::vector<T>& v) {
+  pool.emplace_back(new DBuf);
+  DBuf& b = *pool.back();
+  b.alloc(std::max<size_t>(1, v.size()) * sizeof(T));
+  if (!v.empty()) CK(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return b.as<T>();
+}
+template <class T>
+T* dalloc(std::vector<std::unique_ptr<DBuf>>& pool, size_t n) {
+  pool.emplace_back(new DBuf);
+  pool.back()->alloc(std::max<size_t>(1, n) * sizeof(T));
+  CK(cudaMemset(pool.back()->p, 0, std::max<size_t>(1, n) * sizeof(T)));
+  return pool.back()->as<T>();
+}
+template <class A>
+std::vector<int32_t> to_i32(const std::vector<A>& v) {
+  std::vector<int32_t> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (int32_t)v[i];
+  return o;
+}
+
+struct LevelDev {
+  int n = 0, n_colors = 0;
+  std::vector<int> color_off;  // host
+  Topo topo{};
+  int* iperm = nullptr;  // new -> original
+  double* vol = nullptr;
+  double *W = nullptr, *W0 = nullptr, *alpha = nullptr, *R = nullptr, *P = nullptr, *Rstar = nullptr;
+  double *D = nullptr, *dte = nullptr, *dti = nullptr;
+  double *dWs64 = nullptr, *dW64 = nullptr;
+  float *dWs32 = nullptr, *dW32 = nullptr;
+  int* parent = nullptr;  // this level's cell -> next coarser level cell
+  int *ch_off = nullptr, *ch_idx = nullptr;  // children in the finer level
+};
+
+struct MeshDev {
+  int dim = 0, nv = 0, nlev = 0;
+  Hierarchy H;
+  bool has_hierarchy = false, has_state = false;
+  std::vector<std::unique_ptr<DBuf>> pool;
+  DevFine fine{};
+  double *G = nullptr, *coef = nullptr, *Fface = nullptr, *Wface = nullptr, *aface = nullptr;
+  double *gradnew = nullptr, *norm_part = nullptr, *last_norm = nullptr, *hist = nullptr;
+  double* stage = nullptr;  // staging for permuted I/O, size n * max(nv*dim, ncoef*nv)
+  size_t stage_elems = 0;
+  int* cycle = nullptr;
+  int max_hist = 0;
+  int norm_blocks = 0;
+  double* winf = nullptr;
+  std::vector<double> winf_h;
+  Counters* cnt = nullptr;
+  std::vector<LevelDev> lev;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  ~MeshDev() {
+    for (auto& g : graph)
+      if (g) cudaGraphExecDestroy(g);
+  }
+};
+
+}  // namespace
+}  // namespace cgks
+
+struct cgks_ctx {
+  cgks_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::map<int, std::unique_ptr<cgks::MeshDev>> meshes;
+  std::string err;
+  std::vector<std::unique_ptr<cgks::DBuf>> scratch;  // point-evaluation helpers
+};
+
+namespace cgks {
+namespace {
+
+MeshDev& get_mesh(cgks_t* h, int id) {
+  auto it = h->meshes.find(id);
+  if (it == h->meshes.end()) throw ArgError("unknown mesh id " + std::to_string(id));
+  return *it->second;
+}
+
+PhysParams phys(const cgks_config& c, int dim) {
+  PhysParams p;
+  p.gamma = c.gamma;
+  p.K = dim == 2 ? (4.0 - 2.0 * c.gamma) / (c.gamma - 1.0) : (5.0 - 3.0 * c.gamma) / (c.gamma - 1.0);
+  p.c1 = c.tau_c1;
+  p.c2 = c.tau_c2;
+  return p;
+}
+
+// ---- device structures from the host hierarchy ----------------------------
+void build_fine_device(MeshDev& M) {
+  const FineLevel& F = M.H.fine;
+  const int dim = F.dim, nfc = F.nfc;
+  const int64_t n = F.n;
+  auto& P = M.pool;
+  DevFine d{};
+  d.n = (int)n;
+  d.nf = (int)F.nf;
+  d.fL = upload(P, to_i32(F.fL));
+  d.fR = upload(P, to_i32(F.fR));
+  d.ftag = upload(P, F.ftag);
+  d.fn = upload(P, F.fn);
+  d.fS = upload(P, F.fS);
+  d.XL = upload(P, F.XL);
+  d.XR = upload(P, F.XR);
+  d.cface = upload(P, to_i32(F.cface));
+  std::vector<signed char> cs(F.cside.begin(), F.cside.end());
+  d.cside = upload(P, cs);
+  d.cnbr = upload(P, to_i32(F.cnbr));
+  // variable-major per-cell geometry
+  auto transpose = [&](const std::vector<double>& a, int w) {
+    std::vector<double> t((size_t)w * n);
+    for (int64_t c = 0; c < n; ++c)
+      for (int k = 0; k < w; ++k) t[(size_t)k * n + c] = a[(size_t)c * w + k];
+    return t;
+  };
+  d.op = upload(P, transpose(F.op, F.nop));
+  std::vector<unsigned char> ok(F.op_ok.begin(), F.op_ok.end());
+  d.op_ok = upload(P, ok);
+  d.avg0 = upload(P, transpose(F.avg0, F.nk));
+  d.gg = upload(P, transpose(F.gg, nfc * dim));
+  d.m2 = upload(P, transpose(F.m2, dim * dim));
+  d.vol = upload(P, F.vol);
+  std::vector<double> bsc(n);
+  for (int64_t c = 0; c < n; ++c) bsc[c] = std::pow(F.vol[c], 2.0 / dim);
+  d.bsc = upload(P, bsc);
+  M.fine = d;
+}
+
+Topo make_topo(MeshDev& M, int64_t n, const std::vector<int64_t>& off, const std::vector<int64_t>& nbr,
+               const std::vector<int32_t>& tag, const std::vector<int8_t>& side, const std::vector<double>& S,
+               const std::vector<double>& nrm, const double* vol_dev) {
+  auto& P = M.pool;
+  Topo t{};
+  t.n = (int)n;
+  t.off = upload(P, to_i32(off));
+  t.nbr = upload(P, to_i32(nbr));
+  t.tag = upload(P, tag);
+  std::vector<signed char> sd(side.begin(), side.end());
+  t.side = upload(P, sd);
+  t.S = upload(P, S);
+  t.nrm = upload(P, nrm);
+  t.vol = vol_dev;
+  return t;
+}
+
+void alloc_level_state(MeshDev& M, LevelDev& L) {
+  auto& P = M.pool;
+  const int nv = M.nv;
+  L.W = dalloc<double>(P, (size_t)L.n * nv);
+  L.W0 = dalloc<double>(P, (size_t)L.n * nv);
+  L.alpha = dalloc<double>(P, L.n);
+  L.R = dalloc<double>(P, (size_t)L.n * nv);
+  L.P = dalloc<double>(P, (size_t)L.n * nv);
+  L.Rstar = dalloc<double>(P, (size_t)L.n * nv);
+  L.D = dalloc<double>(P, L.n);
+  L.dte = dalloc<double>(P, L.n);
+  L.dti = dalloc<double>(P, L.n);
+  L.dWs64 = dalloc<double>(P, (size_t)L.n * nv);
+  L.dW64 = dalloc<double>(P, (size_t)L.n * nv);
+  L.dWs32 = dalloc<float>(P, (size_t)L.n * nv);
+  L.dW32 = dalloc<float>(P, (size_t)L.n * nv);
+}
+
+void build_levels_device(MeshDev& M) {
+  const FineLevel& F = M.H.fine;
+  const int dim = F.dim, nfc = F.nfc;
+  M.lev.clear();
+  M.lev.resize(1 + M.H.coarse.size());
+  // fine level
+  {
+    LevelDev& L = M.lev[0];
+    L.n = (int)F.n;
+    L.n_colors = F.n_colors;
+    L.color_off.assign(F.color_off.begin(), F.color_off.end());
+    L.iperm = upload(M.pool, to_i32(F.iperm));
+    L.vol = const_cast<double*>(M.fine.vol);
+    std::vector<int64_t> off(F.n + 1), nbr(F.n * nfc);
+    std::vector<int32_t> tag(F.n * nfc);
+    std::vector<int8_t> side(F.n * nfc);
+    std::vector<double> S(F.n * nfc), nrm(F.n * nfc * dim);
+    for (int64_t c = 0; c <= F.n; ++c) off[c] = c * nfc;
+    for (int64_t c = 0; c < F.n; ++c)
+      for (int k = 0; k < nfc; ++k) {
+        const int64_t e = c * nfc + k, f = F.cface[e];
+        nbr[e] = F.cnbr[e];
+        tag[e] = F.ftag[f];
+        side[e] = F.cside[e];
+        S[e] = F.fS[f];
+        for (int d = 0; d < dim; ++d) nrm[e * dim + d] = F.cside[e] * F.fn[f * dim + d];
+      }
+    L.topo = make_topo(M, F.n, off, nbr, tag, side, S, nrm, L.vol);
+    alloc_level_state(M, L);
+  }
+  for (size_t l = 0; l < M.H.coarse.size(); ++l) {
+    const CoarseLevel& C = M.H.coarse[l];
+    LevelDev& L = M.lev[l + 1];
+    L.n = (int)C.n;
+    L.n_colors = C.n_colors;
+    L.color_off.assign(C.color_off.begin(), C.color_off.end());
+    L.iperm = upload(M.pool, to_i32(C.iperm));
+    L.vol = upload(M.pool, C.vol);
+    const int64_t ne = C.cf_off[C.n];
+    std::vector<int64_t> nbr(ne);
+    std::vector<int32_t> tag(ne);
+    std::vector<double> S(ne), nrm(ne * dim);
+    for (int64_t J = 0; J < C.n; ++J)
+      for (int64_t e = C.cf_off[J]; e < C.cf_off[J + 1]; ++e) {
+        const int64_t f = C.cf_face[e];
+        const int sd = C.cf_side[e];
+        nbr[e] = sd > 0 ? C.fR[f] : C.fL[f];
+        tag[e] = C.ftag[f];
+        S[e] = C.fS[f];
+        for (int d = 0; d < dim; ++d) nrm[e * dim + d] = sd * C.fn[f * dim + d];
+      }
+    L.topo = make_topo(M, C.n, C.cf_off, nbr, tag, C.cf_side, S, nrm, L.vol);
+    alloc_level_state(M, L);
+    L.ch_off = upload(M.pool, to_i32(C.ch_off));
+    L.ch_idx = upload(M.pool, to_i32(C.ch_idx));
+    M.lev[l].parent = upload(M.pool, to_i32(C.parent_of_fine));
+  }
+  // fine-only buffers
+  const int nv = M.nv, nc = dim == 2 ? 6 : 10;
+  auto& P = M.pool;
+  M.G = dalloc<double>(P, (size_t)F.n * nv * dim);
+  M.coef = dalloc<double>(P, (size_t)F.n * nv * nc);
+  M.Fface = dalloc<double>(P, (size_t)F.nf * nv);
+  M.Wface = dalloc<double>(P, (size_t)F.nf * nv);
+  M.aface = dalloc<double>(P, F.nf);
+  M.gradnew = dalloc<double>(P, (size_t)F.n * nv * dim);
+  M.norm_blocks = (int)blocks_for(F.n);
+  M.norm_part = dalloc<double>(P, (size_t)M.norm_blocks * 2 * nv);
+  M.last_norm = dalloc<double>(P, 2 * nv);
+  M.max_hist = 1 << 16;
+  M.hist = dalloc<double>(P, (size_t)M.max_hist * 2 * nv);
+  M.cycle = dalloc<int>(P, 1);
+  M.stage_elems = (size_t)F.n * std::max(nv * dim, nv * nc);
+  M.stage = dalloc<double>(P, M.stage_elems);
+  M.cnt = dalloc<Counters>(P, 1);
+  M.winf = dalloc<double>(P, nv);
+  if (!M.winf_h.empty()) CK(cudaMemcpy(M.winf, M.winf_h.data(), nv * sizeof(double), cudaMemcpyHostToDevice));
+}
+
+// ---- kernels sequences ------------------------------------------------------
+template <int DIM>
+void launch_recon(cgks_t* h, MeshDev& M) {
+  LevelDev& L = M.lev[0];
+  k_recon<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
+      M.fine, L.W, M.G, L.alpha, M.winf, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, h->cfg.weno_gamma_high,
+      h->cfg.weno_eps, M.coef, L.dte, L.dti, M.cnt);
+}
+
+template <int DIM>
+void launch_flux(cgks_t* h, MeshDev& M) {
+  LevelDev& L = M.lev[0];
+  constexpr int NGP = Dims<DIM>::NGP, FPW = 32 / NGP;
+  const int64_t warps = (M.fine.nf + FPW - 1) / FPW;
+  const int64_t threads = warps * 32;
+  k_flux<DIM><<<blocks_for(threads), kBlock, 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, phys(h->cfg, DIM),
+                                                               M.Fface, M.Wface, M.aface);
+}
+
+// fine residual: slopes_update -> G <- alpha * grad_new; want_diag -> LU-SGS D;
+// want_norm -> norm partials + final (hist when record)
+template <int DIM>
+void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bool want_norm, bool record,
+                   double* alpha_out_dev, double* gradnew_dev) {
+  LevelDev& L = M.lev[0];
+  launch_recon<DIM>(h, M);
+  launch_flux<DIM>(h, M);
+  k_gather<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
+      M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R,
+      slopes_update ? M.G : nullptr, alpha_out_dev ? alpha_out_dev : L.alpha, want_diag ? L.D : nullptr,
+      gradnew_dev, want_norm ? M.norm_part : nullptr);
+  if (want_norm)
+    k_norm_final<DIM + 2><<<1, kBlock, 0, h->stream>>>(M.norm_part, M.norm_blocks, L.n, record ? M.hist : nullptr,
+                                                       record ? M.cycle : nullptr, M.max_hist, M.last_norm);
+}
+
+template <int DIM, typename T>
+void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
+  T* dWs = sizeof(T) == 8 ? (T*)L.dWs64 : (T*)L.dWs32;
+  T* dW = sizeof(T) == 8 ? (T*)L.dW64 : (T*)L.dW32;
+  const int nc = L.n_colors;
+  for (int c = 0; c < nc - 1; ++c) {
+    const int lo = L.color_off[c], hi = L.color_off[c + 1];
+    if (hi > lo)
+      k_sweep<DIM, T, 0><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, L.alpha, L.D,
+                                                                         h->cfg.gamma, dWs, dW);
+  }
+  {
+    const int lo = L.color_off[nc - 1], hi = L.color_off[nc];
+    if (hi > lo)
+      k_sweep<DIM, T, 2><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, L.alpha, L.D,
+                                                                         h->cfg.gamma, dWs, dW);
+  }
+  for (int c = nc - 2; c >= 0; --c) {
+    const int lo = L.color_off[c], hi = L.color_off[c + 1];
+    if (hi > lo)
+      k_sweep<DIM, T, 1><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, L.alpha, L.D,
+                                                                         h->cfg.gamma, dWs, dW);
+  }
+  k_update<DIM, T><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, h->cfg.gamma, L.W, dW, M.cnt);
+}
+
+template <int DIM>
+void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag) {
+  const PhysParams p = phys(h->cfg, DIM);
+  k_coarse_prep<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W, Pf, L.alpha, M.winf, h->cfg.gamma, p.K,
+                                                                 h->cfg.cfl_exp, h->cfg.cfl_imp, L.R,
+                                                                 want_diag ? L.D : nullptr);
+}
+
+template <int DIM, typename T>
+void vcycle_body(cgks_t* h, MeshDev& M) {
+  LevelDev& L0 = M.lev[0];
+  const PhysParams p = phys(h->cfg, DIM);
+  // 1. residual, norms, slope update with DF, LU-SGS diagonal
+  fine_residual<DIM>(h, M, true, true, true, true, nullptr, nullptr);
+  // 2. one DF-relaxed LU-SGS pre-smoothing step on -R
+  sweeps<DIM, T>(h, M, L0, nullptr);
+  if (M.nlev == 1) return;
+  // 3. residual at the smoothed state (no slope update); its DF is kept
+  fine_residual<DIM>(h, M, false, false, false, false, nullptr, nullptr);
+  // 4-7. restriction, forcing, coarse smoothing
+  for (int l = 1; l < M.nlev; ++l) {
+    LevelDev& F = M.lev[l - 1];
+    LevelDev& C = M.lev[l];
+    k_restrict<DIM><<<blocks_for(C.n), kBlock, 0, h->stream>>>(C.n, C.ch_off, C.ch_idx, F.vol, C.vol, F.W, F.alpha,
+                                                                F.R, C.W0, C.W, C.alpha, C.Rstar);
+    k_forcing<DIM><<<blocks_for(C.n), kBlock, 0, h->stream>>>(C.topo, C.W0, C.Rstar, M.winf, p.K, C.P);
+    for (int s = 0; s < h->cfg.n_sweep_coarse; ++s) {
+      coarse_prep<DIM>(h, M, C, C.P, true);
+      sweeps<DIM, T>(h, M, C, nullptr);
+    }
+    if (l + 1 < M.nlev) coarse_prep<DIM>(h, M, C, C.P, false);  // R~ = R(W) + P to restrict
+  }
+  // 8. prolongation, coarsest to fine
+  for (int l = M.nlev - 1; l >= 1; --l) {
+    LevelDev& F = M.lev[l - 1];
+    LevelDev& C = M.lev[l];
+    k_prolong<DIM><<<blocks_for(F.n), kBlock, 0, h->stream>>>(F.n, F.parent, F.alpha, C.W, C.W0, h->cfg.gamma, F.W,
+                                                               M.cnt);
+  }
+}
+
+template <int DIM>
+void run_vcycle_body(cgks_t* h, MeshDev& M, int mode) {
+  if (mode == CGKS_MIXED) vcycle_body<DIM, float>(h, M);
+  else vcycle_body<DIM, double>(h, M);
+}
+
+void enqueue_vcycle(cgks_t* h, MeshDev& M, int mode) {
+  if (M.dim == 2) run_vcycle_body<2>(h, M, mode);
+  else run_vcycle_body<3>(h, M, mode);
+}
+
+cudaGraphExec_t get_graph(cgks_t* h, MeshDev& M, int mode) {
+  if (M.graph[mode]) return M.graph[mode];
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    enqueue_vcycle(h, M, mode);
+  } catch (...) {
+    cudaStreamEndCapture(h->stream, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  CK(cudaStreamEndCapture(h->stream, &g));
+  cudaGraphExec_t ge;
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  M.graph[mode] = ge;
+  return ge;
+}
+
+// ---- I/O with permutation ------------------------------------------------
+// copy caller rows (original order) into dst (device colour order)
+void load_rows(cgks_t* h, MeshDev& M, const LevelDev& L, int w, const double* src, bool on_device, double* dst) {
+  const size_t bytes = (size_t)L.n * w * sizeof(double);
+  if ((size_t)L.n * w > M.stage_elems) throw ArgError("staging buffer too small");
+  if (on_device) CK(cudaMemcpyAsync(M.stage, src, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  else CK(cudaMemcpyAsync(M.stage, src, bytes, cudaMemcpyHostToDevice, h->stream));
+  k_gather_rows<<<blocks_for((int64_t)L.n * w), kBlock, 0, h->stream>>>(L.n, w, L.iperm, M.stage, dst);
+  CK(cudaGetLastError());
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));  // host source must outlive the copy
+}
+void store_rows(cgks_t* h, MeshDev& M, const LevelDev& L, int w, const double* src, bool on_device, double* dst) {
+  const size_t bytes = (size_t)L.n * w * sizeof(double);
+  if ((size_t)L.n * w > M.stage_elems) throw ArgError("staging buffer too small");
+  k_scatter_rows<<<blocks_for((int64_t)L.n * w), kBlock, 0, h->stream>>>(L.n, w, L.iperm, src, M.stage);
+  CK(cudaGetLastError());
+  if (on_device) CK(cudaMemcpyAsync(dst, M.stage, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  else {
+    CK(cudaMemcpyAsync(dst, M.stage, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+}
+
+void require_ready(MeshDev& M, bool state) {
+  if (!M.has_hierarchy) throw StateError("cgks_upload_hierarchy has not been called for this mesh");
+  if (state && !M.has_state) throw StateError("cgks_init_state has not been called for this mesh");
+  if (state && M.winf_h.empty()) throw StateError("cgks_set_freestream has not been called for this mesh");
+}
+
+int fail(cgks_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+template <class F>
+int guarded(cgks_t* h, F&& f) {
+  if (!h) return CGKS_ERR_ARG;
+  try {
+    h->err.clear();
+    return f();
+  } catch (const ArgError& e) {
+    return fail(h, CGKS_ERR_ARG, e.what());
+  } catch (const StateError& e) {
+    return fail(h, CGKS_ERR_STATE, e.what());
+  } catch (const CudaError& e) {
+    return fail(h, CGKS_ERR_CUDA, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(h, CGKS_ERR_CUDA, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(h, CGKS_ERR_MESH, e.what());
+  }
+}
+
+}  // namespace
+}  // namespace cgks
+
+using namespace cgks;
+
+extern "C" {
+
+int cgks_default_config(cgks_config* c) {
+  if (!c) return CGKS_ERR_ARG;
+  c->gamma = 1.4;
+  c->cfl_imp = 10.0;
+  c->cfl_exp = 0.5;
+  c->tau_c1 = 0.01;
+  c->tau_c2 = 1.0;
+  c->weno_gamma_high = 0.95;
+  c->weno_eps = 1e-15;
+  c->r_safety = 1.0;
+  c->n_sweep_coarse = 6;
+  c->n_pre = 1;
+  c->n_post = 0;
+  c->check_every = 10;
+  c->tol = 1e-10;
+  c->diverge_factor = 1e6;
+  return CGKS_OK;
+}
+
+int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
+  if (!out) return CGKS_ERR_ARG;
+  *out = nullptr;
+  cgks_t* h = new (std::nothrow) cgks_ctx();
+  if (!h) return CGKS_ERR_CUDA;
+  if (cfg) h->cfg = *cfg;
+  else cgks_default_config(&h->cfg);
+  if (h->cfg.n_pre != 1 || h->cfg.n_post != 0 || h->cfg.n_sweep_coarse < 1 || !(h->cfg.gamma > 1.0) ||
+      h->cfg.r_safety != 1.0 || !(h->cfg.weno_gamma_high > 0.0 && h->cfg.weno_gamma_high <= 1.0) ||
+      h->cfg.check_every < 1) {
+    delete h;
+    return CGKS_ERR_ARG;
+  }
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return CGKS_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  *out = h;
+  return CGKS_OK;
+}
+
+int cgks_destroy(cgks_t* h) {
+  if (!h) return CGKS_OK;
+  cudaStreamSynchronize(h->stream);
+  h->meshes.clear();
+  h->scratch.clear();
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return CGKS_OK;
+}
+
+const char* cgks_last_error(cgks_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int cgks_synchronize(cgks_t* h) {
+  return guarded(h, [&]() -> int {
+    CK(cudaStreamSynchronize(h->stream));
+    return CGKS_OK;
+  });
+}
+
+int cgks_upload_mesh(cgks_t* h, int mesh_id, int dim, int64_t n_cells, const int32_t* cell_nodes,
+                     const double* cell_xyz, int64_t n_bfaces, const int32_t* bface_nodes,
+                     const int32_t* bface_tag) {
+  return guarded(h, [&]() -> int {
+    if ((dim != 2 && dim != 3) || n_cells <= 0 || !cell_nodes || !cell_xyz || n_bfaces < 0 ||
+        (n_bfaces > 0 && (!bface_nodes || !bface_tag)) || n_cells >= (1ll << 30))
+      throw ArgError("invalid mesh arguments");
+    for (int64_t b = 0; b < n_bfaces; ++b)
+      if (bface_tag[b] != CGKS_TAG_WALL && bface_tag[b] != CGKS_TAG_FARFIELD) throw ArgError("unknown boundary tag");
+    auto M = std::make_unique<MeshDev>();
+    M->dim = dim;
+    M->nv = dim + 2;
+    try {
+      build_fine_level(dim, n_cells, cell_nodes, cell_xyz, n_bfaces, bface_nodes, bface_tag, M->H.fine);
+    } catch (const std::runtime_error& e) {
+      return fail(h, CGKS_ERR_MESH, e.what());
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    h->meshes[mesh_id] = std::move(M);
+    return CGKS_OK;
+  });
+}
+
+int cgks_upload_hierarchy(cgks_t* h, int mesh_id, int n_levels, const int32_t* const* parent) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    if (n_levels < 1 || n_levels > 8 || (n_levels > 1 && !parent)) throw ArgError("invalid level count");
+    M.H.coarse.clear();
+    for (auto& g : M.graph)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    try {
+      for (int l = 1; l < n_levels; ++l) {
+        if (!parent[l - 1]) throw ArgError("null parent array");
+        CoarseLevel C;
+        build_coarse_level(M.H, l - 1, parent[l - 1], C);
+        M.H.coarse.push_back(std::move(C));
+      }
+    } catch (const ArgError&) {
+      throw;
+    } catch (const std::runtime_error& e) {
+      return fail(h, CGKS_ERR_MESH, e.what());
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    M.pool.clear();
+    M.nlev = n_levels;
+    build_fine_device(M);
+    build_levels_device(M);
+    M.has_hierarchy = true;
+    M.has_state = false;
+    CK(cudaDeviceSynchronize());
+    return CGKS_OK;
+  });
+}
+
+int cgks_mesh_info(cgks_t* h, int mesh_id, int* n_levels, int64_t* out) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    const int nl = 1 + (int)M.H.coarse.size();
+    if (n_levels) *n_levels = nl;
+    if (out) {
+      out[0] = M.H.fine.n;
+      out[1] = M.H.fine.n_colors;
+      out[2] = M.H.fine.nf;
+      out[3] = M.H.fine.nf - M.H.fine.nf_int;
+      for (int l = 1; l < nl; ++l) {
+        const CoarseLevel& C = M.H.coarse[l - 1];
+        int64_t nb = 0;
+        for (int64_t f = 0; f < C.nf; ++f) nb += C.fR[f] < 0;
+        out[4 * l + 0] = C.n;
+        out[4 * l + 1] = C.n_colors;
+        out[4 * l + 2] = C.nf;
+        out[4 * l + 3] = nb;
+      }
+    }
+    return CGKS_OK;
+  });
+}
+
+int cgks_get_coloring(cgks_t* h, int mesh_id, int level, int32_t* colors) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    if (!colors || level < 0 || level > (int)M.H.coarse.size()) throw ArgError("invalid level");
+    const std::vector<int32_t>& c = level == 0 ? M.H.fine.color_orig : M.H.coarse[level - 1].color_orig;
+    std::memcpy(colors, c.data(), c.size() * sizeof(int32_t));
+    return CGKS_OK;
+  });
+}
+
+int cgks_set_freestream(cgks_t* h, int mesh_id, const double* w) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    if (!w) throw ArgError("null free stream");
+    M.winf_h.assign(w, w + M.nv);
+    if (M.winf) CK(cudaMemcpyAsync(M.winf, M.winf_h.data(), M.nv * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return CGKS_OK;
+  });
+}
+
+int cgks_set_state(cgks_t* h, int mesh_id, const double* W, const double* grad, const double* alpha,
+                   int on_device) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, false);
+    LevelDev& L = M.lev[0];
+    if (W) load_rows(h, M, L, M.nv, W, on_device, L.W);
+    if (grad) load_rows(h, M, L, M.nv * M.dim, grad, on_device, M.G);
+    if (alpha) load_rows(h, M, L, 1, alpha, on_device, L.alpha);
+    if (W) M.has_state = true;
+    return CGKS_OK;
+  });
+}
+
+int cgks_init_state(cgks_t* h, int mesh_id, const double* W, const double* grad, int on_device) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, false);
+    if (!W) throw ArgError("null state");
+    LevelDev& L = M.lev[0];
+    load_rows(h, M, L, M.nv, W, on_device, L.W);
+    if (grad) load_rows(h, M, L, M.nv * M.dim, grad, on_device, M.G);
+    else CK(cudaMemsetAsync(M.G, 0, (size_t)L.n * M.nv * M.dim * sizeof(double), h->stream));
+    k_fill<<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, 1.0, L.alpha);
+    CK(cudaMemsetAsync(M.cnt, 0, sizeof(Counters), h->stream));
+    CK(cudaMemsetAsync(M.cycle, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    M.has_state = true;
+    return CGKS_OK;
+  });
+}
+
+int cgks_get_state(cgks_t* h, int mesh_id, double* W, double* grad, double* alpha, int on_device) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    LevelDev& L = M.lev[0];
+    if (W) store_rows(h, M, L, M.nv, L.W, on_device, W);
+    if (grad) store_rows(h, M, L, M.nv * M.dim, M.G, on_device, grad);
+    if (alpha) store_rows(h, M, L, 1, L.alpha, on_device, alpha);
+    return CGKS_OK;
+  });
+}
+
+int cgks_residual(cgks_t* h, int mesh_id, int level, const double* W_in, double* R_out, double* grad_new_out,
+                  double* alpha_out, int on_device) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    if (level < 0 || level >= M.nlev) throw ArgError("invalid level");
+    if (level == 0) {
+      require_ready(M, true);
+      LevelDev& L = M.lev[0];
+      // alpha of the state is the previous DF; write the new one to a scratch row
+      double* anew = L.D;  // D is rebuilt before every sweep, so it can hold the new DF here
+      if (M.dim == 2) fine_residual<2>(h, M, false, false, true, false, anew, M.gradnew);
+      else fine_residual<3>(h, M, false, false, true, false, anew, M.gradnew);
+      CK(cudaGetLastError());
+      if (R_out) store_rows(h, M, L, M.nv, L.R, on_device, R_out);
+      if (grad_new_out) store_rows(h, M, L, M.nv * M.dim, M.gradnew, on_device, grad_new_out);
+      if (alpha_out) store_rows(h, M, L, 1, anew, on_device, alpha_out);
+      return CGKS_OK;
+    }
+    require_ready(M, false);
+    if (!W_in || grad_new_out || alpha_out) throw ArgError("coarse residual takes W_in and returns R only");
+    if (M.winf_h.empty()) throw StateError("cgks_set_freestream has not been called for this mesh");
+    LevelDev& L = M.lev[level];
+    load_rows(h, M, L, M.nv, W_in, on_device, L.W0);
+    const PhysParams p = phys(h->cfg, M.dim);
+    // R(W) of the level's faces: reuse the forcing kernel with R* = 0, then negate
+    CK(cudaMemsetAsync(L.Rstar, 0, (size_t)L.n * M.nv * sizeof(double), h->stream));
+    if (M.dim == 2) k_coarse_prep<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, nullptr, L.alpha, M.winf, h->cfg.gamma, p.K, h->cfg.cfl_exp, h->cfg.cfl_imp, L.Rstar, nullptr);
+    else k_coarse_prep<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, nullptr, L.alpha, M.winf, h->cfg.gamma, p.K, h->cfg.cfl_exp, h->cfg.cfl_imp, L.Rstar, nullptr);
+    CK(cudaGetLastError());
+    if (R_out) store_rows(h, M, L, M.nv, L.Rstar, on_device, R_out);
+    return CGKS_OK;
+  });
+}
+
+int cgks_reconstruct(cgks_t* h, int mesh_id, double* coef_out, double* dt_exp_out, double* dt_imp_out,
+                     int on_device) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    LevelDev& L = M.lev[0];
+    if (M.dim == 2) launch_recon<2>(h, M);
+    else launch_recon<3>(h, M);
+    CK(cudaGetLastError());
+    const int nc = M.dim == 2 ? 6 : 10;
+    if (coef_out) store_rows(h, M, L, M.nv * nc, M.coef, on_device, coef_out);
+    if (dt_exp_out) store_rows(h, M, L, 1, L.dte, on_device, dt_exp_out);
+    if (dt_imp_out) store_rows(h, M, L, 1, L.dti, on_device, dt_imp_out);
+    return CGKS_OK;
+  });
+}
+
+int cgks_lusgs(cgks_t* h, int mesh_id, int level, int mode, double* W_inout, const double* rhs,
+               const double* alpha, const double* dt_exp, const double* dt_imp, double* dW_out, int on_device) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, false);
+    if (level < 0 || level >= M.nlev || !W_inout || !rhs || !alpha || !dt_exp || !dt_imp ||
+        (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED))
+      throw ArgError("invalid LU-SGS arguments");
+    if (M.winf_h.empty()) throw StateError("cgks_set_freestream has not been called for this mesh");
+    LevelDev& L = M.lev[level];
+    const int nv = M.nv;
+    const size_t wb = (size_t)L.n * nv * sizeof(double);
+    // the level's buffers are used; the fine state (W, alpha) is saved and restored
+    if (level == 0) {
+      CK(cudaMemcpyAsync(L.W0, L.W, wb, cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(L.Rstar, L.alpha, L.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    load_rows(h, M, L, nv, W_inout, on_device, L.W);
+    load_rows(h, M, L, nv, rhs, on_device, L.R);
+    load_rows(h, M, L, 1, alpha, on_device, L.alpha);
+    load_rows(h, M, L, 1, dt_exp, on_device, L.dte);
+    load_rows(h, M, L, 1, dt_imp, on_device, L.dti);
+    k_scale<<<blocks_for((int64_t)L.n * nv), kBlock, 0, h->stream>>>((int64_t)L.n * nv, -1.0, L.R);  // kernels take R = -rhs
+    if (M.dim == 2) {
+      k_diag<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W, L.alpha, L.dte, L.dti, M.winf, h->cfg.gamma, L.D);
+      if (mode == CGKS_MIXED) sweeps<2, float>(h, M, L, nullptr);
+      else sweeps<2, double>(h, M, L, nullptr);
+    } else {
+      k_diag<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W, L.alpha, L.dte, L.dti, M.winf, h->cfg.gamma, L.D);
+      if (mode == CGKS_MIXED) sweeps<3, float>(h, M, L, nullptr);
+      else sweeps<3, double>(h, M, L, nullptr);
+    }
+    CK(cudaGetLastError());
+    store_rows(h, M, L, nv, L.W, on_device, W_inout);
+    if (dW_out) {
+      const double* src = L.dW64;
+      if (mode == CGKS_MIXED) {
+        k_f2d<<<blocks_for((int64_t)L.n * nv), kBlock, 0, h->stream>>>((int64_t)L.n * nv, L.dW32, L.P);
+        src = L.P;
+      }
+      store_rows(h, M, L, nv, src, on_device, dW_out);
+    }
+    if (level == 0) {
+      CK(cudaMemcpyAsync(L.W, L.W0, wb, cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(L.alpha, L.Rstar, L.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return CGKS_OK;
+  });
+}
+
+int cgks_smooth(cgks_t* h, int mesh_id, int level, int n_sweeps) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    if (level != 0 || n_sweeps < 0) throw ArgError("only fine-level smoothing is exposed");
+    for (int s = 0; s < n_sweeps; ++s) {
+      if (M.dim == 2) {
+        fine_residual<2>(h, M, true, true, true, false, nullptr, nullptr);
+        sweeps<2, double>(h, M, M.lev[0], nullptr);
+      } else {
+        fine_residual<3>(h, M, true, true, true, false, nullptr, nullptr);
+        sweeps<3, double>(h, M, M.lev[0], nullptr);
+      }
+    }
+    CK(cudaGetLastError());
+    return CGKS_OK;
+  });
+}
+
+int cgks_vcycle(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int mode, double* norms_out,
+                int* cycles_done) {
+  return guarded(h, [&]() -> int {
+    if (!mesh_ids || n_meshes < 1 || n_cycles < 0 || (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED))
+      throw ArgError("invalid V-cycle arguments");
+    int status = CGKS_OK;
+    for (int k = 0; k < n_meshes; ++k) {
+      MeshDev& M = get_mesh(h, mesh_ids[k]);
+      require_ready(M, true);
+      const int nv = M.nv;
+      cudaGraphExec_t g = get_graph(h, M, mode);
+      int start = 0;
+      CK(cudaMemcpyAsync(&start, M.cycle, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      std::vector<double> hist;
+      int done = 0;
+      double ref = -1.0;
+      bool stop = false;
+      while (done < n_cycles && !stop) {
+        const int chunk = std::min(h->cfg.check_every, n_cycles - done);
+        for (int i = 0; i < chunk; ++i) CK(cudaGraphLaunch(g, h->stream));
+        done += chunk;
+        const int upto = std::min(start + done, M.max_hist);
+        hist.resize((size_t)upto * 2 * nv);
+        CK(cudaMemcpyAsync(hist.data(), M.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (upto > 0) {
+          const double first = hist[0];
+          const double last = hist[(size_t)(upto - 1) * 2 * nv];
+          ref = first;
+          if (!std::isfinite(last) || (first > 0 && last > h->cfg.diverge_factor * first)) {
+            status = CGKS_ERR_DIVERGED;
+            stop = true;
+          } else if (first > 0 && last <= h->cfg.tol * first) {
+            stop = true;
+          }
+        }
+      }
+      (void)ref;
+      Counters c{};
+      CK(cudaMemcpy(&c, M.cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
+      if (c.nonfinite > 0) status = CGKS_ERR_DIVERGED;
+      if (norms_out) {
+        for (int i = 0; i < n_cycles; ++i)
+          for (int j = 0; j < 2 * nv; ++j) {
+            const int idx = start + i;
+            norms_out[((size_t)k * n_cycles + i) * 2 * nv + j] =
+                (i < done && idx < M.max_hist) ? hist[(size_t)idx * 2 * nv + j] : -1.0;
+          }
+      }
+      if (cycles_done) cycles_done[k] = done;
+    }
+    if (status != CGKS_OK) h->err = "residual diverged or became non-finite";
+    return status;
+  });
+}
+
+int cgks_residual_norms(cgks_t* h, int mesh_id, int level, double* out) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    if (level != 0 || !out) throw ArgError("fine-level norms only");
+    CK(cudaMemcpyAsync(out, M.last_norm, 2 * M.nv * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return CGKS_OK;
+  });
+}
+
+int cgks_counters(cgks_t* h, int mesh_id, uint64_t* out) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, false);
+    if (!out) throw ArgError("null output");
+    Counters c{};
+    CK(cudaMemcpyAsync(&c, M.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out[0] = c.recon_fallback;
+    out[1] = c.update_halved;
+    out[2] = c.update_zeroed;
+    out[3] = c.nonfinite;
+    return CGKS_OK;
+  });
+}
+
+int cgks_gks_points(cgks_t* h, int dim, int64_t n, const double* Wl, const double* Gl, const double* Wr,
+                    const double* Gr, const double* dt, double* F, double* Wt, double* alpha) {
+  return guarded(h, [&]() -> int {
+    if ((dim != 2 && dim != 3) || n < 0 || n >= (1ll << 31) || !Wl || !Gl || !Wr || !Gr || !dt || !F || !Wt || !alpha)
+      throw ArgError("invalid point-flux arguments");
+    if (n == 0) return CGKS_OK;
+    const PhysParams p = phys(h->cfg, dim);
+    if (dim == 2) k_gks_points<2><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p, Wl, Gl, Wr, Gr, dt, F, Wt, alpha);
+    else k_gks_points<3><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p, Wl, Gl, Wr, Gr, dt, F, Wt, alpha);
+    CK(cudaGetLastError());
+    return CGKS_OK;
+  });
+}
+
+int cgks_kfvs_points(cgks_t* h, int dim, int64_t n, const double* Wl, const double* Wr, double* F) {
+  return guarded(h, [&]() -> int {
+    if ((dim != 2 && dim != 3) || n < 0 || n >= (1ll << 31) || !Wl || !Wr || !F) throw ArgError("invalid KFVS arguments");
+    if (n == 0) return CGKS_OK;
+    const PhysParams p = phys(h->cfg, dim);
+    if (dim == 2) k_kfvs_points<2><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p.K, Wl, Wr, F);
+    else k_kfvs_points<3><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p.K, Wl, Wr, F);
+    CK(cudaGetLastError());
+    return CGKS_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,920 @@
+// CUDA kernels of one GMG-CGKS V-cycle (sm_103a).
+//
+// Layout: cells are renumbered colour-major on the host, so every LU-SGS
+// colour is a contiguous range [lo, hi) and "neighbour j has a lower colour"
+// is simply j < lo.  Per-cell state W, slopes G and polynomial coefficients
+// are cell-major (a cell's values contiguous) because they are gathered by
+// neighbours and faces; per-cell geometry that only its own thread reads
+// (reconstruction operator, moments) is variable-major so warps read it
+// coalesced.  Every face flux is evaluated once, by ngp adjacent lanes (one
+// per Gauss point) whose results are combined with warp shuffles; cells then
+// gather their faces in a fixed order, so residual sums are deterministic and
+// need no atomics.
+#pragma once
+#include <cstdint>
+
+#include "physics.cuh"
+
+namespace cgks {
+
+constexpr int kBlock = 256;
+
+template <int DIM>
+struct Dims {
+  static constexpr int NV = DIM + 2;
+  static constexpr int NFC = DIM + 1;           // faces per simplex
+  static constexpr int NGP = DIM == 2 ? 2 : 3;  // Gauss points per face
+  static constexpr int NK = DIM == 2 ? 5 : 9;   // quadratic basis size
+  static constexpr int NC = NK + 1;             // polynomial coefficients
+  static constexpr int NQ = DIM == 2 ? 3 : 6;   // quadratic monomials
+  static constexpr int NCOL = NFC + NFC * DIM;  // operator columns
+};
+
+// Fine-level mesh on the device (colour-major cell ids)
+struct DevFine {
+  int n, nf;
+  const int* fL;
+  const int* fR;
+  const int* ftag;
+  const double* fn;   // [nf][dim]
+  const double* fS;   // [nf]
+  const double* XL;   // [nf][ngp][dim]
+  const double* XR;
+  const int* cface;          // [n][nfc]
+  const signed char* cside;  // [n][nfc]
+  const int* cnbr;           // [n][nfc]
+  const double* op;          // [nk*ncol][n]  variable-major
+  const unsigned char* op_ok;
+  const double* avg0;   // [nk][n]
+  const double* gg;     // [nfc*dim][n]
+  const double* m2;     // [dim*dim][n]
+  const double* vol;    // [n]
+  const double* bsc;    // [n] |Omega|^(2/dim)
+};
+
+// Cell -> face entries for the sweeps and cell-based coarse fluxes (CSR).
+struct Topo {
+  int n;
+  const int* off;            // [n+1]
+  const int* nbr;            // neighbour id or -1
+  const int* tag;            // boundary tag (0 interior)
+  const signed char* side;   // +1 if the cell is the face's left cell
+  const double* S;           // face measure
+  const double* nrm;         // [e][dim] outward unit normal from the cell
+  const double* vol;         // [n]
+};
+
+struct Counters {
+  unsigned long long recon_fallback;
+  unsigned long long update_halved;
+  unsigned long long update_zeroed;
+  unsigned long long nonfinite;
+};
+
+// ---------------------------------------------------------------------------
+// K1: reconstruction (Sec 3) + local time steps, one thread per cell
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void quad_pq(int q, int& a, int& b) {
+  if constexpr (DIM == 2) {
+    a = q == 2 ? 1 : 0;
+    b = q == 0 ? 0 : 1;
+  } else {
+    const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+    a = pa[q];
+    b = pb[q];
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ double eval_poly(const double* c, const double* X) {
+  using D = Dims<DIM>;
+  double s = c[0];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) s += c[1 + d] * X[d];
+#pragma unroll
+  for (int q = 0; q < D::NQ; ++q) {
+    int a, b;
+    quad_pq<DIM>(q, a, b);
+    s += c[1 + DIM + q] * X[a] * X[b];
+  }
+  return s;
+}
+template <int DIM>
+__device__ __forceinline__ void grad_poly(const double* c, const double* X, double* g) {
+  using D = Dims<DIM>;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) g[d] = c[1 + d];
+#pragma unroll
+  for (int q = 0; q < D::NQ; ++q) {
+    int a, b;
+    quad_pq<DIM>(q, a, b);
+    g[a] += c[1 + DIM + q] * X[b];
+    g[b] += c[1 + DIM + q] * X[a];
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __restrict__ W,
+                                                  const double* __restrict__ Gr, const double* __restrict__ alpha_prev,
+                                                  const double* __restrict__ winf, double gamma, double cfl_exp,
+                                                  double cfl_imp, double gam_hi, double weps, double* __restrict__ coef,
+                                                  double* __restrict__ dte, double* __restrict__ dti,
+                                                  Counters* __restrict__ cnt) {
+  using D = Dims<DIM>;
+  constexpr int NV = D::NV, NFC = D::NFC, NK = D::NK, NC = D::NC, NCOL = D::NCOL;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= M.n) return;
+  const int n = M.n;
+  double W0[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) W0[v] = W[(size_t)c * NV + v];
+  // neighbour means and slopes (ghosts across boundary faces)
+  double Qm[NFC][NV], Dm[NFC][NV][DIM], nrm[NFC][DIM], Sf[NFC];
+  int fid[NFC];
+  signed char sd[NFC];
+#pragma unroll
+  for (int m = 0; m < NFC; ++m) {
+    const int f = M.cface[(size_t)c * NFC + m];
+    fid[m] = f;
+    sd[m] = M.cside[(size_t)c * NFC + m];
+    Sf[m] = M.fS[f];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) nrm[m][d] = sd[m] * M.fn[(size_t)f * DIM + d];
+    const int j = M.cnbr[(size_t)c * NFC + m];
+    if (j >= 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        Qm[m][v] = W[(size_t)j * NV + v];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) Dm[m][v][d] = Gr[((size_t)j * NV + v) * DIM + d];
+      }
+    } else {
+      const int tag = M.ftag[f];
+      double g0[NV][DIM];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) g0[v][d] = Gr[((size_t)c * NV + v) * DIM + d];
+      ghost_state<DIM>(tag, winf, nrm[m], W0, Qm[m]);
+      ghost_grad<DIM>(tag, winf, nrm[m], g0, Dm[m]);
+    }
+  }
+  // local time steps: dt = CFL V / sum_f S_f (|u.n| + c)
+  {
+    double ke = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) ke += W0[1 + d] * W0[1 + d];
+    const double ir = 1.0 / W0[0];
+    const double cs = sqrt(gamma * (gamma - 1.0) * (W0[NV - 1] - 0.5 * ke * ir) * ir);
+    double sum = 0.0;
+#pragma unroll
+    for (int m = 0; m < NFC; ++m) {
+      double un = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) un += W0[1 + d] * nrm[m][d];
+      sum += Sf[m] * (fabs(un * ir) + cs);
+    }
+    const double V = M.vol[c];
+    dte[c] = cfl_exp * V / sum;
+    dti[c] = cfl_imp * V / sum;
+  }
+  const bool ok = M.op_ok[c] != 0;
+  const double ap = alpha_prev[c];
+  // |Omega|^(2|l|/dim - 1) times int over Omega of (D^l p)^2 = |Omega|^(2|l|/dim) <(D^l p)^2>
+  const double b1s = M.bsc[c];
+  const double b2s = b1s * M.bsc[c];
+  double mom[DIM][DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) mom[a][b] = M.m2[(size_t)(a * DIM + b) * n + c];
+  double P[NV][NC];
+#pragma unroll 1
+  for (int v = 0; v < NV; ++v) {
+    double e[NFC];
+#pragma unroll
+    for (int m = 0; m < NFC; ++m) e[m] = Qm[m][v] - W0[v];
+    // p1: Green-Gauss in difference form, scaled by the previous DF
+    double g1[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < NFC; ++m) s += e[m] * M.gg[(size_t)(m * DIM + d) * n + c];
+      g1[d] = ap * s;
+    }
+    if (!ok) {
+      P[v][0] = W0[v];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) P[v][1 + d] = g1[d];
+#pragma unroll
+      for (int q = 0; q < D::NQ; ++q) P[v][1 + DIM + q] = 0.0;
+      continue;
+    }
+    // p2: a = Op [e; d]
+    double a[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      const double* o = M.op + (size_t)(k * NCOL) * n + c;
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < NFC; ++m) s += o[(size_t)m * n] * e[m];
+#pragma unroll
+      for (int m = 0; m < NFC; ++m)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) s += o[(size_t)(NFC + m * DIM + d) * n] * Dm[m][v][d];
+      a[k] = s;
+    }
+    double c2[NC];
+    double c0 = W0[v];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) c0 -= a[k] * M.avg0[(size_t)k * n + c];
+    c2[0] = c0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) c2[1 + k] = a[k];
+    // smoothness indicators (sum over |l| of |Omega|^(2|l|/dim - 1) int (D^l p)^2)
+    double b1 = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) b1 += g1[d] * g1[d];
+    b1 *= b1s;
+    double H[DIM][DIM];
+#pragma unroll
+    for (int q = 0; q < D::NQ; ++q) {
+      int pa, pb;
+      quad_pq<DIM>(q, pa, pb);
+      H[pa][pb] = (pa == pb ? 2.0 : 1.0) * a[DIM + q];
+      H[pb][pa] = H[pa][pb];
+    }
+    double b2 = 0.0, b2q = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      double s = a[d] * a[d];
+#pragma unroll
+      for (int x = 0; x < DIM; ++x)
+#pragma unroll
+        for (int y = 0; y < DIM; ++y) s += H[d][x] * mom[x][y] * H[d][y];
+      b2 += s;
+#pragma unroll
+      for (int x = d; x < DIM; ++x) b2q += H[d][x] * H[d][x];
+    }
+    b2 = b1s * b2 + b2s * b2q;
+    const double gl = 1.0 - gam_hi;
+    const double tz = fabs(b2 - b1);
+    double wh = gam_hi * (1.0 + tz / (b2 + weps));
+    double wl = gl * (1.0 + tz / (b1 + weps));
+    const double iw = 1.0 / (wh + wl);
+    wh *= iw;
+    wl *= iw;
+    const double fh = wh / gam_hi;
+    P[v][0] = fh * (c2[0] - gl * W0[v]) + wl * W0[v];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) P[v][1 + d] = fh * (c2[1 + d] - gl * g1[d]) + wl * g1[d];
+#pragma unroll
+    for (int q = 0; q < D::NQ; ++q) P[v][1 + DIM + q] = fh * c2[1 + DIM + q];
+  }
+  // positivity at the cell's face Gauss points (reading: first-order fallback)
+  bool bad = false;
+#pragma unroll 1
+  for (int m = 0; m < NFC && !bad; ++m) {
+    const double* X = (sd[m] > 0 ? M.XL : M.XR) + (size_t)fid[m] * D::NGP * DIM;
+#pragma unroll
+    for (int g = 0; g < D::NGP; ++g) {
+      double Wp[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Wp[v] = eval_poly<DIM>(P[v], X + g * DIM);
+      double ke = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) ke += Wp[1 + d] * Wp[1 + d];
+      const double pr = Wp[NV - 1] - 0.5 * ke / Wp[0];
+      if (!(Wp[0] > 0.0) || !(pr > 0.0)) bad = true;
+    }
+  }
+  if (bad) {
+    atomicAdd(&cnt->recon_fallback, 1ull);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      P[v][0] = W0[v];
+#pragma unroll
+      for (int k = 1; k < NC; ++k) P[v][k] = 0.0;
+    }
+  }
+  double* out = coef + (size_t)c * NV * NC;
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) out[v * NC + k] = P[v][k];
+}
+
+// ---------------------------------------------------------------------------
+// K2: gas-kinetic flux, one lane per (face, Gauss point)
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __restrict__ coef,
+                                                 const double* __restrict__ dte, const double* __restrict__ winf,
+                                                 PhysParams P, double* __restrict__ Fface, double* __restrict__ Wface,
+                                                 double* __restrict__ aface) {
+  using D = Dims<DIM>;
+  constexpr int NV = D::NV, NC = D::NC, NGP = D::NGP;
+  constexpr int FPW = 32 / NGP;  // faces per warp
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int g = lane % NGP;
+  const int f = warp * FPW + lane / NGP;
+  const bool active = lane < FPW * NGP && f < M.nf;
+  double Fs[NV], Ws[NV], af = 1.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { Fs[v] = 0.0; Ws[v] = 0.0; }
+  if (active) {
+    const int L = M.fL[f], R = M.fR[f];
+    double n[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) n[d] = M.fn[(size_t)f * DIM + d];
+    const Frame<DIM> fr = make_frame<DIM>(n);
+    double Wl[NV], gl[NV][DIM], Wr[NV], gr[NV][DIM];
+    {
+      const double* X = M.XL + ((size_t)f * NGP + g) * DIM;
+      double x[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) x[d] = X[d];
+      const double* c = coef + (size_t)L * NV * NC;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double cc[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) cc[k] = c[v * NC + k];
+        Wl[v] = eval_poly<DIM>(cc, x);
+        grad_poly<DIM>(cc, x, gl[v]);
+      }
+    }
+    double dt = dte[L];
+    if (R >= 0) {
+      const double* X = M.XR + ((size_t)f * NGP + g) * DIM;
+      double x[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) x[d] = X[d];
+      const double* c = coef + (size_t)R * NV * NC;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double cc[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) cc[k] = c[v * NC + k];
+        Wr[v] = eval_poly<DIM>(cc, x);
+        grad_poly<DIM>(cc, x, gr[v]);
+      }
+      dt = fmin(dt, dte[R]);
+    } else {
+      const int tag = M.ftag[f];
+      ghost_state<DIM>(tag, winf, n, Wl, Wr);
+      ghost_grad<DIM>(tag, winf, n, gl, gr);
+    }
+    double wl[NV], wr[NV], Gl[DIM][NV], Gr[DIM][NV], Fl[NV], Wt[NV];
+    to_local<DIM>(fr, Wl, wl);
+    to_local<DIM>(fr, Wr, wr);
+    grad_to_local<DIM>(fr, gl, Gl);
+    grad_to_local<DIM>(fr, gr, Gr);
+    gks_flux<DIM>(P, wl, Gl, wr, Gr, dt, Fl, Wt);
+    af = df_factor<DIM>(P.gamma, wl, wr);
+    double Fg[NV], Wg[NV];
+    to_global<DIM>(fr, Fl, Fg);
+    to_global<DIM>(fr, Wt, Wg);
+    const double w = M.fS[f] * (1.0 / NGP);  // equal Gauss weights on every face
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { Fs[v] = w * Fg[v]; Ws[v] = w * Wg[v]; }
+  }
+  // combine the NGP lanes of a face (group leader = lane with g == 0)
+  const int leader = lane - g;
+#pragma unroll
+  for (int k = 1; k < NGP; ++k) {
+    const int src = leader + k;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double fo = __shfl_sync(0xffffffffu, Fs[v], src < 32 ? src : lane);
+      const double wo = __shfl_sync(0xffffffffu, Ws[v], src < 32 ? src : lane);
+      if (g == 0) { Fs[v] += fo; Ws[v] += wo; }
+    }
+    const double ao = __shfl_sync(0xffffffffu, af, src < 32 ? src : lane);
+    if (g == 0) af *= ao;
+  }
+  if (active && g == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Fface[(size_t)f * NV + v] = Fs[v];
+      Wface[(size_t)f * NV + v] = Ws[v];
+    }
+    aface[f] = af;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LU-SGS diagonal with DF relaxation (Sec 4.3):
+// D_i = alpha (V/dt_imp + 1/2 sum S r) + (1 - alpha) V/dt_exp
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ double lusgs_diag(const Topo& T, int c, const double* W, const double* Wi,
+                                             const double* winf, double gamma, double alpha, double dte, double dti) {
+  constexpr int NV = DIM + 2;
+  double sr = 0.0;
+  for (int e = T.off[c]; e < T.off[c + 1]; ++e) {
+    double nn[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) nn[d] = T.nrm[(size_t)e * DIM + d];
+    const int j = T.nbr[e];
+    double Wj[NV];
+    if (j >= 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Wj[v] = W[(size_t)j * NV + v];
+    } else {
+      ghost_state<DIM>(T.tag[e], winf, nn, Wi, Wj);
+    }
+    sr += T.S[e] * spectral_radius<DIM, double>(gamma, Wi, Wj, nn);
+  }
+  const double V = T.vol[c];
+  return alpha * (V / dti + 0.5 * sr) + (1.0 - alpha) * V / dte;
+}
+
+// ---------------------------------------------------------------------------
+// K3: per-cell gather of residual, new slopes (Sec 2.4) and DF (Sec 3.3)
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const double* __restrict__ Fface,
+                                                   const double* __restrict__ Wface, const double* __restrict__ aface,
+                                                   const double* __restrict__ W, const double* __restrict__ winf,
+                                                   double gamma, const double* __restrict__ dte,
+                                                   const double* __restrict__ dti, double* __restrict__ R,
+                                                   double* __restrict__ Gout, double* __restrict__ alpha,
+                                                   double* __restrict__ Dg, double* __restrict__ gradnew_out,
+                                                   double* __restrict__ norm_part) {
+  using Dm = Dims<DIM>;
+  constexpr int NV = Dm::NV, NFC = Dm::NFC;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double rl2[NV], rmax[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { rl2[v] = 0.0; rmax[v] = 0.0; }
+  if (c < M.n) {
+    double r[NV], gn[NV][DIM], a = 1.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      r[v] = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) gn[v][d] = 0.0;
+    }
+#pragma unroll
+    for (int m = 0; m < NFC; ++m) {
+      const int f = M.cface[(size_t)c * NFC + m];
+      const double s = M.cside[(size_t)c * NFC + m];
+      double nn[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) nn[d] = s * M.fn[(size_t)f * DIM + d];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        r[v] += s * Fface[(size_t)f * NV + v];
+        const double wv = Wface[(size_t)f * NV + v];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) gn[v][d] += wv * nn[d];
+      }
+      a *= aface[f];
+    }
+    const double iV = 1.0 / M.vol[c];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      R[(size_t)c * NV + v] = r[v];
+      const double q = r[v] * iV;
+      rl2[v] = q * q;
+      rmax[v] = fabs(q);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const double g = gn[v][d] * iV;
+        if (gradnew_out) gradnew_out[((size_t)c * NV + v) * DIM + d] = g;
+        if (Gout) Gout[((size_t)c * NV + v) * DIM + d] = a * g;  // slope update with DF
+      }
+    }
+    alpha[c] = a;
+    if (Dg) {
+      double Wi[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Wi[v] = W[(size_t)c * NV + v];
+      Dg[c] = lusgs_diag<DIM>(T, c, W, Wi, winf, gamma, a, dte[c], dti[c]);
+    }
+  }
+  if (norm_part) {
+    // block reduction in a fixed order: warp shuffles then warp 0
+    __shared__ double sh[2 * NV][kBlock / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = rl2[v], mx = rmax[v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+      }
+      if (lane == 0) { sh[2 * v][wid] = s; sh[2 * v + 1][wid] = mx; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double s = 0.0, mx = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) { s += sh[2 * v][w]; mx = fmax(mx, sh[2 * v + 1][w]); }
+        norm_part[(size_t)blockIdx.x * 2 * NV + 2 * v] = s;
+        norm_part[(size_t)blockIdx.x * 2 * NV + 2 * v + 1] = mx;
+      }
+    }
+  }
+}
+
+// final norm reduction (one block, fixed order) -> out[nv][2] = RMS, max
+template <int NV>
+__global__ void k_norm_final(const double* __restrict__ part, int nblocks, int ncells, double* __restrict__ hist,
+                             int* __restrict__ cycle, int max_hist, double* __restrict__ last) {
+  __shared__ double s[2 * NV][kBlock];
+  for (int i = 0; i < 2 * NV; ++i) {
+    double acc = (i & 1) ? 0.0 : 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+      const double x = part[(size_t)b * 2 * NV + i];
+      acc = (i & 1) ? fmax(acc, x) : acc + x;
+    }
+    s[i][threadIdx.x] = acc;
+  }
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int i = 0; i < 2 * NV; ++i)
+        s[i][threadIdx.x] = (i & 1) ? fmax(s[i][threadIdx.x], s[i][threadIdx.x + st])
+                                    : s[i][threadIdx.x] + s[i][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double out[2 * NV];
+    for (int v = 0; v < NV; ++v) {
+      out[2 * v] = sqrt(s[2 * v][0] / ncells);
+      out[2 * v + 1] = s[2 * v + 1][0];
+    }
+    if (last)
+      for (int i = 0; i < 2 * NV; ++i) last[i] = out[i];
+    if (hist && cycle) {
+      const int k = *cycle;
+      if (k < max_hist)
+        for (int i = 0; i < 2 * NV; ++i) hist[(size_t)k * 2 * NV + i] = out[i];
+      *cycle = k + 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4 / K5: multi-colour LU-SGS sweeps (Eqs. gpu-forward-relaxation and
+// gpu-backward-relaxation), one launch per colour over cells [lo, hi).
+// T is the sweep precision (double, or float in the mixed mode).
+// rhs = -(R + P) with P the coarse forcing (nullptr on the fine level).
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__device__ __forceinline__ void offdiag_term(const Topo& Tp, int e, const double* W, const T* dWsrc,
+                                             const double* Wi, double gamma, T* acc) {
+  constexpr int NV = DIM + 2;
+  const int j = Tp.nbr[e];
+  T nn[DIM], Wj[NV], Wit[NV], dj[NV], dF[NV];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) nn[d] = (T)Tp.nrm[(size_t)e * DIM + d];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Wj[v] = (T)W[(size_t)j * NV + v];
+    Wit[v] = (T)Wi[v];
+    dj[v] = dWsrc[(size_t)j * NV + v];
+  }
+  const T r = spectral_radius<DIM, T>((T)gamma, Wit, Wj, nn);
+  if constexpr (sizeof(T) == 8) {
+    // plain difference of Euler fluxes in FP64
+    T F1[NV], F0[NV], Wp[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wp[v] = Wj[v] + dj[v];
+    euler_flux<DIM, T>((T)gamma, Wp, nn, F1);
+    euler_flux<DIM, T>((T)gamma, Wj, nn, F0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dF[v] = F1[v] - F0[v];
+  } else {
+    euler_flux_increment<DIM, T>((T)gamma, Wj, dj, nn, dF);
+  }
+  const T S = (T)Tp.S[e];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] += S * (dF[v] - r * dj[v]);
+}
+
+// mode 0: forward (neighbours j < lo); mode 1: backward (j >= hi);
+// mode 2: the top colour, forward then dW = dW*.
+template <int DIM, typename T, int MODE>
+__global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const double* __restrict__ W,
+                                                  const double* __restrict__ R, const double* __restrict__ Pf,
+                                                  const double* __restrict__ alpha, const double* __restrict__ Dg,
+                                                  double gamma, T* __restrict__ dWs, T* __restrict__ dW) {
+  constexpr int NV = DIM + 2;
+  const int c = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= hi) return;
+  double Wi[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Wi[v] = W[(size_t)c * NV + v];
+  T acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0;
+  const T* src = MODE == 1 ? dW : dWs;
+  for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) {
+    const int j = Tp.nbr[e];
+    if (j < 0) continue;  // ghost increments are zero
+    if (MODE == 1 ? (j < hi) : (j >= lo)) continue;
+    offdiag_term<DIM, T>(Tp, e, W, src, Wi, gamma, acc);
+  }
+  const T ha = (T)(0.5 * alpha[c]);
+  const T iD = (T)(1.0 / Dg[c]);
+  if (MODE == 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dW[(size_t)c * NV + v] = dWs[(size_t)c * NV + v] - ha * acc[v] * iD;
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double rhs = -(R[(size_t)c * NV + v] + (Pf ? Pf[(size_t)c * NV + v] : 0.0));
+      const T x = ((T)rhs - ha * acc[v]) * iD;
+      dWs[(size_t)c * NV + v] = x;
+      if (MODE == 2) dW[(size_t)c * NV + v] = x;
+    }
+  }
+}
+
+// state update with the positivity guard (reading): halve up to 10 times, else drop
+template <int DIM>
+__device__ __forceinline__ int guarded_add(double gamma, double* W, const double* dW) {
+  constexpr int NV = DIM + 2;
+  double s = 1.0;
+  for (int it = 0; it <= 10; ++it) {
+    double Wn[NV], ke = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wn[v] = W[v] + s * dW[v];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) ke += Wn[1 + d] * Wn[1 + d];
+    if (Wn[0] > 0.0 && (Wn[NV - 1] - 0.5 * ke / Wn[0]) > 0.0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) W[v] = Wn[v];
+      return it;
+    }
+    s *= 0.5;
+  }
+  return -1;
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(kBlock) k_update(int n, double gamma, double* __restrict__ W,
+                                                   const T* __restrict__ dW, Counters* __restrict__ cnt) {
+  constexpr int NV = DIM + 2;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double w[NV], d[NV];
+  bool finite = true;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    w[v] = W[(size_t)c * NV + v];
+    d[v] = (double)dW[(size_t)c * NV + v];
+    finite = finite && isfinite(d[v]);
+  }
+  if (!finite) {
+    atomicAdd(&cnt->nonfinite, 1ull);
+    return;
+  }
+  const int r = guarded_add<DIM>(gamma, w, d);
+  if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
+  if (r < 0) atomicAdd(&cnt->update_zeroed, 1ull);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) W[(size_t)c * NV + v] = w[v];
+}
+
+// ---------------------------------------------------------------------------
+// K6: coarse level: first-order KFVS residual (+ forcing), time steps and the
+// LU-SGS diagonal, one thread per cell.  Each face flux is evaluated with the
+// face's own orientation from both sides, so the two copies are identical.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void kfvs_entry(const Topo& Tp, int e, const double* W, const double* Wi,
+                                           const double* winf, double K, double* r) {
+  constexpr int NV = DIM + 2;
+  double nn[DIM], nf[DIM], Wj[NV];
+  const double sd = Tp.side[e];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) { nn[d] = Tp.nrm[(size_t)e * DIM + d]; nf[d] = sd * nn[d]; }
+  const int j = Tp.nbr[e];
+  if (j >= 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wj[v] = W[(size_t)j * NV + v];
+  } else {
+    ghost_state<DIM>(Tp.tag[e], winf, nn, Wi, Wj);
+  }
+  const double* WL = sd > 0 ? Wi : Wj;
+  const double* WR = sd > 0 ? Wj : Wi;
+  const Frame<DIM> fr = make_frame<DIM>(nf);
+  double wl[NV], wr[NV], Fl[NV], Fg[NV];
+  to_local<DIM>(fr, WL, wl);
+  to_local<DIM>(fr, WR, wr);
+  kfvs_flux<DIM>(K, wl, wr, Fl);
+  to_global<DIM>(fr, Fl, Fg);
+  const double S = Tp.S[e] * sd;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) r[v] += S * Fg[v];
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_coarse_prep(Topo Tp, const double* __restrict__ W,
+                                                        const double* __restrict__ Pf, const double* __restrict__ alpha,
+                                                        const double* __restrict__ winf, double gamma, double K,
+                                                        double cfl_exp, double cfl_imp, double* __restrict__ Rt,
+                                                        double* __restrict__ Dg) {
+  constexpr int NV = DIM + 2;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Tp.n) return;
+  double Wi[NV], r[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { Wi[v] = W[(size_t)c * NV + v]; r[v] = 0.0; }
+  double ke = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) ke += Wi[1 + d] * Wi[1 + d];
+  const double ir = 1.0 / Wi[0];
+  const double cs = sqrt(gamma * (gamma - 1.0) * (Wi[NV - 1] - 0.5 * ke * ir) * ir);
+  double sum = 0.0;
+  for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) {
+    kfvs_entry<DIM>(Tp, e, W, Wi, winf, K, r);
+    double un = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) un += Wi[1 + d] * Tp.nrm[(size_t)e * DIM + d];
+    sum += Tp.S[e] * (fabs(un * ir) + cs);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Rt[(size_t)c * NV + v] = r[v] + (Pf ? Pf[(size_t)c * NV + v] : 0.0);
+  if (Dg) {
+    const double V = Tp.vol[c];
+    Dg[c] = lusgs_diag<DIM>(Tp, c, W, Wi, winf, gamma, alpha[c], cfl_exp * V / sum, cfl_imp * V / sum);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K7: restriction (Sec 5.2): volume-weighted state, summed residual, min DF
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int* __restrict__ ch_off,
+                                                     const int* __restrict__ ch_idx, const double* __restrict__ vol_f,
+                                                     const double* __restrict__ vol_c, const double* __restrict__ Wf,
+                                                     const double* __restrict__ af, const double* __restrict__ Rf,
+                                                     double* __restrict__ W0, double* __restrict__ Wc,
+                                                     double* __restrict__ ac, double* __restrict__ Rstar) {
+  constexpr int NV = DIM + 2;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  double w[NV], r[NV], a = 1.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { w[v] = 0.0; r[v] = 0.0; }
+  for (int k = ch_off[I]; k < ch_off[I + 1]; ++k) {
+    const int i = ch_idx[k];
+    const double V = vol_f[i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      w[v] += V * Wf[(size_t)i * NV + v];
+      r[v] += Rf[(size_t)i * NV + v];
+    }
+    a = fmin(a, af[i]);
+  }
+  const double iV = 1.0 / vol_c[I];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double x = w[v] * iV;
+    W0[(size_t)I * NV + v] = x;
+    Wc[(size_t)I * NV + v] = x;
+    Rstar[(size_t)I * NV + v] = r[v];
+  }
+  ac[I] = a;
+}
+
+// FAS forcing P = R* - R(W0) (reading: the coarse residual R(W) + P equals R*
+// at W = W0)
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_forcing(Topo Tp, const double* __restrict__ W0,
+                                                    const double* __restrict__ Rstar, const double* __restrict__ winf,
+                                                    double K, double* __restrict__ Pf) {
+  constexpr int NV = DIM + 2;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Tp.n) return;
+  double Wi[NV], r[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { Wi[v] = W0[(size_t)c * NV + v]; r[v] = 0.0; }
+  for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) kfvs_entry<DIM>(Tp, e, W0, Wi, winf, K, r);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Pf[(size_t)c * NV + v] = Rstar[(size_t)c * NV + v] - r[v];
+}
+
+// ---------------------------------------------------------------------------
+// K8: DF-limited injection prolongation (Eq. prolongation)
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_prolong(int nf, const int* __restrict__ parent,
+                                                    const double* __restrict__ af, const double* __restrict__ Wc,
+                                                    const double* __restrict__ Wc0, double gamma, double* __restrict__ Wf,
+                                                    Counters* __restrict__ cnt) {
+  constexpr int NV = DIM + 2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  const int I = parent[i];
+  double w[NV], d[NV];
+  const double a = af[i];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    w[v] = Wf[(size_t)i * NV + v];
+    d[v] = a * (Wc[(size_t)I * NV + v] - Wc0[(size_t)I * NV + v]);
+  }
+  const int r = guarded_add<DIM>(gamma, w, d);
+  if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
+  if (r < 0) atomicAdd(&cnt->update_zeroed, 1ull);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Wf[(size_t)i * NV + v] = w[v];
+}
+
+// ---------------------------------------------------------------------------
+// helpers: permutation scatter / gather of per-cell rows
+// ---------------------------------------------------------------------------
+// out[orig[c]] = in[c] (rows of width w): device colour order -> original order
+__global__ void k_scatter_rows(int n, int w, const int* __restrict__ iperm, const double* __restrict__ in,
+                               double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * w) return;
+  const int c = (int)(t / w), k = (int)(t % w);
+  out[(size_t)iperm[c] * w + k] = in[t];
+}
+// out[c] = in[orig[c]]: original order -> device colour order
+__global__ void k_gather_rows(int n, int w, const int* __restrict__ iperm, const double* __restrict__ in,
+                              double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * w) return;
+  const int c = (int)(t / w), k = (int)(t % w);
+  out[t] = in[(size_t)iperm[c] * w + k];
+}
+__global__ void k_fill(int64_t n, double v, double* __restrict__ x) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) x[t] = v;
+}
+
+
+__global__ void k_scale(int64_t n, double a, double* __restrict__ x) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) x[t] *= a;
+}
+__global__ void k_f2d(int64_t n, const float* __restrict__ x, double* __restrict__ y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = (double)x[t];
+}
+// LU-SGS diagonal from given time steps and DF factors
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_diag(Topo Tp, const double* __restrict__ W, const double* __restrict__ alpha,
+                                                 const double* __restrict__ dte, const double* __restrict__ dti,
+                                                 const double* __restrict__ winf, double gamma, double* __restrict__ Dg) {
+  constexpr int NV = DIM + 2;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Tp.n) return;
+  double Wi[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Wi[v] = W[(size_t)c * NV + v];
+  Dg[c] = lusgs_diag<DIM>(Tp, c, W, Wi, winf, gamma, alpha[c], dte[c], dti[c]);
+}
+
+// pointwise gas-kinetic flux for parity checks (local frame inputs)
+template <int DIM>
+__global__ void k_gks_points(int n, PhysParams P, const double* __restrict__ Wl, const double* __restrict__ Gl,
+                             const double* __restrict__ Wr, const double* __restrict__ Gr,
+                             const double* __restrict__ dt, double* __restrict__ F, double* __restrict__ Wt,
+                             double* __restrict__ alpha) {
+  constexpr int NV = DIM + 2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double wl[NV], wr[NV], gl[DIM][NV], gr[DIM][NV], f[NV], w[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { wl[v] = Wl[(size_t)i * NV + v]; wr[v] = Wr[(size_t)i * NV + v]; }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      gl[d][v] = Gl[((size_t)i * DIM + d) * NV + v];
+      gr[d][v] = Gr[((size_t)i * DIM + d) * NV + v];
+    }
+  gks_flux<DIM>(P, wl, gl, wr, gr, dt[i], f, w);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { F[(size_t)i * NV + v] = f[v]; Wt[(size_t)i * NV + v] = w[v]; }
+  alpha[i] = df_factor<DIM>(P.gamma, wl, wr);
+}
+
+template <int DIM>
+__global__ void k_kfvs_points(int n, double K, const double* __restrict__ Wl, const double* __restrict__ Wr,
+                              double* __restrict__ F) {
+  constexpr int NV = DIM + 2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double wl[NV], wr[NV], f[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { wl[v] = Wl[(size_t)i * NV + v]; wr[v] = Wr[(size_t)i * NV + v]; }
+  kfvs_flux<DIM>(K, wl, wr, f);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[(size_t)i * NV + v] = f[v];
+}
+
+}  // namespace cgks

@@ -1,0 +1,561 @@
+// Device physics of the compact gas-kinetic scheme: Maxwellian moments,
+// the time-accurate gas-kinetic interface flux and point value, the KFVS
+// flux, the Euler flux and its increments, local frames and boundary ghosts.
+//
+// Paper (arXiv 2509.06347) references:
+//   Sec 2.1  BGK model, Maxwellian, K internal degrees of freedom
+//   Sec 2.3  Eqs. integral1, flux-3d-1, flux-3d-2, dis1, equli,
+//            compatibility2, dis2, co, co-moment (gas-kinetic solver)
+//   Sec 2.4  point value W(x, t^{n+1}) from the same distribution
+//   Sec 3.3  discontinuity feedback factor
+//   Sec 4.2  Euler flux T(W).n used by the LU-SGS flux splitting
+//   Sec 5.2  first-order KFVS flux on the coarse levels
+// Readings (the paper defers them): numerical collision time
+// tau = C1 dt + C2 |pl - pr| / (pl + pr) dt; interface-equilibrium slopes are
+// the mean of both sides; KFVS = collisionless split of constant states;
+// slip wall = mirror ghost; supersonic far field = free stream on inflow faces,
+// interior copy on outflow faces.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace cgks {
+
+struct PhysParams {
+  double gamma;   // ratio of specific heats
+  double K;       // internal degrees of freedom
+  double c1, c2;  // collision-time coefficients
+};
+
+// Moments of a (half-)Maxwellian normalised by density: mu[n] = <u^n> in the
+// normal direction over the chosen half line (or full line), mv/mw over the
+// tangential lines, xi2/xi4 the internal-energy moments.
+template <int DIM>
+struct Mom {
+  double mu[7];
+  double mv[6];
+  double mw[6];
+  double xi2, xi4;
+};
+
+// primitive: rho, U[DIM], lambda = rho / (2 p)
+template <int DIM>
+struct Prim {
+  double rho, lam;
+  double U[DIM];
+};
+
+template <int DIM>
+__device__ __forceinline__ Prim<DIM> to_prim(const double* W, double K) {
+  Prim<DIM> p;
+  p.rho = W[0];
+  const double ir = 1.0 / W[0];
+  double ke = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    p.U[d] = W[1 + d] * ir;
+    ke += p.U[d] * W[1 + d];
+  }
+  // E - rho|U|^2/2 = (K + DIM) rho / (4 lambda)
+  p.lam = 0.25 * (K + DIM) * W[0] / (W[DIM + 1] - 0.5 * ke);
+  return p;
+}
+
+// tangential and internal-energy moments (shared by full and half spaces)
+template <int DIM>
+__device__ __forceinline__ void tang_moments(const Prim<DIM>& p, double K, Mom<DIM>& m) {
+  const double h = 0.5 / p.lam;
+  const double V = DIM > 1 ? p.U[1 % DIM] : 0.0;
+  m.mv[0] = 1.0;
+  m.mv[1] = V;
+#pragma unroll
+  for (int n = 0; n < 4; ++n) m.mv[n + 2] = V * m.mv[n + 1] + (n + 1) * h * m.mv[n];
+  if constexpr (DIM == 3) {
+    const double Wv = p.U[DIM - 1];
+    m.mw[0] = 1.0;
+    m.mw[1] = Wv;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) m.mw[n + 2] = Wv * m.mw[n + 1] + (n + 1) * h * m.mw[n];
+  } else {
+#pragma unroll
+    for (int n = 0; n < 6; ++n) m.mw[n] = n == 0 ? 1.0 : 0.0;
+  }
+  m.xi2 = K * h;
+  m.xi4 = (K * K + 2.0 * K) * h * h;
+}
+
+// normal moments: half = 0 full line, +1 u > 0, -1 u < 0
+template <int DIM>
+__device__ __forceinline__ void normal_moments(const Prim<DIM>& p, int half, Mom<DIM>& m) {
+  const double U = p.U[0];
+  const double h = 0.5 / p.lam;
+  if (half == 0) {
+    m.mu[0] = 1.0;
+    m.mu[1] = U;
+  } else {
+    const double sl = sqrt(p.lam);
+    const double te = exp(-p.lam * U * U) * (0.5 * M_2_SQRTPI * 0.5) / sl;  // e^{-lam U^2} / (2 sqrt(pi lam))
+    const double hs = 0.5 * erfc(-half * sl * U);
+    m.mu[0] = hs;
+    m.mu[1] = U * hs + half * te;
+  }
+#pragma unroll
+  for (int n = 0; n < 5; ++n) m.mu[n + 2] = U * m.mu[n + 1] + (n + 1) * h * m.mu[n];
+}
+
+// G(a, b, c) = <u^a v^b w^c>
+template <int DIM, int A, int B, int C>
+__device__ __forceinline__ double G(const Mom<DIM>& m) {
+  if (DIM == 2 && C > 0) return 0.0;
+  return m.mu[A] * m.mv[B] * (DIM == 3 ? m.mw[C] : 1.0);
+}
+
+// <u^a v^b w^c psi>
+template <int DIM, int A, int B, int C>
+__device__ __forceinline__ void psi_mom(const Mom<DIM>& m, double* out) {
+  out[0] = G<DIM, A, B, C>(m);
+  out[1] = G<DIM, A + 1, B, C>(m);
+  if (DIM >= 2) out[2] = G<DIM, A, B + 1, C>(m);
+  if (DIM == 3) out[3] = G<DIM, A, B, C + 1>(m);
+  out[DIM + 1] = 0.5 * (G<DIM, A + 2, B, C>(m) + G<DIM, A, B + 2, C>(m) +
+                        (DIM == 3 ? G<DIM, A, B, C + 2>(m) : 0.0) + m.xi2 * G<DIM, A, B, C>(m));
+}
+
+// <u^a v^b w^c xi^2 psi>
+template <int DIM, int A, int B, int C>
+__device__ __forceinline__ void psi_xi_mom(const Mom<DIM>& m, double* out) {
+  out[0] = m.xi2 * G<DIM, A, B, C>(m);
+  out[1] = m.xi2 * G<DIM, A + 1, B, C>(m);
+  if (DIM >= 2) out[2] = m.xi2 * G<DIM, A, B + 1, C>(m);
+  if (DIM == 3) out[3] = m.xi2 * G<DIM, A, B, C + 1>(m);
+  out[DIM + 1] = 0.5 * (m.xi2 * (G<DIM, A + 2, B, C>(m) + G<DIM, A, B + 2, C>(m) +
+                                 (DIM == 3 ? G<DIM, A, B, C + 2>(m) : 0.0)) +
+                        m.xi4 * G<DIM, A, B, C>(m));
+}
+
+// acc += <u^a v^b w^c psi (s . psi)>
+template <int DIM, int A, int B, int C>
+__device__ __forceinline__ void add_psi_s_mom(const Mom<DIM>& m, const double* s, double scale, double* acc) {
+  constexpr int NV = DIM + 2;
+  double t[NV];
+  psi_mom<DIM, A, B, C>(m, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] += scale * s[0] * t[i];
+  psi_mom<DIM, A + 1, B, C>(m, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] += scale * s[1] * t[i];
+  psi_mom<DIM, A, B + 1, C>(m, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] += scale * s[2] * t[i];
+  if (DIM == 3) {
+    psi_mom<DIM, A, B, C + 1>(m, t);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += scale * s[3] * t[i];
+  }
+  const double h = 0.5 * scale * s[DIM + 1];
+  psi_mom<DIM, A + 2, B, C>(m, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] += h * t[i];
+  psi_mom<DIM, A, B + 2, C>(m, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] += h * t[i];
+  if (DIM == 3) {
+    psi_mom<DIM, A, B, C + 2>(m, t);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += h * t[i];
+  }
+  psi_xi_mom<DIM, A, B, C>(m, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] += h * t[i];
+}
+
+// Solve <psi (a . psi)> = b for a (b normalised by density): explicit inverse
+// of the Maxwellian moment matrix.
+template <int DIM>
+__device__ __forceinline__ void slope_solve(const Prim<DIM>& p, double K, const double* b, double* a) {
+  const double N = K + DIM;
+  double q2 = 0.0, ub = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    q2 += p.U[d] * p.U[d];
+    ub += p.U[d] * (b[1 + d] - p.U[d] * b[0]);
+  }
+  const double e = q2 + N / (2.0 * p.lam);
+  const double aE = (4.0 * p.lam * p.lam / N) * (2.0 * b[DIM + 1] - e * b[0] - 2.0 * ub);
+  double s = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    a[1 + d] = 2.0 * p.lam * (b[1 + d] - p.U[d] * b[0]) - p.U[d] * aE;
+    s += p.U[d] * a[1 + d];
+  }
+  a[DIM + 1] = aE;
+  a[0] = b[0] - s - 0.5 * aE * e;
+}
+
+// <psi (a_n u + a_t1 v + a_t2 w)> with slopes a[DIM][NV], raised by u^KU
+template <int DIM, int KU>
+__device__ __forceinline__ void au_mom(const Mom<DIM>& m, const double (*a)[DIM + 2], double scale, double* acc) {
+  add_psi_s_mom<DIM, KU + 1, 0, 0>(m, a[0], scale, acc);
+  add_psi_s_mom<DIM, KU, 1, 0>(m, a[1], scale, acc);
+  if (DIM == 3) add_psi_s_mom<DIM, KU, 0, 1>(m, a[DIM - 1], scale, acc);
+}
+
+// Gas-kinetic flux (time average over [0, dt]) and point value at t = dt in
+// the local frame (u normal).  G?[d][v] = derivative along local direction d.
+template <int DIM>
+__device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*Gl)[DIM + 2], const double* Wr,
+                         const double (*Gr)[DIM + 2], double dt, double* F, double* Wt) {
+  constexpr int NV = DIM + 2;
+  const double K = P.K;
+  const Prim<DIM> pl = to_prim<DIM>(Wl, K), pr = to_prim<DIM>(Wr, K);
+  // half-space moments for the kinetic part
+  Mom<DIM> ml, mr;
+  tang_moments<DIM>(pl, K, ml);
+  tang_moments<DIM>(pr, K, mr);
+  normal_moments<DIM>(pl, +1, ml);
+  normal_moments<DIM>(pr, -1, mr);
+  // interface equilibrium from half-space moments (Eq. compatibility2)
+  double Wc[NV], t[NV];
+  psi_mom<DIM, 0, 0, 0>(ml, Wc);
+  psi_mom<DIM, 0, 0, 0>(mr, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) Wc[i] = pl.rho * Wc[i] + pr.rho * t[i];
+  const Prim<DIM> pc = to_prim<DIM>(Wc, K);
+  Mom<DIM> mc;
+  tang_moments<DIM>(pc, K, mc);
+  normal_moments<DIM>(pc, 0, mc);
+  // spatial slopes of the three Maxwellians (Eq. co)
+  double al[DIM][NV], ar[DIM][NV], ac[DIM][NV], b[NV];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double il = 1.0 / pl.rho, irr = 1.0 / pr.rho, ic = 1.0 / pc.rho;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) b[i] = Gl[d][i] * il;
+    slope_solve<DIM>(pl, K, b, al[d]);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) b[i] = Gr[d][i] * irr;
+    slope_solve<DIM>(pr, K, b, ar[d]);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) b[i] = 0.5 * (Gl[d][i] + Gr[d][i]) * ic;
+    slope_solve<DIM>(pc, K, b, ac[d]);
+  }
+  // time slopes from <A + a.u> = 0 (full-space moments of each Maxwellian)
+  double Al[NV], Ar[NV], Ac[NV];
+  {
+    Mom<DIM> fl = ml, fr = mr;
+    normal_moments<DIM>(pl, 0, fl);
+    normal_moments<DIM>(pr, 0, fr);
+    double s[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] = 0.0;
+    au_mom<DIM, 0>(fl, al, -1.0, s);
+    slope_solve<DIM>(pl, K, s, Al);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] = 0.0;
+    au_mom<DIM, 0>(fr, ar, -1.0, s);
+    slope_solve<DIM>(pr, K, s, Ar);
+  }
+  double PAc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) PAc[i] = 0.0;
+  au_mom<DIM, 0>(mc, ac, 1.0, PAc);
+  {
+    double s[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] = -PAc[i];
+    slope_solve<DIM>(pc, K, s, Ac);
+  }
+  // collision time and time integrals
+  const double pL = 0.5 * pl.rho / pl.lam, pR = 0.5 * pr.rho / pr.lam;
+  const double tau = P.c1 * dt + P.c2 * fabs(pL - pR) / (pL + pR) * dt;
+  const double e = exp(-dt / tau);
+  const double T1 = dt - tau * (1.0 - e);
+  const double T2 = -tau * dt + 2.0 * tau * tau - tau * (dt + 2.0 * tau) * e;
+  const double T3 = 0.5 * dt * dt - tau * dt + tau * tau * (1.0 - e);
+  const double T4 = tau * (1.0 - e);
+  const double T5 = tau * tau - tau * (dt + tau) * e;
+  const double C1 = 1.0 - e, C2 = (dt + tau) * e - tau, C3 = dt - tau + tau * e;
+  // --- equilibrium part (g^c, full space)
+  double fx[NV], wx[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) { fx[i] = 0.0; wx[i] = 0.0; }
+  psi_mom<DIM, 1, 0, 0>(mc, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) fx[i] += T1 * t[i];
+  au_mom<DIM, 1>(mc, ac, T2, fx);
+  add_psi_s_mom<DIM, 1, 0, 0>(mc, Ac, T3, fx);
+  psi_mom<DIM, 0, 0, 0>(mc, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) wx[i] += C1 * t[i] + C2 * PAc[i];
+  add_psi_s_mom<DIM, 0, 0, 0>(mc, Ac, C3, wx);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) { F[i] = pc.rho * fx[i]; Wt[i] = pc.rho * wx[i]; }
+  // --- kinetic part (g^l on u > 0, g^r on u < 0)
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const Mom<DIM>& m = side == 0 ? ml : mr;
+    const double(*a)[NV] = side == 0 ? al : ar;
+    const double* Ak = side == 0 ? Al : Ar;
+    const double rho = side == 0 ? pl.rho : pr.rho;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) { fx[i] = 0.0; wx[i] = 0.0; }
+    psi_mom<DIM, 1, 0, 0>(m, t);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) fx[i] += T4 * t[i];
+    au_mom<DIM, 1>(m, a, -(tau * T4 + T5), fx);
+    add_psi_s_mom<DIM, 1, 0, 0>(m, Ak, -tau * T4, fx);
+    psi_mom<DIM, 0, 0, 0>(m, t);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) wx[i] += e * t[i];
+    au_mom<DIM, 0>(m, a, -e * (tau + dt), wx);
+    add_psi_s_mom<DIM, 0, 0, 0>(m, Ak, -e * tau, wx);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) { F[i] += rho * fx[i]; Wt[i] += rho * wx[i]; }
+  }
+  const double idt = 1.0 / dt;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) F[i] *= idt;
+}
+
+// KFVS flux of constant states, local frame
+template <int DIM>
+__device__ __forceinline__ void kfvs_flux(double K, const double* Wl, const double* Wr, double* F) {
+  constexpr int NV = DIM + 2;
+  const Prim<DIM> pl = to_prim<DIM>(Wl, K), pr = to_prim<DIM>(Wr, K);
+  Mom<DIM> ml, mr;
+  tang_moments<DIM>(pl, K, ml);
+  tang_moments<DIM>(pr, K, mr);
+  normal_moments<DIM>(pl, +1, ml);
+  normal_moments<DIM>(pr, -1, mr);
+  double a[NV], b[NV];
+  psi_mom<DIM, 1, 0, 0>(ml, a);
+  psi_mom<DIM, 1, 0, 0>(mr, b);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) F[i] = pl.rho * a[i] + pr.rho * b[i];
+}
+
+// DF point factor 1 / (1 + D^2) from local-frame states (Sec 3.3)
+template <int DIM>
+__device__ __forceinline__ double df_factor(double gamma, const double* Wl, const double* Wr) {
+  double kl = 0.0, kr = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) { kl += Wl[1 + d] * Wl[1 + d]; kr += Wr[1 + d] * Wr[1 + d]; }
+  const double pl = (gamma - 1.0) * (Wl[DIM + 1] - 0.5 * kl / Wl[0]);
+  const double pr = (gamma - 1.0) * (Wr[DIM + 1] - 0.5 * kr / Wr[0]);
+  const double il = 1.0 / (Wl[0] * sqrt(gamma * pl / Wl[0]));  // 1 / (rho c)
+  const double ir = 1.0 / (Wr[0] * sqrt(gamma * pr / Wr[0]));
+  const double dp = fabs(pl - pr);
+  double D = dp / pl + dp / pr;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double dm = Wl[1 + d] * il - Wr[1 + d] * ir;
+    D += dm * dm;
+  }
+  return 1.0 / (1.0 + D * D);
+}
+
+// ---------------------------------------------------------------------------
+// frames: rows n, t1, t2
+template <int DIM>
+struct Frame {
+  double r[DIM][DIM];
+};
+template <int DIM>
+__device__ __forceinline__ Frame<DIM> make_frame(const double* n) {
+  Frame<DIM> f;
+  if constexpr (DIM == 2) {
+    f.r[0][0] = n[0]; f.r[0][1] = n[1];
+    f.r[1][0] = -n[1]; f.r[1][1] = n[0];
+  } else {
+    int a = 0;
+    if (fabs(n[1]) < fabs(n[a])) a = 1;
+    if (fabs(n[DIM - 1]) < fabs(n[a])) a = 2;
+    double e[3] = {0.0, 0.0, 0.0};
+    e[a] = 1.0;
+    double t1[3] = {n[1] * e[2] - n[2] * e[1], n[2] * e[0] - n[0] * e[2], n[0] * e[1] - n[1] * e[0]};
+    const double il = 1.0 / sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+    for (int i = 0; i < 3; ++i) t1[i] *= il;
+    const double t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
+    for (int i = 0; i < DIM; ++i) { f.r[0][i] = n[i]; f.r[1][i] = t1[i]; f.r[DIM - 1][i] = t2[i]; }
+  }
+  return f;
+}
+template <int DIM>
+__device__ __forceinline__ void to_local(const Frame<DIM>& f, const double* W, double* Wl) {
+  Wl[0] = W[0];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) s += f.r[a][d] * W[1 + d];
+    Wl[1 + a] = s;
+  }
+  Wl[DIM + 1] = W[DIM + 1];
+}
+template <int DIM>
+__device__ __forceinline__ void to_global(const Frame<DIM>& f, const double* Wl, double* W) {
+  W[0] = Wl[0];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) s += f.r[a][d] * Wl[1 + a];
+    W[1 + d] = s;
+  }
+  W[DIM + 1] = Wl[DIM + 1];
+}
+// global gradient g[v][d] -> local derivatives Gl[a][v'] (direction a, rotated variable v')
+template <int DIM>
+__device__ __forceinline__ void grad_to_local(const Frame<DIM>& f, const double (*g)[DIM], double (*Gl)[DIM + 2]) {
+  constexpr int NV = DIM + 2;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    double dir[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) s += f.r[a][d] * g[v][d];
+      dir[v] = s;
+    }
+    to_local<DIM>(f, dir, Gl[a]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Euler flux T(W).n and its increment T(W + dW).n - T(W).n
+template <int DIM, typename T>
+__device__ __forceinline__ void euler_flux(T gamma, const T* W, const T* n, T* F) {
+  T ke = 0, un = 0;
+  const T ir = T(1) / W[0];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) { ke += W[1 + d] * W[1 + d]; un += W[1 + d] * n[d]; }
+  un *= ir;
+  const T p = (gamma - T(1)) * (W[DIM + 1] - T(0.5) * ke * ir);
+  F[0] = W[0] * un;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) F[1 + d] = W[1 + d] * un + p * n[d];
+  F[DIM + 1] = (W[DIM + 1] + p) * un;
+}
+
+// cancellation-free increment: with u' = (m + dm)/(rho + drho), du = u' - u
+// computed from (dm - u drho)/(rho + drho), every term is a product with an
+// increment, so the result carries relative (not absolute) rounding.
+template <int DIM, typename T>
+__device__ __forceinline__ void euler_flux_increment(T gamma, const T* W, const T* dW, const T* n, T* dF) {
+  const T rho = W[0], rho1 = W[0] + dW[0];
+  const T ir = T(1) / rho, ir1 = T(1) / rho1;
+  T u[DIM], du[DIM], u1[DIM];
+  T un = 0, dun = 0, u1n = 0, ke_d = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    u[d] = W[1 + d] * ir;
+    du[d] = (dW[1 + d] - u[d] * dW[0]) * ir1;
+    u1[d] = u[d] + du[d];
+    un += u[d] * n[d];
+    dun += du[d] * n[d];
+  }
+  u1n = un + dun;
+  // d(rho |u|^2 / 2) = drho |u'|^2 / 2 + rho (u + u') . du / 2
+  T u1sq = 0, sdu = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) { u1sq += u1[d] * u1[d]; sdu += (u[d] + u1[d]) * du[d]; }
+  ke_d = T(0.5) * dW[0] * u1sq + T(0.5) * rho * sdu;
+  T q2 = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) q2 += u[d] * u[d];
+  const T p = (gamma - T(1)) * (W[DIM + 1] - T(0.5) * rho * q2);
+  const T dp = (gamma - T(1)) * (dW[DIM + 1] - ke_d);
+  dF[0] = dW[0] * u1n + rho * dun;  // d(rho u_n)
+#pragma unroll
+  for (int d = 0; d < DIM; ++d)
+    dF[1 + d] = dW[0] * u1[d] * u1n + rho * (du[d] * u1n + u[d] * dun) + dp * n[d];
+  dF[DIM + 1] = (dW[DIM + 1] + dp) * u1n + (W[DIM + 1] + p) * dun;
+}
+
+// spectral radius |u.n| + c at the arithmetic mean of two states
+template <int DIM, typename T>
+__device__ __forceinline__ T spectral_radius(T gamma, const T* Wa, const T* Wb, const T* n) {
+  T m[DIM + 2];
+#pragma unroll
+  for (int i = 0; i < DIM + 2; ++i) m[i] = T(0.5) * (Wa[i] + Wb[i]);
+  T ke = 0, un = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) { ke += m[1 + d] * m[1 + d]; un += m[1 + d] * n[d]; }
+  const T ir = T(1) / m[0];
+  const T p = (gamma - T(1)) * (m[DIM + 1] - T(0.5) * ke * ir);
+  return fabs(un * ir) + sqrt(gamma * p * ir);
+}
+
+// ---------------------------------------------------------------------------
+// boundary ghosts, global frame
+enum : int { kTagWall = 1, kTagFarfield = 2 };
+
+template <int DIM>
+__device__ __forceinline__ bool inflow(const double* winf, const double* n) {
+  double un = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) un += winf[1 + d] * n[d];
+  return un < 0.0;
+}
+template <int DIM>
+__device__ __forceinline__ void ghost_state(int tag, const double* winf, const double* n, const double* W, double* Wg) {
+  constexpr int NV = DIM + 2;
+  if (tag == kTagWall) {
+    double mn = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) mn += W[1 + d] * n[d];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Wg[i] = W[i];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) Wg[1 + d] = W[1 + d] - 2.0 * mn * n[d];
+  } else if (inflow<DIM>(winf, n)) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Wg[i] = winf[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Wg[i] = W[i];
+  }
+}
+// gradient g[v][d] of the ghost field
+template <int DIM>
+__device__ __forceinline__ void ghost_grad(int tag, const double* winf, const double* n, const double (*g)[DIM],
+                                           double (*gg)[DIM]) {
+  constexpr int NV = DIM + 2;
+  if (tag == kTagWall) {
+    // scalars: (I - 2nn^T) grad;  momentum: (I - 2nn^T) (dm/dx) (I - 2nn^T)
+    double t[NV][DIM];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) s += g[v][d] * n[d];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) t[v][d] = g[v][d] - 2.0 * s * n[d];
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      double s = 0.0;
+#pragma unroll
+      for (int e = 0; e < DIM; ++e) s += n[e] * t[1 + e][d];
+#pragma unroll
+      for (int e = 0; e < DIM; ++e) t[1 + e][d] -= 2.0 * n[e] * s;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) gg[v][d] = t[v][d];
+  } else if (inflow<DIM>(winf, n)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) gg[v][d] = 0.0;
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) gg[v][d] = g[v][d];
+  }
+}
+
+}  // namespace cgks

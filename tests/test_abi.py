@@ -1,0 +1,34 @@
+"""CPU checks of the C-ABI library: it loads without a GPU and exports every
+entry point declared in include/cgks.h; the binding names match."""
+import os
+import re
+
+import pytest
+
+from paper_2509_06347_b300 import build, cgks
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    txt = open(os.path.join(ROOT, "include", "cgks.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cgks_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_binding_exports():
+    assert declared() == sorted(cgks.EXPORTS)
+
+
+def test_library_loads_and_exports_every_symbol():
+    path = build.build()
+    lib = cgks.load_library(path)
+    for name in declared():
+        assert hasattr(lib, name), name
+
+
+def test_default_config_values():
+    cfg = cgks.default_config()
+    assert cfg.gamma == 1.4 and cfg.cfl_imp == 10.0 and cfg.cfl_exp == 0.5
+    assert cfg.n_sweep_coarse == 6 and cfg.n_pre == 1 and cfg.n_post == 0
+    assert cfg.tol == 1e-10
