@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the GMG-CGKS V-cycle on one B300 (or N independent replicas).
+
+Workload: inviscid Mach-5 flow over the unit cylinder, O-mesh of 64 x 32
+coarse quads (radial ratio 1.05, outer radius 15) split into triangles and
+refined twice: 65,536 fine cells, 3-level nested hierarchy; FP64 residual and
+DF factor with FP32 LU-SGS sweeps (MIXED; --mode fp64 for the all-FP64 run).
+A step is one whole V-cycle.  The metric is fine-cell V-cycles per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 launch with torch.distributed.run; each rank solves its own copy of
+the workload (the path does not shard a single mesh), no collective on the data
+path, max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_06347_b300 import synth  # noqa: E402
+
+METRIC = "fine-cell V-cycles/s"
+UNIT = "cell-cycles/s"
+WORKLOAD = "cylinder_mach5_65536tri_3level"
+L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
+# FP64 operations per Gauss point of the gas-kinetic flux kernel (2-D): from
+# the ncu instruction counts of k_flux<2> (2 x DFMA + DADD + DMUL per launch
+# divided by the launch's Gauss points); see profiles/k_flux_cylinder65k.md.
+FLUX_FLOP_PER_GP_2D = 3406.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", action="store_true",
+                    help="only warm-up + steps, for ncu launch lists")
+    return ap.parse_args()
+
+
+def workload():
+    mesh = synth.cylinder_mesh(n_theta=64, n_r=32, ratio=1.05, n_refine=2)
+    w = synth.freestream(5.0)
+    return mesh, w, synth.uniform_state(mesh, w)
+
+
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------------
+def cpu_baseline(mesh, w, W0, budget_s: float = 25.0):
+    """The oracle as it stands, single-threaded on the host: whole V-cycles of
+    the same workload until about budget_s seconds have been spent."""
+    import oracle
+    t0 = time.perf_counter()
+    om = oracle.OracleMesh(mesh)
+    setup = time.perf_counter() - t0
+    n = len(W0)
+    cfg = oracle.cfg_vector(2, winf=w)
+    W, G, a = W0.copy(), np.zeros((n, 4, 2)), np.ones(n)
+    cycles, spent = 0, 0.0
+    while cycles == 0 or spent < budget_s * 0.5:
+        t0 = time.perf_counter()
+        out = om.vcycle(cfg, W, G, a, 1)
+        spent += time.perf_counter() - t0
+        W, G, a = out["W"], out["grad"], out["alpha"]
+        cycles += 1
+    return {"value": n * cycles / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{cycles} whole V-cycle(s) of the {n}-cell workload from the free stream "
+                      f"(FP64, single thread; mesh setup {setup:.1f} s not timed)"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle (plain FP64 C, one host thread) on the same
+    workload and metric; each step is one whole V-cycle, capped so the run
+    stays within a few minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    mesh, w, W0 = workload()
+    om = oracle.OracleMesh(mesh)
+    n = len(W0)
+    cfg = oracle.cfg_vector(2, winf=w)
+    W, G, a = W0.copy(), np.zeros((n, 4, 2)), np.ones(n)
+    t0 = time.perf_counter()
+    out = om.vcycle(cfg, W, G, a, 1)
+    per = time.perf_counter() - t0
+    W, G, a = out["W"], out["grad"], out["alpha"]
+    warm = min(args.warmup, max(0, int(30.0 / per)))
+    steps = max(1, min(args.steps, int(150.0 / per)))
+    if warm > 1:
+        out = om.vcycle(cfg, W, G, a, warm - 1)
+        W, G, a = out["W"], out["grad"], out["alpha"]
+    t0 = time.perf_counter()
+    out = om.vcycle(cfg, W, G, a, steps)
+    el = time.perf_counter() - t0
+    val = n * steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": n, "levels": 3, "mode": "fp64 (oracle)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} V-cycles after {warm} warm-up cycles "
+                                       f"(capped from --steps {args.steps} to stay within minutes)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2509_06347_b300 import build, cgks
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+    mode = cgks.MIXED if args.mode == "mixed" else cgks.PLAIN_FP64
+    mesh, w, W0 = workload()
+    n = len(W0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = cgks.Context(stream=stream.cuda_stream)
+    ctx.setup(1, mesh, w, W0)
+    info = ctx.cgks_mesh_info(1)
+    launches_per_cycle = ctx.cgks_launch_count(1, mode)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # warm-up (graph capture + replays)
+    ctx.cgks_vcycle_launch([1], max(3, args.warmup), mode)
+    barrier()
+    if args.profile_steps:
+        ctx.cgks_vcycle_launch([1], args.steps, mode)
+        barrier()
+        return
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = str(local)
+    clk = ClockSampler(uuid)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict the working set from L2 between steps (untimed)
+            ev[k][0].record(stream)
+            ctx.cgks_vcycle_launch([1], 1, mode)
+            ev[k][1].record(stream)
+    barrier()
+    clocks = clk.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = t_ms
+    if dist:
+        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * n * args.steps / (t_max * 1e-3)
+
+    # dominant kernel: gas-kinetic face fluxes, timed alone at the current state
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            ctx.cgks_run_stage(1, 0)
+            flush.fill_(float(k))
+            kev[k][0].record(stream)
+            ctx.cgks_run_stage(1, 1)
+            kev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_flux = sum(a.elapsed_time(b) for a, b in kev) / args.steps * 1e-3
+    n_gp = info[0]["faces"] * 2
+    fp64_peak = ctx.cgks_fma_probe(0) * 1e12
+    achieved = FLUX_FLOP_PER_GP_2D * n_gp / t_flux
+
+    # end to end through the public API with host buffers: state in, one
+    # V-cycle, residual norms and state out, every step
+    Wh = torch.empty((n, 4), dtype=torch.float64).pin_memory().numpy()
+    Wh[:] = W0
+    ctx.cgks_get_state(1, Wh)
+    norms = torch.empty((1, 4, 2), dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = min(args.steps, 20)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        ctx.cgks_set_state(1, Wh)
+        ctx.cgks_vcycle([1], 1, mode, norms, check=False)
+        ctx.cgks_get_state(1, Wh)
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": world * n * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * 4 * 8,
+           "d2h_bytes_per_step": n * 4 * 8 + 4 * 2 * 8}
+
+    # convergence of the timed run
+    hist = np.zeros((1, 4, 2))
+    rn = ctx.cgks_residual_norms(1, 0)
+    counters = ctx.cgks_counters(1)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(mesh, w, W0)
+    peaks = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32" if mode == cgks.MIXED else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": n, "levels": [lv["cells"] for lv in info],
+                   "colors": [lv["colors"] for lv in info], "mode": args.mode, "mach": 5.0,
+                   "cfl_imp": 10.0, "coarse_sweeps": 6, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"kernel": "k_flux<2> (gas-kinetic face flux)", "bound": "alu",
+                     "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s (FP64)",
+                     "frac": achieved / fp64_peak, "traffic": None,
+                     "peak_source": "FP64 FMA-chain probe of this library on this GPU (cgks_fma_probe)",
+                     "flop_per_gp": FLUX_FLOP_PER_GP_2D, "gauss_points": n_gp,
+                     "ms_per_launch": t_flux * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_cycle * args.steps,
+        "clocks": clocks,
+        "residual_rms_rho_last": float(rn[0, 0]),
+        "counters": {"recon_fallback": int(counters[0]), "update_halved": int(counters[1]),
+                     "update_zeroed": int(counters[2]), "nonfinite": int(counters[3])},
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -204,6 +204,26 @@ int cgks_gks_points(cgks_t* h, int dim, int64_t n, const double* Wl, const doubl
 /* First-order KFVS flux of constant states, device pointers [n][nv]. */
 int cgks_kfvs_points(cgks_t* h, int dim, int64_t n, const double* Wl, const double* Wr, double* F);
 
+/* Profiling hook: enqueues one stage of the fine residual at the current
+ * state on the library stream (no synchronisation): 0 = reconstruction and
+ * time steps, 1 = gas-kinetic face fluxes, 2 = gather.  Stage 1 needs stage 0
+ * of the same state to have run. */
+int cgks_run_stage(cgks_t* h, int mesh_id, int stage);
+
+/* Number of kernel launches in one captured V-cycle of mesh_id in `mode`
+ * (captures the graph if needed). */
+int cgks_launch_count(cgks_t* h, int mesh_id, int mode, int* count);
+
+/* Enqueues n_cycles V-cycles of each mesh (the captured graph) on the stream
+ * without synchronising or checking convergence; the per-cycle norms are
+ * recorded on the device as in cgks_vcycle. */
+int cgks_vcycle_launch(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int mode);
+
+/* Arithmetic-throughput probe: independent FMA chains on every SM (precision
+ * 0 = FP64, 1 = FP32); *tflops receives the rate measured with CUDA events.
+ * Synchronises the stream.  Used as the ALU roofline denominator. */
+int cgks_fma_probe(cgks_t* h, int precision, double* tflops);
+
 /* Waits for all work of h on its stream. */
 int cgks_synchronize(cgks_t* h);
 

@@ -26,7 +26,9 @@ EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_erro
            "cgks_upload_hierarchy", "cgks_mesh_info", "cgks_get_coloring", "cgks_set_freestream",
            "cgks_init_state", "cgks_get_state", "cgks_set_state", "cgks_residual", "cgks_reconstruct",
            "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
-           "cgks_gks_points", "cgks_kfvs_points", "cgks_synchronize"]
+           "cgks_gks_points", "cgks_kfvs_points", "cgks_run_stage", "cgks_launch_count",
+           "cgks_vcycle_launch", "cgks_fma_probe",
+           "cgks_synchronize"]
 
 
 class CgksError(RuntimeError):
@@ -77,6 +79,10 @@ def load_library(path: str = LIB_PATH):
         "cgks_counters": [P, I, P],
         "cgks_gks_points": [P, I, I64, P, P, P, P, P, P, P, P],
         "cgks_kfvs_points": [P, I, I64, P, P, P],
+        "cgks_run_stage": [P, I, I],
+        "cgks_vcycle_launch": [P, P, I, I, I],
+        "cgks_fma_probe": [P, I, P],
+        "cgks_launch_count": [P, I, I, P],
         "cgks_synchronize": [P],
     }
     for name, args in sig.items():
@@ -240,6 +246,23 @@ class Context:
 
     def cgks_kfvs_points(self, dim, Wl, Wr, F):
         self._check(self._L.cgks_kfvs_points(self.h, dim, Wl.shape[0], _ptr(Wl), _ptr(Wr), _ptr(F)))
+
+    def cgks_vcycle_launch(self, mesh_ids, n_cycles: int, mode: int = PLAIN_FP64):
+        ids = np.ascontiguousarray(mesh_ids, np.int32)
+        self._check(self._L.cgks_vcycle_launch(self.h, _ptr(ids), ids.size, n_cycles, mode))
+
+    def cgks_fma_probe(self, precision: int = 0) -> float:
+        out = C.c_double()
+        self._check(self._L.cgks_fma_probe(self.h, precision, C.byref(out)))
+        return out.value
+
+    def cgks_run_stage(self, mesh_id: int, stage: int):
+        self._check(self._L.cgks_run_stage(self.h, mesh_id, stage))
+
+    def cgks_launch_count(self, mesh_id: int, mode: int) -> int:
+        out = C.c_int()
+        self._check(self._L.cgks_launch_count(self.h, mesh_id, mode, C.byref(out)))
+        return out.value
 
     def cgks_synchronize(self):
         self._check(self._L.cgks_synchronize(self.h))

@@ -109,6 +109,7 @@ struct MeshDev {
   Counters* cnt = nullptr;
   std::vector<LevelDev> lev;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_kernels[2] = {0, 0};
   ~MeshDev() {
     for (auto& g : graph)
       if (g) cudaGraphExecDestroy(g);
@@ -425,6 +426,17 @@ cudaGraphExec_t get_graph(cgks_t* h, MeshDev& M, int mode) {
     throw;
   }
   CK(cudaStreamEndCapture(h->stream, &g));
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  int nk = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    nk += t == cudaGraphNodeTypeKernel;
+  }
+  M.graph_kernels[mode] = nk;
   cudaGraphExec_t ge;
   cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
   cudaGraphDestroy(g);
@@ -915,6 +927,85 @@ int cgks_gks_points(cgks_t* h, int dim, int64_t n, const double* Wl, const doubl
     if (dim == 2) k_gks_points<2><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p, Wl, Gl, Wr, Gr, dt, F, Wt, alpha);
     else k_gks_points<3><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p, Wl, Gl, Wr, Gr, dt, F, Wt, alpha);
     CK(cudaGetLastError());
+    return CGKS_OK;
+  });
+}
+
+int cgks_vcycle_launch(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int mode) {
+  return guarded(h, [&]() -> int {
+    if (!mesh_ids || n_meshes < 1 || n_cycles < 0 || (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED))
+      throw ArgError("invalid V-cycle arguments");
+    for (int k = 0; k < n_meshes; ++k) {
+      MeshDev& M = get_mesh(h, mesh_ids[k]);
+      require_ready(M, true);
+      cudaGraphExec_t g = get_graph(h, M, mode);
+      for (int i = 0; i < n_cycles; ++i) CK(cudaGraphLaunch(g, h->stream));
+    }
+    return CGKS_OK;
+  });
+}
+
+int cgks_fma_probe(cgks_t* h, int precision, double* tflops) {
+  return guarded(h, [&]() -> int {
+    if (!tflops || (precision != 0 && precision != 1)) throw ArgError("invalid probe arguments");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 16, threads = 256, chains = 8;
+    const int iters = precision == 0 ? 4096 : 65536;
+    DBuf out;
+    out.alloc((size_t)blocks * threads * 8);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float ms = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {  // the last of 4 runs is timed (warm clocks)
+      CK(cudaEventRecord(e0, h->stream));
+      if (precision == 0)
+        k_fma_probe<double, 8><<<blocks, threads, 0, h->stream>>>(out.as<double>(), iters, 0.999999, 1e-7);
+      else
+        k_fma_probe<float, 8><<<blocks, threads, 0, h->stream>>>(out.as<float>(), iters, 0.999999f, 1e-7f);
+      CK(cudaEventRecord(e1, h->stream));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *tflops = 2.0 * blocks * threads * (double)iters * chains / (ms * 1e-3) / 1e12;
+    return CGKS_OK;
+  });
+}
+
+int cgks_run_stage(cgks_t* h, int mesh_id, int stage) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    if (stage < 0 || stage > 2) throw ArgError("stage must be 0, 1 or 2");
+    LevelDev& L = M.lev[0];
+    if (stage == 0) {
+      if (M.dim == 2) launch_recon<2>(h, M);
+      else launch_recon<3>(h, M);
+    } else if (stage == 1) {
+      if (M.dim == 2) launch_flux<2>(h, M);
+      else launch_flux<3>(h, M);
+    } else {
+      if (M.dim == 2)
+        k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr);
+      else
+        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr);
+    }
+    CK(cudaGetLastError());
+    return CGKS_OK;
+  });
+}
+
+int cgks_launch_count(cgks_t* h, int mesh_id, int mode, int* count) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    if (!count || (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED)) throw ArgError("invalid arguments");
+    get_graph(h, M, mode);
+    *count = M.graph_kernels[mode];
     return CGKS_OK;
   });
 }

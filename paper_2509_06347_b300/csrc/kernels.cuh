@@ -878,6 +878,22 @@ __global__ void __launch_bounds__(kBlock) k_diag(Topo Tp, const double* __restri
   Dg[c] = lusgs_diag<DIM>(Tp, c, W, Wi, winf, gamma, alpha[c], dte[c], dti[c]);
 }
 
+// FMA-throughput probe: CH independent chains per thread
+template <typename T, int CH>
+__global__ void k_fma_probe(T* __restrict__ out, int iters, T a, T b) {
+  T x[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) x[c] = fma(x[c], a, b);
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) s += x[c];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // pointwise gas-kinetic flux for parity checks (local frame inputs)
 template <int DIM>
 __global__ void k_gks_points(int n, PhysParams P, const double* __restrict__ Wl, const double* __restrict__ Gl,
