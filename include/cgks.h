@@ -68,6 +68,13 @@ typedef struct cgks_config {
   int check_every;        /* V-cycles between convergence checks in cgks_vcycle (10) */
   double tol;             /* residual drop that stops cgks_vcycle (1e-10) */
   double diverge_factor;  /* residual growth over the first cycle that aborts (1e6) */
+  int fine_smoother;      /* 0: one DF-relaxed multi-colour LU-SGS step driven by the
+                             third-order residual; 1: explicit local-time-step update
+                             W -= dt_exp R / V (Eq. smo) (0) */
+  int df_relax;           /* 1: DF-weighted implicit/explicit LU-SGS (Sec 4.3); 0: fully
+                             implicit LU-SGS, DF ignored (ablation) (1) */
+  int df_prolong;         /* 1: prolongation scaled by DF (Eq. prolongation); 0: plain
+                             injection (ablation) (1) */
 } cgks_config;
 
 typedef struct cgks_ctx cgks_t;

@@ -42,7 +42,8 @@ class Config(C.Structure):
                 ("tau_c1", C.c_double), ("tau_c2", C.c_double), ("weno_gamma_high", C.c_double),
                 ("weno_eps", C.c_double), ("r_safety", C.c_double), ("n_sweep_coarse", C.c_int),
                 ("n_pre", C.c_int), ("n_post", C.c_int), ("check_every", C.c_int), ("tol", C.c_double),
-                ("diverge_factor", C.c_double)]
+                ("diverge_factor", C.c_double), ("fine_smoother", C.c_int), ("df_relax", C.c_int),
+                ("df_prolong", C.c_int)]
 
 
 _lib = None

@@ -84,6 +84,7 @@ struct LevelDev {
   int* iperm = nullptr;  // new -> original
   double* vol = nullptr;
   double *W = nullptr, *W0 = nullptr, *alpha = nullptr, *R = nullptr, *P = nullptr, *Rstar = nullptr;
+  double* ones = nullptr;  // DF = 1 everywhere (ablation switches)
   double *D = nullptr, *dte = nullptr, *dti = nullptr;
   double *dWs64 = nullptr, *dW64 = nullptr;
   float *dWs32 = nullptr, *dW32 = nullptr;
@@ -209,6 +210,7 @@ void alloc_level_state(MeshDev& M, LevelDev& L) {
   L.W = dalloc<double>(P, (size_t)L.n * nv);
   L.W0 = dalloc<double>(P, (size_t)L.n * nv);
   L.alpha = dalloc<double>(P, L.n);
+  L.ones = upload(P, std::vector<double>(L.n, 1.0));
   L.R = dalloc<double>(P, (size_t)L.n * nv);
   L.P = dalloc<double>(P, (size_t)L.n * nv);
   L.Rstar = dalloc<double>(P, (size_t)L.n * nv);
@@ -330,7 +332,7 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
   k_gather<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
       M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R,
       slopes_update ? M.G : nullptr, alpha_out_dev ? alpha_out_dev : L.alpha, want_diag ? L.D : nullptr,
-      gradnew_dev, want_norm ? M.norm_part : nullptr);
+      gradnew_dev, want_norm ? M.norm_part : nullptr, h->cfg.df_relax);
   if (want_norm)
     k_norm_final<DIM + 2><<<1, kBlock, 0, h->stream>>>(M.norm_part, M.norm_blocks, L.n, record ? M.hist : nullptr,
                                                        record ? M.cycle : nullptr, M.max_hist, M.last_norm);
@@ -338,25 +340,26 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
 
 template <int DIM, typename T>
 void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
+  const double* alpha = h->cfg.df_relax ? L.alpha : L.ones;
   T* dWs = sizeof(T) == 8 ? (T*)L.dWs64 : (T*)L.dWs32;
   T* dW = sizeof(T) == 8 ? (T*)L.dW64 : (T*)L.dW32;
   const int nc = L.n_colors;
   for (int c = 0; c < nc - 1; ++c) {
     const int lo = L.color_off[c], hi = L.color_off[c + 1];
     if (hi > lo)
-      k_sweep<DIM, T, 0><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, L.alpha, L.D,
+      k_sweep<DIM, T, 0><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
                                                                          h->cfg.gamma, dWs, dW);
   }
   {
     const int lo = L.color_off[nc - 1], hi = L.color_off[nc];
     if (hi > lo)
-      k_sweep<DIM, T, 2><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, L.alpha, L.D,
+      k_sweep<DIM, T, 2><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
                                                                          h->cfg.gamma, dWs, dW);
   }
   for (int c = nc - 2; c >= 0; --c) {
     const int lo = L.color_off[c], hi = L.color_off[c + 1];
     if (hi > lo)
-      k_sweep<DIM, T, 1><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, L.alpha, L.D,
+      k_sweep<DIM, T, 1><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
                                                                          h->cfg.gamma, dWs, dW);
   }
   k_update<DIM, T><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, h->cfg.gamma, L.W, dW, M.cnt);
@@ -365,7 +368,8 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
 template <int DIM>
 void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag) {
   const PhysParams p = phys(h->cfg, DIM);
-  k_coarse_prep<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W, Pf, L.alpha, M.winf, h->cfg.gamma, p.K,
+  k_coarse_prep<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W, Pf, h->cfg.df_relax ? L.alpha : L.ones,
+                                                                 M.winf, h->cfg.gamma, p.K,
                                                                  h->cfg.cfl_exp, h->cfg.cfl_imp, L.R,
                                                                  want_diag ? L.D : nullptr);
 }
@@ -376,8 +380,12 @@ void vcycle_body(cgks_t* h, MeshDev& M) {
   const PhysParams p = phys(h->cfg, DIM);
   // 1. residual, norms, slope update with DF, LU-SGS diagonal
   fine_residual<DIM>(h, M, true, true, true, true, nullptr, nullptr);
-  // 2. one DF-relaxed LU-SGS pre-smoothing step on -R
-  sweeps<DIM, T>(h, M, L0, nullptr);
+  // 2. pre-smoothing: one DF-relaxed LU-SGS step on -R, or the explicit update
+  if (h->cfg.fine_smoother == 1)
+    k_explicit<DIM><<<blocks_for(L0.n), kBlock, 0, h->stream>>>(L0.n, h->cfg.gamma, L0.R, L0.dte, L0.vol, L0.W,
+                                                                 M.cnt);
+  else
+    sweeps<DIM, T>(h, M, L0, nullptr);
   if (M.nlev == 1) return;
   // 3. residual at the smoothed state (no slope update); its DF is kept
   fine_residual<DIM>(h, M, false, false, false, false, nullptr, nullptr);
@@ -398,8 +406,8 @@ void vcycle_body(cgks_t* h, MeshDev& M) {
   for (int l = M.nlev - 1; l >= 1; --l) {
     LevelDev& F = M.lev[l - 1];
     LevelDev& C = M.lev[l];
-    k_prolong<DIM><<<blocks_for(F.n), kBlock, 0, h->stream>>>(F.n, F.parent, F.alpha, C.W, C.W0, h->cfg.gamma, F.W,
-                                                               M.cnt);
+    k_prolong<DIM><<<blocks_for(F.n), kBlock, 0, h->stream>>>(F.n, F.parent, h->cfg.df_prolong ? F.alpha : F.ones,
+                                                               C.W, C.W0, h->cfg.gamma, F.W, M.cnt);
   }
 }
 
@@ -521,6 +529,9 @@ int cgks_default_config(cgks_config* c) {
   c->check_every = 10;
   c->tol = 1e-10;
   c->diverge_factor = 1e6;
+  c->fine_smoother = 0;
+  c->df_relax = 1;
+  c->df_prolong = 1;
   return CGKS_OK;
 }
 
@@ -533,7 +544,8 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
   else cgks_default_config(&h->cfg);
   if (h->cfg.n_pre != 1 || h->cfg.n_post != 0 || h->cfg.n_sweep_coarse < 1 || !(h->cfg.gamma > 1.0) ||
       h->cfg.r_safety != 1.0 || !(h->cfg.weno_gamma_high > 0.0 && h->cfg.weno_gamma_high <= 1.0) ||
-      h->cfg.check_every < 1) {
+      h->cfg.check_every < 1 || (h->cfg.fine_smoother != 0 && h->cfg.fine_smoother != 1) ||
+      (h->cfg.df_relax != 0 && h->cfg.df_relax != 1) || (h->cfg.df_prolong != 0 && h->cfg.df_prolong != 1)) {
     delete h;
     return CGKS_ERR_ARG;
   }
@@ -990,9 +1002,9 @@ int cgks_run_stage(cgks_t* h, int mesh_id, int stage) {
       else launch_flux<3>(h, M);
     } else {
       if (M.dim == 2)
-        k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr);
+        k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax);
       else
-        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr);
+        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax);
     }
     CK(cudaGetLastError());
     return CGKS_OK;

@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
                                                    const double* __restrict__ dti, double* __restrict__ R,
                                                    double* __restrict__ Gout, double* __restrict__ alpha,
                                                    double* __restrict__ Dg, double* __restrict__ gradnew_out,
-                                                   double* __restrict__ norm_part) {
+                                                   double* __restrict__ norm_part, int df_relax) {
   using Dm = Dims<DIM>;
   constexpr int NV = Dm::NV, NFC = Dm::NFC;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
       double Wi[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) Wi[v] = W[(size_t)c * NV + v];
-      Dg[c] = lusgs_diag<DIM>(T, c, W, Wi, winf, gamma, a, dte[c], dti[c]);
+      Dg[c] = lusgs_diag<DIM>(T, c, W, Wi, winf, gamma, df_relax ? a : 1.0, dte[c], dti[c]);
     }
   }
   if (norm_part) {
@@ -677,6 +677,28 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, double gamma, double* 
   if (!finite) {
     atomicAdd(&cnt->nonfinite, 1ull);
     return;
+  }
+  const int r = guarded_add<DIM>(gamma, w, d);
+  if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
+  if (r < 0) atomicAdd(&cnt->update_zeroed, 1ull);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) W[(size_t)c * NV + v] = w[v];
+}
+
+// explicit local-time-step update W -= dt_exp R / V (Eq. smo, fine smoother option)
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_explicit(int n, double gamma, const double* __restrict__ R,
+                                                     const double* __restrict__ dte, const double* __restrict__ vol,
+                                                     double* __restrict__ W, Counters* __restrict__ cnt) {
+  constexpr int NV = DIM + 2;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const double s = -dte[c] / vol[c];
+  double w[NV], d[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    w[v] = W[(size_t)c * NV + v];
+    d[v] = s * R[(size_t)c * NV + v];
   }
   const int r = guarded_add<DIM>(gamma, w, d);
   if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
