@@ -85,6 +85,9 @@ struct LevelDev {
   double* vol = nullptr;
   double *W = nullptr, *W0 = nullptr, *alpha = nullptr, *R = nullptr, *P = nullptr, *Rstar = nullptr;
   double* ones = nullptr;  // DF = 1 everywhere (ablation switches)
+  FaceSet faces{};
+  double* Fc = nullptr;     // coarse face fluxes [nf][nv]
+  double* rface = nullptr;  // spectral radius per face [nf]
   double *D = nullptr, *dte = nullptr, *dti = nullptr;
   double *dWs64 = nullptr, *dW64 = nullptr;
   float *dWs32 = nullptr, *dW32 = nullptr;
@@ -138,14 +141,7 @@ MeshDev& get_mesh(cgks_t* h, int id) {
   return *it->second;
 }
 
-PhysParams phys(const cgks_config& c, int dim) {
-  PhysParams p;
-  p.gamma = c.gamma;
-  p.K = dim == 2 ? (4.0 - 2.0 * c.gamma) / (c.gamma - 1.0) : (5.0 - 3.0 * c.gamma) / (c.gamma - 1.0);
-  p.c1 = c.tau_c1;
-  p.c2 = c.tau_c2;
-  return p;
-}
+PhysParams phys(const cgks_config& c, int dim) { return make_phys(c.gamma, dim, c.tau_c1, c.tau_c2); }
 
 // ---- device structures from the host hierarchy ----------------------------
 void build_fine_device(MeshDev& M) {
@@ -189,7 +185,7 @@ void build_fine_device(MeshDev& M) {
 
 Topo make_topo(MeshDev& M, int64_t n, const std::vector<int64_t>& off, const std::vector<int64_t>& nbr,
                const std::vector<int32_t>& tag, const std::vector<int8_t>& side, const std::vector<double>& S,
-               const std::vector<double>& nrm, const double* vol_dev) {
+               const std::vector<double>& nrm, const double* vol_dev, const std::vector<int64_t>& face) {
   auto& P = M.pool;
   Topo t{};
   t.n = (int)n;
@@ -201,6 +197,7 @@ Topo make_topo(MeshDev& M, int64_t n, const std::vector<int64_t>& off, const std
   t.S = upload(P, S);
   t.nrm = upload(P, nrm);
   t.vol = vol_dev;
+  t.face = upload(P, to_i32(face));
   return t;
 }
 
@@ -236,7 +233,7 @@ void build_levels_device(MeshDev& M) {
     L.color_off.assign(F.color_off.begin(), F.color_off.end());
     L.iperm = upload(M.pool, to_i32(F.iperm));
     L.vol = const_cast<double*>(M.fine.vol);
-    std::vector<int64_t> off(F.n + 1), nbr(F.n * nfc);
+    std::vector<int64_t> off(F.n + 1), nbr(F.n * nfc), face(F.n * nfc);
     std::vector<int32_t> tag(F.n * nfc);
     std::vector<int8_t> side(F.n * nfc);
     std::vector<double> S(F.n * nfc), nrm(F.n * nfc * dim);
@@ -245,13 +242,16 @@ void build_levels_device(MeshDev& M) {
       for (int k = 0; k < nfc; ++k) {
         const int64_t e = c * nfc + k, f = F.cface[e];
         nbr[e] = F.cnbr[e];
+        face[e] = f;
         tag[e] = F.ftag[f];
         side[e] = F.cside[e];
         S[e] = F.fS[f];
         for (int d = 0; d < dim; ++d) nrm[e * dim + d] = F.cside[e] * F.fn[f * dim + d];
       }
-    L.topo = make_topo(M, F.n, off, nbr, tag, side, S, nrm, L.vol);
+    L.topo = make_topo(M, F.n, off, nbr, tag, side, S, nrm, L.vol, face);
     alloc_level_state(M, L);
+    L.faces = FaceSet{M.fine.nf, M.fine.fL, M.fine.fR, M.fine.ftag, M.fine.fn, M.fine.fS};
+    L.rface = dalloc<double>(M.pool, F.nf);
   }
   for (size_t l = 0; l < M.H.coarse.size(); ++l) {
     const CoarseLevel& C = M.H.coarse[l];
@@ -268,14 +268,19 @@ void build_levels_device(MeshDev& M) {
     for (int64_t J = 0; J < C.n; ++J)
       for (int64_t e = C.cf_off[J]; e < C.cf_off[J + 1]; ++e) {
         const int64_t f = C.cf_face[e];
+        (void)f;
         const int sd = C.cf_side[e];
         nbr[e] = sd > 0 ? C.fR[f] : C.fL[f];
         tag[e] = C.ftag[f];
         S[e] = C.fS[f];
         for (int d = 0; d < dim; ++d) nrm[e * dim + d] = sd * C.fn[f * dim + d];
       }
-    L.topo = make_topo(M, C.n, C.cf_off, nbr, tag, C.cf_side, S, nrm, L.vol);
+    L.topo = make_topo(M, C.n, C.cf_off, nbr, tag, C.cf_side, S, nrm, L.vol, C.cf_face);
     alloc_level_state(M, L);
+    L.faces = FaceSet{(int)C.nf, upload(M.pool, to_i32(C.fL)), upload(M.pool, to_i32(C.fR)), upload(M.pool, C.ftag),
+                      upload(M.pool, C.fn), upload(M.pool, C.fS)};
+    L.Fc = dalloc<double>(M.pool, (size_t)C.nf * M.nv);
+    L.rface = dalloc<double>(M.pool, C.nf);
     L.ch_off = upload(M.pool, to_i32(C.ch_off));
     L.ch_idx = upload(M.pool, to_i32(C.ch_idx));
     M.lev[l].parent = upload(M.pool, to_i32(C.parent_of_fine));
@@ -318,7 +323,7 @@ void launch_flux(cgks_t* h, MeshDev& M) {
   const int64_t warps = (M.fine.nf + FPW - 1) / FPW;
   const int64_t threads = warps * 32;
   k_flux<DIM><<<blocks_for(threads), kBlock, 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, phys(h->cfg, DIM),
-                                                               M.Fface, M.Wface, M.aface);
+                                                               M.Fface, M.Wface, M.aface, L.W, L.rface);
 }
 
 // fine residual: slopes_update -> G <- alpha * grad_new; want_diag -> LU-SGS D;
@@ -332,7 +337,7 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
   k_gather<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
       M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R,
       slopes_update ? M.G : nullptr, alpha_out_dev ? alpha_out_dev : L.alpha, want_diag ? L.D : nullptr,
-      gradnew_dev, want_norm ? M.norm_part : nullptr, h->cfg.df_relax);
+      gradnew_dev, want_norm ? M.norm_part : nullptr, h->cfg.df_relax, L.rface);
   if (want_norm)
     k_norm_final<DIM + 2><<<1, kBlock, 0, h->stream>>>(M.norm_part, M.norm_blocks, L.n, record ? M.hist : nullptr,
                                                        record ? M.cycle : nullptr, M.max_hist, M.last_norm);
@@ -348,19 +353,19 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
     const int lo = L.color_off[c], hi = L.color_off[c + 1];
     if (hi > lo)
       k_sweep<DIM, T, 0><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
-                                                                         h->cfg.gamma, dWs, dW);
+                                                                         L.rface, h->cfg.gamma, dWs, dW);
   }
   {
     const int lo = L.color_off[nc - 1], hi = L.color_off[nc];
     if (hi > lo)
       k_sweep<DIM, T, 2><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
-                                                                         h->cfg.gamma, dWs, dW);
+                                                                         L.rface, h->cfg.gamma, dWs, dW);
   }
   for (int c = nc - 2; c >= 0; --c) {
     const int lo = L.color_off[c], hi = L.color_off[c + 1];
     if (hi > lo)
       k_sweep<DIM, T, 1><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
-                                                                         h->cfg.gamma, dWs, dW);
+                                                                         L.rface, h->cfg.gamma, dWs, dW);
   }
   k_update<DIM, T><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, h->cfg.gamma, L.W, dW, M.cnt);
 }
@@ -368,10 +373,20 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
 template <int DIM>
 void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag) {
   const PhysParams p = phys(h->cfg, DIM);
-  k_coarse_prep<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W, Pf, h->cfg.df_relax ? L.alpha : L.ones,
-                                                                 M.winf, h->cfg.gamma, p.K,
-                                                                 h->cfg.cfl_exp, h->cfg.cfl_imp, L.R,
-                                                                 want_diag ? L.D : nullptr);
+  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, 128), 128, 0, h->stream>>>(L.faces, L.W, M.winf, p, L.Fc,
+                                                                         want_diag ? L.rface : nullptr);
+  k_coarse_cell<DIM><<<blocks_for(L.n, 128), 128, 0, h->stream>>>(
+      L.topo, L.W, L.Fc, L.rface, Pf, nullptr, h->cfg.df_relax ? L.alpha : L.ones, h->cfg.gamma, h->cfg.cfl_exp,
+      h->cfg.cfl_imp, L.R, want_diag ? L.D : nullptr);
+}
+
+// FAS forcing P = R* - R(W0) on a coarse level
+template <int DIM>
+void coarse_forcing(cgks_t* h, MeshDev& M, LevelDev& L) {
+  const PhysParams p = phys(h->cfg, DIM);
+  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, 128), 128, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, nullptr);
+  k_coarse_cell<DIM><<<blocks_for(L.n, 128), 128, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, L.Rstar,
+                                                                    L.alpha, h->cfg.gamma, 0.0, 0.0, L.P, nullptr);
 }
 
 template <int DIM, typename T>
@@ -395,7 +410,7 @@ void vcycle_body(cgks_t* h, MeshDev& M) {
     LevelDev& C = M.lev[l];
     k_restrict<DIM><<<blocks_for(C.n), kBlock, 0, h->stream>>>(C.n, C.ch_off, C.ch_idx, F.vol, C.vol, F.W, F.alpha,
                                                                 F.R, C.W0, C.W, C.alpha, C.Rstar);
-    k_forcing<DIM><<<blocks_for(C.n), kBlock, 0, h->stream>>>(C.topo, C.W0, C.Rstar, M.winf, p.K, C.P);
+    coarse_forcing<DIM>(h, M, C);
     for (int s = 0; s < h->cfg.n_sweep_coarse; ++s) {
       coarse_prep<DIM>(h, M, C, C.P, true);
       sweeps<DIM, T>(h, M, C, nullptr);
@@ -748,10 +763,14 @@ int cgks_residual(cgks_t* h, int mesh_id, int level, const double* W_in, double*
     LevelDev& L = M.lev[level];
     load_rows(h, M, L, M.nv, W_in, on_device, L.W0);
     const PhysParams p = phys(h->cfg, M.dim);
-    // R(W) of the level's faces: reuse the forcing kernel with R* = 0, then negate
-    CK(cudaMemsetAsync(L.Rstar, 0, (size_t)L.n * M.nv * sizeof(double), h->stream));
-    if (M.dim == 2) k_coarse_prep<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, nullptr, L.alpha, M.winf, h->cfg.gamma, p.K, h->cfg.cfl_exp, h->cfg.cfl_imp, L.Rstar, nullptr);
-    else k_coarse_prep<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, nullptr, L.alpha, M.winf, h->cfg.gamma, p.K, h->cfg.cfl_exp, h->cfg.cfl_imp, L.Rstar, nullptr);
+    // R(W) of the level's faces with zero forcing
+    if (M.dim == 2) {
+      k_face_kfvs<2><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, nullptr);
+      k_coarse_cell<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, nullptr, L.alpha, h->cfg.gamma, 0.0, 0.0, L.Rstar, nullptr);
+    } else {
+      k_face_kfvs<3><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, nullptr);
+      k_coarse_cell<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, nullptr, L.alpha, h->cfg.gamma, 0.0, 0.0, L.Rstar, nullptr);
+    }
     CK(cudaGetLastError());
     if (R_out) store_rows(h, M, L, M.nv, L.Rstar, on_device, R_out);
     return CGKS_OK;
@@ -798,12 +817,15 @@ int cgks_lusgs(cgks_t* h, int mesh_id, int level, int mode, double* W_inout, con
     load_rows(h, M, L, 1, dt_exp, on_device, L.dte);
     load_rows(h, M, L, 1, dt_imp, on_device, L.dti);
     k_scale<<<blocks_for((int64_t)L.n * nv), kBlock, 0, h->stream>>>((int64_t)L.n * nv, -1.0, L.R);  // kernels take R = -rhs
+    const PhysParams pp = phys(h->cfg, M.dim);
     if (M.dim == 2) {
-      k_diag<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W, L.alpha, L.dte, L.dti, M.winf, h->cfg.gamma, L.D);
+      k_face_kfvs<2><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.W, M.winf, pp, nullptr, L.rface);
+      k_diag<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.rface, L.alpha, L.dte, L.dti, L.D);
       if (mode == CGKS_MIXED) sweeps<2, float>(h, M, L, nullptr);
       else sweeps<2, double>(h, M, L, nullptr);
     } else {
-      k_diag<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W, L.alpha, L.dte, L.dti, M.winf, h->cfg.gamma, L.D);
+      k_face_kfvs<3><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.W, M.winf, pp, nullptr, L.rface);
+      k_diag<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.rface, L.alpha, L.dte, L.dti, L.D);
       if (mode == CGKS_MIXED) sweeps<3, float>(h, M, L, nullptr);
       else sweeps<3, double>(h, M, L, nullptr);
     }
@@ -1002,9 +1024,9 @@ int cgks_run_stage(cgks_t* h, int mesh_id, int stage) {
       else launch_flux<3>(h, M);
     } else {
       if (M.dim == 2)
-        k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax);
+        k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax, L.rface);
       else
-        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax);
+        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax, L.rface);
     }
     CK(cudaGetLastError());
     return CGKS_OK;
@@ -1027,8 +1049,8 @@ int cgks_kfvs_points(cgks_t* h, int dim, int64_t n, const double* Wl, const doub
     if ((dim != 2 && dim != 3) || n < 0 || n >= (1ll << 31) || !Wl || !Wr || !F) throw ArgError("invalid KFVS arguments");
     if (n == 0) return CGKS_OK;
     const PhysParams p = phys(h->cfg, dim);
-    if (dim == 2) k_kfvs_points<2><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p.K, Wl, Wr, F);
-    else k_kfvs_points<3><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p.K, Wl, Wr, F);
+    if (dim == 2) k_kfvs_points<2><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p, Wl, Wr, F);
+    else k_kfvs_points<3><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p, Wl, Wr, F);
     CK(cudaGetLastError());
     return CGKS_OK;
   });

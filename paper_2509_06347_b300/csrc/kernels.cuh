@@ -62,6 +62,17 @@ struct Topo {
   const double* S;           // face measure
   const double* nrm;         // [e][dim] outward unit normal from the cell
   const double* vol;         // [n]
+  const int* face;           // face index of the entry in the level's face list
+};
+
+// A level's faces (unique, L -> R orientation; R = -1 on boundary faces)
+struct FaceSet {
+  int nf;
+  const int* fL;
+  const int* fR;
+  const int* ftag;
+  const double* fn;  // [nf][dim]
+  const double* fS;  // [nf]
 };
 
 struct Counters {
@@ -313,7 +324,8 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __restrict__ coef,
                                                  const double* __restrict__ dte, const double* __restrict__ winf,
                                                  PhysParams P, double* __restrict__ Fface, double* __restrict__ Wface,
-                                                 double* __restrict__ aface) {
+                                                 double* __restrict__ aface, const double* __restrict__ Wc,
+                                                 double* __restrict__ rface) {
   using D = Dims<DIM>;
   constexpr int NV = D::NV, NC = D::NC, NGP = D::NGP;
   constexpr int FPW = 32 / NGP;  // faces per warp
@@ -403,6 +415,20 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __rest
       Wface[(size_t)f * NV + v] = Ws[v];
     }
     aface[f] = af;
+    // spectral radius of the LU-SGS splitting at the mean of the cell means
+    const int L = M.fL[f], R = M.fR[f];
+    double n[DIM], WL[NV], WR[NV];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) n[d] = M.fn[(size_t)f * DIM + d];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) WL[v] = Wc[(size_t)L * NV + v];
+    if (R >= 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) WR[v] = Wc[(size_t)R * NV + v];
+    } else {
+      ghost_state<DIM>(M.ftag[f], winf, n, WL, WR);
+    }
+    rface[f] = spectral_radius<DIM, double>(P.gamma, WL, WR, n);
   }
 }
 
@@ -411,24 +437,10 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __rest
 // D_i = alpha (V/dt_imp + 1/2 sum S r) + (1 - alpha) V/dt_exp
 // ---------------------------------------------------------------------------
 template <int DIM>
-__device__ __forceinline__ double lusgs_diag(const Topo& T, int c, const double* W, const double* Wi,
-                                             const double* winf, double gamma, double alpha, double dte, double dti) {
-  constexpr int NV = DIM + 2;
+__device__ __forceinline__ double lusgs_diag(const Topo& T, int c, const double* rface, double alpha, double dte,
+                                             double dti) {
   double sr = 0.0;
-  for (int e = T.off[c]; e < T.off[c + 1]; ++e) {
-    double nn[DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) nn[d] = T.nrm[(size_t)e * DIM + d];
-    const int j = T.nbr[e];
-    double Wj[NV];
-    if (j >= 0) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) Wj[v] = W[(size_t)j * NV + v];
-    } else {
-      ghost_state<DIM>(T.tag[e], winf, nn, Wi, Wj);
-    }
-    sr += T.S[e] * spectral_radius<DIM, double>(gamma, Wi, Wj, nn);
-  }
+  for (int e = T.off[c]; e < T.off[c + 1]; ++e) sr += T.S[e] * rface[T.face[e]];
   const double V = T.vol[c];
   return alpha * (V / dti + 0.5 * sr) + (1.0 - alpha) * V / dte;
 }
@@ -444,7 +456,8 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
                                                    const double* __restrict__ dti, double* __restrict__ R,
                                                    double* __restrict__ Gout, double* __restrict__ alpha,
                                                    double* __restrict__ Dg, double* __restrict__ gradnew_out,
-                                                   double* __restrict__ norm_part, int df_relax) {
+                                                   double* __restrict__ norm_part, int df_relax,
+                                                   const double* __restrict__ rface) {
   using Dm = Dims<DIM>;
   constexpr int NV = Dm::NV, NFC = Dm::NFC;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -490,12 +503,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
       }
     }
     alpha[c] = a;
-    if (Dg) {
-      double Wi[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) Wi[v] = W[(size_t)c * NV + v];
-      Dg[c] = lusgs_diag<DIM>(T, c, W, Wi, winf, gamma, df_relax ? a : 1.0, dte[c], dti[c]);
-    }
+    if (Dg) Dg[c] = lusgs_diag<DIM>(T, c, rface, df_relax ? a : 1.0, dte[c], dti[c]);
   }
   if (norm_part) {
     // block reduction in a fixed order: warp shuffles then warp 0
@@ -570,19 +578,18 @@ __global__ void k_norm_final(const double* __restrict__ part, int nblocks, int n
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 __device__ __forceinline__ void offdiag_term(const Topo& Tp, int e, const double* W, const T* dWsrc,
-                                             const double* Wi, double gamma, T* acc) {
+                                             const double* rface, double gamma, T* acc) {
   constexpr int NV = DIM + 2;
   const int j = Tp.nbr[e];
-  T nn[DIM], Wj[NV], Wit[NV], dj[NV], dF[NV];
+  T nn[DIM], Wj[NV], dj[NV], dF[NV];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) nn[d] = (T)Tp.nrm[(size_t)e * DIM + d];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     Wj[v] = (T)W[(size_t)j * NV + v];
-    Wit[v] = (T)Wi[v];
     dj[v] = dWsrc[(size_t)j * NV + v];
   }
-  const T r = spectral_radius<DIM, T>((T)gamma, Wit, Wj, nn);
+  const T r = (T)rface[Tp.face[e]];
   if constexpr (sizeof(T) == 8) {
     // plain difference of Euler fluxes in FP64
     T F1[NV], F0[NV], Wp[NV];
@@ -606,13 +613,11 @@ template <int DIM, typename T, int MODE>
 __global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const double* __restrict__ W,
                                                   const double* __restrict__ R, const double* __restrict__ Pf,
                                                   const double* __restrict__ alpha, const double* __restrict__ Dg,
-                                                  double gamma, T* __restrict__ dWs, T* __restrict__ dW) {
+                                                  const double* __restrict__ rface, double gamma,
+                                                  T* __restrict__ dWs, T* __restrict__ dW) {
   constexpr int NV = DIM + 2;
   const int c = lo + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= hi) return;
-  double Wi[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Wi[v] = W[(size_t)c * NV + v];
   T acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0;
@@ -621,7 +626,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const
     const int j = Tp.nbr[e];
     if (j < 0) continue;  // ghost increments are zero
     if (MODE == 1 ? (j < hi) : (j >= lo)) continue;
-    offdiag_term<DIM, T>(Tp, e, W, src, Wi, gamma, acc);
+    offdiag_term<DIM, T>(Tp, e, W, src, rface, gamma, acc);
   }
   const T ha = (T)(0.5 * alpha[c]);
   const T iD = (T)(1.0 / Dg[c]);
@@ -708,68 +713,87 @@ __global__ void __launch_bounds__(kBlock) k_explicit(int n, double gamma, const 
 }
 
 // ---------------------------------------------------------------------------
-// K6: coarse level: first-order KFVS residual (+ forcing), time steps and the
-// LU-SGS diagonal, one thread per cell.  Each face flux is evaluated with the
-// face's own orientation from both sides, so the two copies are identical.
+// K6: coarse levels: first-order KFVS face flux (S-weighted, global frame) and
+// the spectral radius of the LU-SGS splitting, once per face ...
 // ---------------------------------------------------------------------------
 template <int DIM>
-__device__ __forceinline__ void kfvs_entry(const Topo& Tp, int e, const double* W, const double* Wi,
-                                           const double* winf, double K, double* r) {
+__global__ void __launch_bounds__(kBlock) k_face_kfvs(FaceSet Fs, const double* __restrict__ W,
+                                                      const double* __restrict__ winf, PhysParams P,
+                                                      double* __restrict__ Fout, double* __restrict__ rout) {
   constexpr int NV = DIM + 2;
-  double nn[DIM], nf[DIM], Wj[NV];
-  const double sd = Tp.side[e];
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= Fs.nf) return;
+  const int L = Fs.fL[f], R = Fs.fR[f];
+  double n[DIM], WL[NV], WR[NV];
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) { nn[d] = Tp.nrm[(size_t)e * DIM + d]; nf[d] = sd * nn[d]; }
-  const int j = Tp.nbr[e];
-  if (j >= 0) {
+  for (int d = 0; d < DIM; ++d) n[d] = Fs.fn[(size_t)f * DIM + d];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Wj[v] = W[(size_t)j * NV + v];
+  for (int v = 0; v < NV; ++v) WL[v] = W[(size_t)L * NV + v];
+  if (R >= 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) WR[v] = W[(size_t)R * NV + v];
   } else {
-    ghost_state<DIM>(Tp.tag[e], winf, nn, Wi, Wj);
+    ghost_state<DIM>(Fs.ftag[f], winf, n, WL, WR);
   }
-  const double* WL = sd > 0 ? Wi : Wj;
-  const double* WR = sd > 0 ? Wj : Wi;
-  const Frame<DIM> fr = make_frame<DIM>(nf);
-  double wl[NV], wr[NV], Fl[NV], Fg[NV];
-  to_local<DIM>(fr, WL, wl);
-  to_local<DIM>(fr, WR, wr);
-  kfvs_flux<DIM>(K, wl, wr, Fl);
-  to_global<DIM>(fr, Fl, Fg);
-  const double S = Tp.S[e] * sd;
+  if (Fout) {
+    const Frame<DIM> fr = make_frame<DIM>(n);
+    double wl[NV], wr[NV], Fl[NV], Fg[NV];
+    to_local<DIM>(fr, WL, wl);
+    to_local<DIM>(fr, WR, wr);
+    kfvs_flux<DIM>(P, wl, wr, Fl);
+    to_global<DIM>(fr, Fl, Fg);
+    const double S = Fs.fS[f];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) r[v] += S * Fg[v];
+    for (int v = 0; v < NV; ++v) Fout[(size_t)f * NV + v] = S * Fg[v];
+  }
+  if (rout) rout[f] = spectral_radius<DIM, double>(P.gamma, WL, WR, n);
 }
 
+// ... then per cell: R~ = sum_f +-S F + P (or, with Rstar, the forcing
+// P = R* - R), local time steps and the DF-relaxed LU-SGS diagonal.
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_coarse_prep(Topo Tp, const double* __restrict__ W,
-                                                        const double* __restrict__ Pf, const double* __restrict__ alpha,
-                                                        const double* __restrict__ winf, double gamma, double K,
-                                                        double cfl_exp, double cfl_imp, double* __restrict__ Rt,
+__global__ void __launch_bounds__(kBlock) k_coarse_cell(Topo Tp, const double* __restrict__ W,
+                                                        const double* __restrict__ Fface,
+                                                        const double* __restrict__ rface,
+                                                        const double* __restrict__ Pf,
+                                                        const double* __restrict__ Rstar,
+                                                        const double* __restrict__ alpha, double gamma,
+                                                        double cfl_exp, double cfl_imp, double* __restrict__ out,
                                                         double* __restrict__ Dg) {
   constexpr int NV = DIM + 2;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= Tp.n) return;
-  double Wi[NV], r[NV];
+  double r[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) { Wi[v] = W[(size_t)c * NV + v]; r[v] = 0.0; }
-  double ke = 0.0;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) ke += Wi[1 + d] * Wi[1 + d];
-  const double ir = 1.0 / Wi[0];
-  const double cs = sqrt(gamma * (gamma - 1.0) * (Wi[NV - 1] - 0.5 * ke * ir) * ir);
-  double sum = 0.0;
+  for (int v = 0; v < NV; ++v) r[v] = 0.0;
   for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) {
-    kfvs_entry<DIM>(Tp, e, W, Wi, winf, K, r);
-    double un = 0.0;
+    const int f = Tp.face[e];
+    const double sd = Tp.side[e];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) un += Wi[1 + d] * Tp.nrm[(size_t)e * DIM + d];
-    sum += Tp.S[e] * (fabs(un * ir) + cs);
+    for (int v = 0; v < NV; ++v) r[v] += sd * Fface[(size_t)f * NV + v];
   }
 #pragma unroll
-  for (int v = 0; v < NV; ++v) Rt[(size_t)c * NV + v] = r[v] + (Pf ? Pf[(size_t)c * NV + v] : 0.0);
+  for (int v = 0; v < NV; ++v) {
+    if (Rstar) out[(size_t)c * NV + v] = Rstar[(size_t)c * NV + v] - r[v];
+    else out[(size_t)c * NV + v] = r[v] + (Pf ? Pf[(size_t)c * NV + v] : 0.0);
+  }
   if (Dg) {
+    double Wi[NV], ke = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wi[v] = W[(size_t)c * NV + v];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) ke += Wi[1 + d] * Wi[1 + d];
+    const double ir = 1.0 / Wi[0];
+    const double cs = sqrt(gamma * (gamma - 1.0) * (Wi[NV - 1] - 0.5 * ke * ir) * ir);
+    double sum = 0.0;
+    for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) {
+      double un = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) un += Wi[1 + d] * Tp.nrm[(size_t)e * DIM + d];
+      sum += Tp.S[e] * (fabs(un * ir) + cs);
+    }
     const double V = Tp.vol[c];
-    Dg[c] = lusgs_diag<DIM>(Tp, c, W, Wi, winf, gamma, alpha[c], cfl_exp * V / sum, cfl_imp * V / sum);
+    Dg[c] = lusgs_diag<DIM>(Tp, c, rface, alpha[c], cfl_exp * V / sum, cfl_imp * V / sum);
   }
 }
 
@@ -808,23 +832,6 @@ __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int* __restri
     Rstar[(size_t)I * NV + v] = r[v];
   }
   ac[I] = a;
-}
-
-// FAS forcing P = R* - R(W0) (reading: the coarse residual R(W) + P equals R*
-// at W = W0)
-template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_forcing(Topo Tp, const double* __restrict__ W0,
-                                                    const double* __restrict__ Rstar, const double* __restrict__ winf,
-                                                    double K, double* __restrict__ Pf) {
-  constexpr int NV = DIM + 2;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= Tp.n) return;
-  double Wi[NV], r[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) { Wi[v] = W0[(size_t)c * NV + v]; r[v] = 0.0; }
-  for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) kfvs_entry<DIM>(Tp, e, W0, Wi, winf, K, r);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Pf[(size_t)c * NV + v] = Rstar[(size_t)c * NV + v] - r[v];
 }
 
 // ---------------------------------------------------------------------------
@@ -888,16 +895,12 @@ __global__ void k_f2d(int64_t n, const float* __restrict__ x, double* __restrict
 }
 // LU-SGS diagonal from given time steps and DF factors
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_diag(Topo Tp, const double* __restrict__ W, const double* __restrict__ alpha,
-                                                 const double* __restrict__ dte, const double* __restrict__ dti,
-                                                 const double* __restrict__ winf, double gamma, double* __restrict__ Dg) {
-  constexpr int NV = DIM + 2;
+__global__ void __launch_bounds__(kBlock) k_diag(Topo Tp, const double* __restrict__ rface,
+                                                 const double* __restrict__ alpha, const double* __restrict__ dte,
+                                                 const double* __restrict__ dti, double* __restrict__ Dg) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= Tp.n) return;
-  double Wi[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Wi[v] = W[(size_t)c * NV + v];
-  Dg[c] = lusgs_diag<DIM>(Tp, c, W, Wi, winf, gamma, alpha[c], dte[c], dti[c]);
+  Dg[c] = lusgs_diag<DIM>(Tp, c, rface, alpha[c], dte[c], dti[c]);
 }
 
 // FMA-throughput probe: CH independent chains per thread
@@ -942,7 +945,7 @@ __global__ void k_gks_points(int n, PhysParams P, const double* __restrict__ Wl,
 }
 
 template <int DIM>
-__global__ void k_kfvs_points(int n, double K, const double* __restrict__ Wl, const double* __restrict__ Wr,
+__global__ void k_kfvs_points(int n, PhysParams P, const double* __restrict__ Wl, const double* __restrict__ Wr,
                               double* __restrict__ F) {
   constexpr int NV = DIM + 2;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -950,7 +953,7 @@ __global__ void k_kfvs_points(int n, double K, const double* __restrict__ Wl, co
   double wl[NV], wr[NV], f[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) { wl[v] = Wl[(size_t)i * NV + v]; wr[v] = Wr[(size_t)i * NV + v]; }
-  kfvs_flux<DIM>(K, wl, wr, f);
+  kfvs_flux<DIM>(P, wl, wr, f);
 #pragma unroll
   for (int v = 0; v < NV; ++v) F[(size_t)i * NV + v] = f[v];
 }

@@ -25,7 +25,21 @@ struct PhysParams {
   double gamma;   // ratio of specific heats
   double K;       // internal degrees of freedom
   double c1, c2;  // collision-time coefficients
+  // derived on the host: N = K + dim, 2/N, 4/N
+  double N, twoOverN, fourOverN;
 };
+
+inline PhysParams make_phys(double gamma, int dim, double c1, double c2) {
+  PhysParams p;
+  p.gamma = gamma;
+  p.K = dim == 2 ? (4.0 - 2.0 * gamma) / (gamma - 1.0) : (5.0 - 3.0 * gamma) / (gamma - 1.0);
+  p.c1 = c1;
+  p.c2 = c2;
+  p.N = p.K + dim;
+  p.twoOverN = 2.0 / p.N;
+  p.fourOverN = 4.0 / p.N;
+  return p;
+}
 
 // Moments of a (half-)Maxwellian normalised by density: mu[n] = <u^n> in the
 // normal direction over the chosen half line (or full line), mv/mw over the
@@ -41,30 +55,31 @@ struct Mom {
 // primitive: rho, U[DIM], lambda = rho / (2 p)
 template <int DIM>
 struct Prim {
-  double rho, lam;
+  double rho, irho, lam, h;  // h = 1 / (2 lambda)
   double U[DIM];
 };
 
 template <int DIM>
-__device__ __forceinline__ Prim<DIM> to_prim(const double* W, double K) {
+__device__ __forceinline__ Prim<DIM> to_prim(const double* W, const PhysParams& P) {
   Prim<DIM> p;
   p.rho = W[0];
-  const double ir = 1.0 / W[0];
+  p.irho = 1.0 / W[0];
   double ke = 0.0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    p.U[d] = W[1 + d] * ir;
+    p.U[d] = W[1 + d] * p.irho;
     ke += p.U[d] * W[1 + d];
   }
-  // E - rho|U|^2/2 = (K + DIM) rho / (4 lambda)
-  p.lam = 0.25 * (K + DIM) * W[0] / (W[DIM + 1] - 0.5 * ke);
+  // E - rho|U|^2/2 = (K + DIM) rho / (4 lambda) = (K + DIM) rho h / 2
+  p.h = (W[DIM + 1] - 0.5 * ke) * p.irho * P.twoOverN;
+  p.lam = 0.5 / p.h;
   return p;
 }
 
 // tangential and internal-energy moments (shared by full and half spaces)
 template <int DIM>
 __device__ __forceinline__ void tang_moments(const Prim<DIM>& p, double K, Mom<DIM>& m) {
-  const double h = 0.5 / p.lam;
+  const double h = p.h;
   const double V = DIM > 1 ? p.U[1 % DIM] : 0.0;
   m.mv[0] = 1.0;
   m.mv[1] = V;
@@ -88,13 +103,13 @@ __device__ __forceinline__ void tang_moments(const Prim<DIM>& p, double K, Mom<D
 template <int DIM>
 __device__ __forceinline__ void normal_moments(const Prim<DIM>& p, int half, Mom<DIM>& m) {
   const double U = p.U[0];
-  const double h = 0.5 / p.lam;
+  const double h = p.h;
   if (half == 0) {
     m.mu[0] = 1.0;
     m.mu[1] = U;
   } else {
     const double sl = sqrt(p.lam);
-    const double te = exp(-p.lam * U * U) * (0.5 * M_2_SQRTPI * 0.5) / sl;  // e^{-lam U^2} / (2 sqrt(pi lam))
+    const double te = exp(-p.lam * U * U) * (0.5 * M_2_SQRTPI) * (sl * h);  // e^{-lam U^2} / (2 sqrt(pi lam))
     const double hs = 0.5 * erfc(-half * sl * U);
     m.mu[0] = hs;
     m.mu[1] = U * hs + half * te;
@@ -172,16 +187,15 @@ __device__ __forceinline__ void add_psi_s_mom(const Mom<DIM>& m, const double* s
 // Solve <psi (a . psi)> = b for a (b normalised by density): explicit inverse
 // of the Maxwellian moment matrix.
 template <int DIM>
-__device__ __forceinline__ void slope_solve(const Prim<DIM>& p, double K, const double* b, double* a) {
-  const double N = K + DIM;
+__device__ __forceinline__ void slope_solve(const Prim<DIM>& p, const PhysParams& P, const double* b, double* a) {
   double q2 = 0.0, ub = 0.0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     q2 += p.U[d] * p.U[d];
     ub += p.U[d] * (b[1 + d] - p.U[d] * b[0]);
   }
-  const double e = q2 + N / (2.0 * p.lam);
-  const double aE = (4.0 * p.lam * p.lam / N) * (2.0 * b[DIM + 1] - e * b[0] - 2.0 * ub);
+  const double e = q2 + P.N * p.h;
+  const double aE = (P.fourOverN * p.lam * p.lam) * (2.0 * b[DIM + 1] - e * b[0] - 2.0 * ub);
   double s = 0.0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
@@ -207,7 +221,7 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
                          const double (*Gr)[DIM + 2], double dt, double* F, double* Wt) {
   constexpr int NV = DIM + 2;
   const double K = P.K;
-  const Prim<DIM> pl = to_prim<DIM>(Wl, K), pr = to_prim<DIM>(Wr, K);
+  const Prim<DIM> pl = to_prim<DIM>(Wl, P), pr = to_prim<DIM>(Wr, P);
   // half-space moments for the kinetic part
   Mom<DIM> ml, mr;
   tang_moments<DIM>(pl, K, ml);
@@ -220,7 +234,7 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
   psi_mom<DIM, 0, 0, 0>(mr, t);
 #pragma unroll
   for (int i = 0; i < NV; ++i) Wc[i] = pl.rho * Wc[i] + pr.rho * t[i];
-  const Prim<DIM> pc = to_prim<DIM>(Wc, K);
+  const Prim<DIM> pc = to_prim<DIM>(Wc, P);
   Mom<DIM> mc;
   tang_moments<DIM>(pc, K, mc);
   normal_moments<DIM>(pc, 0, mc);
@@ -228,16 +242,16 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
   double al[DIM][NV], ar[DIM][NV], ac[DIM][NV], b[NV];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const double il = 1.0 / pl.rho, irr = 1.0 / pr.rho, ic = 1.0 / pc.rho;
+    const double il = pl.irho, irr = pr.irho, ic = pc.irho;
 #pragma unroll
     for (int i = 0; i < NV; ++i) b[i] = Gl[d][i] * il;
-    slope_solve<DIM>(pl, K, b, al[d]);
+    slope_solve<DIM>(pl, P, b, al[d]);
 #pragma unroll
     for (int i = 0; i < NV; ++i) b[i] = Gr[d][i] * irr;
-    slope_solve<DIM>(pr, K, b, ar[d]);
+    slope_solve<DIM>(pr, P, b, ar[d]);
 #pragma unroll
     for (int i = 0; i < NV; ++i) b[i] = 0.5 * (Gl[d][i] + Gr[d][i]) * ic;
-    slope_solve<DIM>(pc, K, b, ac[d]);
+    slope_solve<DIM>(pc, P, b, ac[d]);
   }
   // time slopes from <A + a.u> = 0 (full-space moments of each Maxwellian)
   double Al[NV], Ar[NV], Ac[NV];
@@ -249,11 +263,11 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
 #pragma unroll
     for (int i = 0; i < NV; ++i) s[i] = 0.0;
     au_mom<DIM, 0>(fl, al, -1.0, s);
-    slope_solve<DIM>(pl, K, s, Al);
+    slope_solve<DIM>(pl, P, s, Al);
 #pragma unroll
     for (int i = 0; i < NV; ++i) s[i] = 0.0;
     au_mom<DIM, 0>(fr, ar, -1.0, s);
-    slope_solve<DIM>(pr, K, s, Ar);
+    slope_solve<DIM>(pr, P, s, Ar);
   }
   double PAc[NV];
 #pragma unroll
@@ -263,10 +277,10 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
     double s[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) s[i] = -PAc[i];
-    slope_solve<DIM>(pc, K, s, Ac);
+    slope_solve<DIM>(pc, P, s, Ac);
   }
   // collision time and time integrals
-  const double pL = 0.5 * pl.rho / pl.lam, pR = 0.5 * pr.rho / pr.lam;
+  const double pL = pl.rho * pl.h, pR = pr.rho * pr.h;
   const double tau = P.c1 * dt + P.c2 * fabs(pL - pR) / (pL + pR) * dt;
   const double e = exp(-dt / tau);
   const double T1 = dt - tau * (1.0 - e);
@@ -319,9 +333,10 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
 
 // KFVS flux of constant states, local frame
 template <int DIM>
-__device__ __forceinline__ void kfvs_flux(double K, const double* Wl, const double* Wr, double* F) {
+__device__ __forceinline__ void kfvs_flux(const PhysParams& P, const double* Wl, const double* Wr, double* F) {
   constexpr int NV = DIM + 2;
-  const Prim<DIM> pl = to_prim<DIM>(Wl, K), pr = to_prim<DIM>(Wr, K);
+  const double K = P.K;
+  const Prim<DIM> pl = to_prim<DIM>(Wl, P), pr = to_prim<DIM>(Wr, P);
   Mom<DIM> ml, mr;
   tang_moments<DIM>(pl, K, ml);
   tang_moments<DIM>(pr, K, mr);
