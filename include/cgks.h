@@ -231,6 +231,34 @@ int cgks_vcycle_launch(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycle
  * Synchronises the stream.  Used as the ALU roofline denominator. */
 int cgks_fma_probe(cgks_t* h, int precision, double* tflops);
 
+/*
+ * Batched solves.  After uploading the union of several meshes (disconnected
+ * components, e.g. from concatenated inputs) as one mesh, tag each fine cell
+ * (original order) with its member index 0..n_groups-1 and give each member
+ * its own free stream winf [n_groups][nv] (host, copied).  Every coarse cell
+ * must lie inside one member.  All members then advance together in every
+ * launch of the V-cycle: each colour phase covers that colour of every member.
+ */
+int cgks_set_groups(cgks_t* h, int mesh_id, int n_groups, const int32_t* group_of_cell, const double* winf);
+
+/*
+ * V-cycles of a grouped mesh: up to n_cycles cycles; every cfg.check_every
+ * cycles each member whose RMS density residual has dropped by cfg.tol from
+ * its first recorded cycle is frozen (its state no longer changes) and its
+ * cycle count stored in cycles_to_tol [n_groups] (-1 if not reached); stops
+ * when every member is frozen.  norms_out (host, nullable)
+ * [n_cycles][n_groups][nv][2] as in cgks_vcycle; *cycles_done (nullable).
+ */
+int cgks_vcycle_groups(cgks_t* h, int mesh_id, int n_cycles, int mode, double* norms_out, int* cycles_to_tol,
+                       int* cycles_done);
+
+/* Autotuner: times candidate block sizes (64, 128, 256 threads) of the
+ * reconstruction, flux, sweep and coarse face/cell kernels on this mesh at its
+ * current state and keeps the fastest; blocks_out (nullable) [7] receives the
+ * chosen sizes (reconstruction, flux, gather, sweep, coarse face, coarse cell,
+ * update).  Captured graphs are rebuilt on the next V-cycle. */
+int cgks_autotune(cgks_t* h, int mesh_id, int* blocks_out);
+
 /* Waits for all work of h on its stream. */
 int cgks_synchronize(cgks_t* h);
 

@@ -27,7 +27,8 @@ EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_erro
            "cgks_init_state", "cgks_get_state", "cgks_set_state", "cgks_residual", "cgks_reconstruct",
            "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
            "cgks_gks_points", "cgks_kfvs_points", "cgks_run_stage", "cgks_launch_count",
-           "cgks_vcycle_launch", "cgks_fma_probe",
+           "cgks_vcycle_launch", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
+           "cgks_autotune",
            "cgks_synchronize"]
 
 
@@ -83,6 +84,9 @@ def load_library(path: str = LIB_PATH):
         "cgks_run_stage": [P, I, I],
         "cgks_vcycle_launch": [P, P, I, I, I],
         "cgks_fma_probe": [P, I, P],
+        "cgks_set_groups": [P, I, I, P, P],
+        "cgks_vcycle_groups": [P, I, I, I, P, P, P],
+        "cgks_autotune": [P, I, P],
         "cgks_launch_count": [P, I, I, P],
         "cgks_synchronize": [P],
     }
@@ -256,6 +260,26 @@ class Context:
         out = C.c_double()
         self._check(self._L.cgks_fma_probe(self.h, precision, C.byref(out)))
         return out.value
+
+    def cgks_set_groups(self, mesh_id: int, group_of_cell, winf):
+        g = np.ascontiguousarray(group_of_cell, np.int32)
+        w = np.ascontiguousarray(winf, np.float64)
+        self._check(self._L.cgks_set_groups(self.h, mesh_id, w.shape[0], _ptr(g), _ptr(w)))
+        self.meshes[mesh_id]["groups"] = w.shape[0]
+
+    def cgks_vcycle_groups(self, mesh_id: int, n_cycles: int, mode: int = PLAIN_FP64, norms=None, check=True):
+        G = self.meshes[mesh_id]["groups"]
+        conv = np.zeros(G, np.int32)
+        done = C.c_int()
+        rc = self._L.cgks_vcycle_groups(self.h, mesh_id, n_cycles, mode, _ptr(norms), _ptr(conv), C.byref(done))
+        if check:
+            self._check(rc)
+        return conv, done.value, rc
+
+    def cgks_autotune(self, mesh_id: int):
+        out = np.zeros(7, np.int32)
+        self._check(self._L.cgks_autotune(self.h, mesh_id, _ptr(out)))
+        return out
 
     def cgks_run_stage(self, mesh_id: int, stage: int):
         self._check(self._L.cgks_run_stage(self.h, mesh_id, stage))

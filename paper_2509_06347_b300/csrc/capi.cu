@@ -95,6 +95,8 @@ struct LevelDev {
   int *ch_off = nullptr, *ch_idx = nullptr;  // children in the finer level
 };
 
+enum BlockClass { B_RECON = 0, B_FLUX, B_GATHER, B_SWEEP, B_FACE, B_CELL, B_UPDATE };
+
 struct MeshDev {
   int dim = 0, nv = 0, nlev = 0;
   Hierarchy H;
@@ -114,6 +116,16 @@ struct MeshDev {
   std::vector<LevelDev> lev;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_kernels[2] = {0, 0};
+  // batched members (groups of cells with their own free stream)
+  int n_groups = 1;
+  std::vector<std::unique_ptr<DBuf>> gpool;
+  std::vector<int*> lgrp;  // per level: group of each cell (device), empty if ungrouped
+  double* qcell = nullptr;
+  int *goff = nullptr, *gidx = nullptr, *active = nullptr;
+  double *hist_g = nullptr, *last_g = nullptr;
+  std::vector<int> gcount;
+  // launch block sizes per kernel class (autotuned)
+  int blk[7] = {256, 256, 256, 256, 128, 128, 256};
   ~MeshDev() {
     for (auto& g : graph)
       if (g) cudaGraphExecDestroy(g);
@@ -311,7 +323,7 @@ void build_levels_device(MeshDev& M) {
 template <int DIM>
 void launch_recon(cgks_t* h, MeshDev& M) {
   LevelDev& L = M.lev[0];
-  k_recon<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
+  k_recon<DIM><<<blocks_for(L.n, M.blk[B_RECON]), M.blk[B_RECON], 0, h->stream>>>(
       M.fine, L.W, M.G, L.alpha, M.winf, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, h->cfg.weno_gamma_high,
       h->cfg.weno_eps, M.coef, L.dte, L.dti, M.cnt);
 }
@@ -322,7 +334,7 @@ void launch_flux(cgks_t* h, MeshDev& M) {
   constexpr int NGP = Dims<DIM>::NGP, FPW = 32 / NGP;
   const int64_t warps = (M.fine.nf + FPW - 1) / FPW;
   const int64_t threads = warps * 32;
-  k_flux<DIM><<<blocks_for(threads), kBlock, 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, phys(h->cfg, DIM),
+  k_flux<DIM><<<blocks_for(threads, M.blk[B_FLUX]), M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, phys(h->cfg, DIM),
                                                                M.Fface, M.Wface, M.aface, L.W, L.rface);
 }
 
@@ -334,13 +346,22 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
   LevelDev& L = M.lev[0];
   launch_recon<DIM>(h, M);
   launch_flux<DIM>(h, M);
-  k_gather<DIM><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
+  const bool grouped = !M.lgrp.empty();
+  // norm partials need whole blocks of kBlock threads
+  const int gb = (want_norm && !grouped) ? kBlock : M.blk[B_GATHER];
+  k_gather<DIM><<<blocks_for(L.n, gb), gb, 0, h->stream>>>(
       M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R,
       slopes_update ? M.G : nullptr, alpha_out_dev ? alpha_out_dev : L.alpha, want_diag ? L.D : nullptr,
-      gradnew_dev, want_norm ? M.norm_part : nullptr, h->cfg.df_relax, L.rface);
-  if (want_norm)
+      gradnew_dev, (want_norm && !grouped) ? M.norm_part : nullptr, h->cfg.df_relax, L.rface,
+      (want_norm && grouped) ? M.qcell : nullptr, (grouped && !alpha_out_dev) ? M.active : nullptr);
+  if (want_norm && !grouped)
     k_norm_final<DIM + 2><<<1, kBlock, 0, h->stream>>>(M.norm_part, M.norm_blocks, L.n, record ? M.hist : nullptr,
                                                        record ? M.cycle : nullptr, M.max_hist, M.last_norm);
+  if (want_norm && grouped) {
+    k_group_norm<DIM + 2><<<M.n_groups, kBlock, 0, h->stream>>>(M.qcell, M.goff, M.gidx, record ? M.hist_g : nullptr,
+                                                                M.cycle, M.max_hist, M.n_groups, M.last_g);
+    if (record) k_bump<<<1, 1, 0, h->stream>>>(M.cycle);
+  }
 }
 
 template <int DIM, typename T>
@@ -352,30 +373,33 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
   for (int c = 0; c < nc - 1; ++c) {
     const int lo = L.color_off[c], hi = L.color_off[c + 1];
     if (hi > lo)
-      k_sweep<DIM, T, 0><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
+      k_sweep<DIM, T, 0><<<blocks_for(hi - lo, M.blk[B_SWEEP]), M.blk[B_SWEEP], 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
                                                                          L.rface, h->cfg.gamma, dWs, dW);
   }
   {
     const int lo = L.color_off[nc - 1], hi = L.color_off[nc];
     if (hi > lo)
-      k_sweep<DIM, T, 2><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
+      k_sweep<DIM, T, 2><<<blocks_for(hi - lo, M.blk[B_SWEEP]), M.blk[B_SWEEP], 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
                                                                          L.rface, h->cfg.gamma, dWs, dW);
   }
   for (int c = nc - 2; c >= 0; --c) {
     const int lo = L.color_off[c], hi = L.color_off[c + 1];
     if (hi > lo)
-      k_sweep<DIM, T, 1><<<blocks_for(hi - lo), kBlock, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
+      k_sweep<DIM, T, 1><<<blocks_for(hi - lo, M.blk[B_SWEEP]), M.blk[B_SWEEP], 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
                                                                          L.rface, h->cfg.gamma, dWs, dW);
   }
-  k_update<DIM, T><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, h->cfg.gamma, L.W, dW, M.cnt);
+  const bool fine = &L == &M.lev[0];
+  const bool masked = fine && !M.lgrp.empty();
+  k_update<DIM, T><<<blocks_for(L.n, M.blk[B_UPDATE]), M.blk[B_UPDATE], 0, h->stream>>>(
+      L.n, h->cfg.gamma, L.W, dW, M.cnt, masked ? M.lgrp[0] : nullptr, masked ? M.active : nullptr);
 }
 
 template <int DIM>
 void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag) {
   const PhysParams p = phys(h->cfg, DIM);
-  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, 128), 128, 0, h->stream>>>(L.faces, L.W, M.winf, p, L.Fc,
-                                                                         want_diag ? L.rface : nullptr);
-  k_coarse_cell<DIM><<<blocks_for(L.n, 128), 128, 0, h->stream>>>(
+  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, M.blk[B_FACE]), M.blk[B_FACE], 0, h->stream>>>(
+      L.faces, L.W, M.winf, p, L.Fc, want_diag ? L.rface : nullptr);
+  k_coarse_cell<DIM><<<blocks_for(L.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(
       L.topo, L.W, L.Fc, L.rface, Pf, nullptr, h->cfg.df_relax ? L.alpha : L.ones, h->cfg.gamma, h->cfg.cfl_exp,
       h->cfg.cfl_imp, L.R, want_diag ? L.D : nullptr);
 }
@@ -384,8 +408,10 @@ void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want
 template <int DIM>
 void coarse_forcing(cgks_t* h, MeshDev& M, LevelDev& L) {
   const PhysParams p = phys(h->cfg, DIM);
-  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, 128), 128, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, nullptr);
-  k_coarse_cell<DIM><<<blocks_for(L.n, 128), 128, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, L.Rstar,
+  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, M.blk[B_FACE]), M.blk[B_FACE], 0, h->stream>>>(L.faces, L.W0, M.winf,
+                                                                                              p, L.Fc, nullptr);
+  k_coarse_cell<DIM><<<blocks_for(L.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr,
+                                                                                        nullptr, L.Rstar,
                                                                     L.alpha, h->cfg.gamma, 0.0, 0.0, L.P, nullptr);
 }
 
@@ -397,8 +423,9 @@ void vcycle_body(cgks_t* h, MeshDev& M) {
   fine_residual<DIM>(h, M, true, true, true, true, nullptr, nullptr);
   // 2. pre-smoothing: one DF-relaxed LU-SGS step on -R, or the explicit update
   if (h->cfg.fine_smoother == 1)
-    k_explicit<DIM><<<blocks_for(L0.n), kBlock, 0, h->stream>>>(L0.n, h->cfg.gamma, L0.R, L0.dte, L0.vol, L0.W,
-                                                                 M.cnt);
+    k_explicit<DIM><<<blocks_for(L0.n), kBlock, 0, h->stream>>>(
+        L0.n, h->cfg.gamma, L0.R, L0.dte, L0.vol, L0.W, M.cnt, M.lgrp.empty() ? nullptr : M.lgrp[0],
+        M.lgrp.empty() ? nullptr : M.active);
   else
     sweeps<DIM, T>(h, M, L0, nullptr);
   if (M.nlev == 1) return;
@@ -421,8 +448,11 @@ void vcycle_body(cgks_t* h, MeshDev& M) {
   for (int l = M.nlev - 1; l >= 1; --l) {
     LevelDev& F = M.lev[l - 1];
     LevelDev& C = M.lev[l];
+    const bool masked = l == 1 && !M.lgrp.empty();
     k_prolong<DIM><<<blocks_for(F.n), kBlock, 0, h->stream>>>(F.n, F.parent, h->cfg.df_prolong ? F.alpha : F.ones,
-                                                               C.W, C.W0, h->cfg.gamma, F.W, M.cnt);
+                                                               C.W, C.W0, h->cfg.gamma, F.W, M.cnt,
+                                                               masked ? M.lgrp[0] : nullptr,
+                                                               masked ? M.active : nullptr);
   }
 }
 
@@ -639,6 +669,11 @@ int cgks_upload_hierarchy(cgks_t* h, int mesh_id, int n_levels, const int32_t* c
       return fail(h, CGKS_ERR_MESH, e.what());
     }
     CK(cudaStreamSynchronize(h->stream));
+    M.lgrp.clear();
+    M.gpool.clear();
+    M.qcell = nullptr;
+    M.n_groups = 1;
+    if (M.winf_h.size() > (size_t)M.nv) M.winf_h.resize(M.nv);
     M.pool.clear();
     M.nlev = n_levels;
     build_fine_device(M);
@@ -1024,9 +1059,9 @@ int cgks_run_stage(cgks_t* h, int mesh_id, int stage) {
       else launch_flux<3>(h, M);
     } else {
       if (M.dim == 2)
-        k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax, L.rface);
+        k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax, L.rface, nullptr, nullptr);
       else
-        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax, L.rface);
+        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax, L.rface, nullptr, nullptr);
     }
     CK(cudaGetLastError());
     return CGKS_OK;
@@ -1040,6 +1075,198 @@ int cgks_launch_count(cgks_t* h, int mesh_id, int mode, int* count) {
     if (!count || (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED)) throw ArgError("invalid arguments");
     get_graph(h, M, mode);
     *count = M.graph_kernels[mode];
+    return CGKS_OK;
+  });
+}
+
+int cgks_set_groups(cgks_t* h, int mesh_id, int n_groups, const int32_t* group_of_cell, const double* winf) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, false);
+    if (n_groups < 1 || !group_of_cell || !winf) throw ArgError("invalid group arguments");
+    const int nv = M.nv;
+    const FineLevel& F = M.H.fine;
+    // group of every cell on every level (new ids); coarse cells inherit the
+    // group of their children, which must agree
+    std::vector<std::vector<int>> grp(M.nlev);
+    grp[0].resize(F.n);
+    std::vector<int> count(n_groups, 0);
+    for (int64_t c = 0; c < F.n; ++c) {
+      const int g = group_of_cell[F.iperm[c]];
+      if (g < 0 || g >= n_groups) throw ArgError("group id out of range");
+      grp[0][c] = g;
+      count[g]++;
+    }
+    for (int g = 0; g < n_groups; ++g)
+      if (count[g] == 0) throw ArgError("empty group");
+    for (int l = 1; l < M.nlev; ++l) {
+      const CoarseLevel& C = M.H.coarse[l - 1];
+      grp[l].assign(C.n, -1);
+      for (int64_t i = 0; i < (int64_t)grp[l - 1].size(); ++i) {
+        const int64_t I = C.parent_of_fine[i];
+        if (grp[l][I] >= 0 && grp[l][I] != grp[l - 1][i]) throw ArgError("a coarse cell spans two groups");
+        grp[l][I] = grp[l - 1][i];
+      }
+    }
+    M.gpool.clear();
+    M.lgrp.assign(M.nlev, nullptr);
+    for (int l = 0; l < M.nlev; ++l) {
+      M.lgrp[l] = upload(M.gpool, grp[l]);
+      M.lev[l].faces.grp = M.lgrp[l];
+    }
+    M.fine.grp = M.lgrp[0];
+    // fine cells of each group in colour order
+    std::vector<int> off(n_groups + 1, 0), idx(F.n);
+    for (int g = 0; g < n_groups; ++g) off[g + 1] = off[g] + count[g];
+    std::vector<int> pos(off.begin(), off.end() - 1);
+    for (int64_t c = 0; c < F.n; ++c) idx[pos[grp[0][c]]++] = (int)c;
+    M.goff = upload(M.gpool, off);
+    M.gidx = upload(M.gpool, idx);
+    M.qcell = dalloc<double>(M.gpool, (size_t)F.n * 2 * nv);
+    M.hist_g = dalloc<double>(M.gpool, (size_t)M.max_hist * n_groups * 2 * nv);
+    M.last_g = dalloc<double>(M.gpool, (size_t)n_groups * 2 * nv);
+    M.active = upload(M.gpool, std::vector<int>(n_groups, 1));
+    M.gcount = count;
+    M.n_groups = n_groups;
+    M.winf_h.assign(winf, winf + (size_t)n_groups * nv);
+    DBuf* wb = new DBuf;
+    M.gpool.emplace_back(wb);
+    wb->alloc((size_t)n_groups * nv * sizeof(double));
+    CK(cudaMemcpy(wb->p, winf, (size_t)n_groups * nv * sizeof(double), cudaMemcpyHostToDevice));
+    M.winf = wb->as<double>();
+    for (auto& g : M.graph)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    CK(cudaDeviceSynchronize());
+    return CGKS_OK;
+  });
+}
+
+int cgks_vcycle_groups(cgks_t* h, int mesh_id, int n_cycles, int mode, double* norms_out, int* cycles_to_tol,
+                       int* cycles_done) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    if (M.lgrp.empty()) throw StateError("cgks_set_groups has not been called for this mesh");
+    if (n_cycles < 0 || (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED)) throw ArgError("invalid arguments");
+    const int G = M.n_groups, nv = M.nv;
+    cudaGraphExec_t g = get_graph(h, M, mode);
+    int start = 0;
+    CK(cudaMemcpyAsync(&start, M.cycle, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<int> act(G, 1), conv(G, -1);
+    std::vector<double> hist, first(G, -1.0);
+    int done = 0, status = CGKS_OK;
+    CK(cudaMemcpyAsync(M.active, act.data(), G * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    while (done < n_cycles) {
+      const int chunk = std::min(h->cfg.check_every, n_cycles - done);
+      for (int i = 0; i < chunk; ++i) CK(cudaGraphLaunch(g, h->stream));
+      const int upto = std::min(start + done + chunk, M.max_hist);
+      hist.resize((size_t)upto * G * 2 * nv);
+      CK(cudaMemcpyAsync(hist.data(), M.hist_g, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (int k = start + done; k < upto; ++k)
+        for (int q = 0; q < G; ++q) {
+          const double r = hist[((size_t)k * G + q) * 2 * nv];
+          if (first[q] < 0) first[q] = r;
+          if (!std::isfinite(r) || (first[q] > 0 && r > h->cfg.diverge_factor * first[q])) status = CGKS_ERR_DIVERGED;
+          if (conv[q] < 0 && act[q] && first[q] > 0 && r <= h->cfg.tol * first[q]) {
+            conv[q] = k - start + 1;
+            act[q] = 0;  // converged: freeze this member
+          }
+        }
+      done += chunk;
+      CK(cudaMemcpyAsync(M.active, act.data(), G * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      if (status != CGKS_OK || std::all_of(act.begin(), act.end(), [](int a) { return a == 0; })) break;
+    }
+    std::fill(act.begin(), act.end(), 1);
+    CK(cudaMemcpyAsync(M.active, act.data(), G * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (norms_out)
+      for (int i = 0; i < n_cycles; ++i)
+        for (int j = 0; j < G * 2 * nv; ++j) {
+          const size_t idx = (size_t)(start + i) * G * 2 * nv + j;
+          norms_out[(size_t)i * G * 2 * nv + j] = (i < done && start + i < M.max_hist) ? hist[idx] : -1.0;
+        }
+    if (cycles_to_tol) std::memcpy(cycles_to_tol, conv.data(), G * sizeof(int));
+    if (cycles_done) *cycles_done = done;
+    if (status != CGKS_OK) h->err = "a batch member diverged";
+    return status;
+  });
+}
+
+int cgks_autotune(cgks_t* h, int mesh_id, int* blocks_out) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    const int cand[3] = {64, 128, 256};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto timeit = [&](auto&& launch) {
+      launch();
+      CK(cudaEventRecord(e0, h->stream));
+      for (int r = 0; r < 5; ++r) launch();
+      CK(cudaEventRecord(e1, h->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      return ms;
+    };
+    // populate R, D, face data at the current state (no state change)
+    if (M.dim == 2) fine_residual<2>(h, M, false, true, false, false, M.gradnew, nullptr);
+    else fine_residual<3>(h, M, false, true, false, false, M.gradnew, nullptr);
+    LevelDev& L = M.lev[0];
+    auto tune = [&](int cls, auto&& launch) {
+      float best = 1e30f;
+      int bb = M.blk[cls];
+      for (int b : cand) {
+        M.blk[cls] = b;
+        const float t = timeit(launch);
+        if (t < best) { best = t; bb = b; }
+      }
+      M.blk[cls] = bb;
+    };
+    const PhysParams p = phys(h->cfg, M.dim);
+    if (M.dim == 2) {
+      tune(B_RECON, [&] { launch_recon<2>(h, M); });
+      tune(B_FLUX, [&] { launch_flux<2>(h, M); });
+      tune(B_SWEEP, [&] {
+        k_sweep<2, float, 0><<<blocks_for(L.color_off[1], M.blk[B_SWEEP]), M.blk[B_SWEEP], 0, h->stream>>>(
+            L.topo, 0, L.color_off[1], L.W, L.R, nullptr, L.alpha, L.D, L.rface, h->cfg.gamma, L.dWs32, L.dW32);
+      });
+      if (M.nlev > 1) {
+        LevelDev& C = M.lev[1];
+        tune(B_FACE, [&] {
+          k_face_kfvs<2><<<blocks_for(C.faces.nf, M.blk[B_FACE]), M.blk[B_FACE], 0, h->stream>>>(C.faces, C.W, M.winf, p, C.Fc, C.rface);
+        });
+        tune(B_CELL, [&] {
+          k_coarse_cell<2><<<blocks_for(C.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(C.topo, C.W, C.Fc, C.rface, nullptr, nullptr, C.alpha, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, C.R, C.D);
+        });
+      }
+    } else {
+      tune(B_RECON, [&] { launch_recon<3>(h, M); });
+      tune(B_FLUX, [&] { launch_flux<3>(h, M); });
+      tune(B_SWEEP, [&] {
+        k_sweep<3, float, 0><<<blocks_for(L.color_off[1], M.blk[B_SWEEP]), M.blk[B_SWEEP], 0, h->stream>>>(
+            L.topo, 0, L.color_off[1], L.W, L.R, nullptr, L.alpha, L.D, L.rface, h->cfg.gamma, L.dWs32, L.dW32);
+      });
+      if (M.nlev > 1) {
+        LevelDev& C = M.lev[1];
+        tune(B_FACE, [&] {
+          k_face_kfvs<3><<<blocks_for(C.faces.nf, M.blk[B_FACE]), M.blk[B_FACE], 0, h->stream>>>(C.faces, C.W, M.winf, p, C.Fc, C.rface);
+        });
+        tune(B_CELL, [&] {
+          k_coarse_cell<3><<<blocks_for(C.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(C.topo, C.W, C.Fc, C.rface, nullptr, nullptr, C.alpha, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, C.R, C.D);
+        });
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    for (auto& g : M.graph)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    if (blocks_out)
+      for (int i = 0; i < 7; ++i) blocks_out[i] = M.blk[i];
     return CGKS_OK;
   });
 }

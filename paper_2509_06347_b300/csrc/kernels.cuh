@@ -50,6 +50,7 @@ struct DevFine {
   const double* m2;     // [dim*dim][n]
   const double* vol;    // [n]
   const double* bsc;    // [n] |Omega|^(2/dim)
+  const int* grp;       // [n] batch group of each cell (free stream index), or null
 };
 
 // Cell -> face entries for the sweeps and cell-based coarse fluxes (CSR).
@@ -73,6 +74,7 @@ struct FaceSet {
   const int* ftag;
   const double* fn;  // [nf][dim]
   const double* fS;  // [nf]
+  const int* grp;    // batch group of each cell of the level, or null
 };
 
 struct Counters {
@@ -167,8 +169,9 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
       for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int d = 0; d < DIM; ++d) g0[v][d] = Gr[((size_t)c * NV + v) * DIM + d];
-      ghost_state<DIM>(tag, winf, nrm[m], W0, Qm[m]);
-      ghost_grad<DIM>(tag, winf, nrm[m], g0, Dm[m]);
+      const double* wi = winf + NV * (M.grp ? M.grp[c] : 0);
+      ghost_state<DIM>(tag, wi, nrm[m], W0, Qm[m]);
+      ghost_grad<DIM>(tag, wi, nrm[m], g0, Dm[m]);
     }
   }
   // local time steps: dt = CFL V / sum_f S_f (|u.n| + c)
@@ -377,8 +380,9 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __rest
       dt = fmin(dt, dte[R]);
     } else {
       const int tag = M.ftag[f];
-      ghost_state<DIM>(tag, winf, n, Wl, Wr);
-      ghost_grad<DIM>(tag, winf, n, gl, gr);
+      const double* wi = winf + NV * (M.grp ? M.grp[L] : 0);
+      ghost_state<DIM>(tag, wi, n, Wl, Wr);
+      ghost_grad<DIM>(tag, wi, n, gl, gr);
     }
     double wl[NV], wr[NV], Gl[DIM][NV], Gr[DIM][NV], Fl[NV], Wt[NV];
     to_local<DIM>(fr, Wl, wl);
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __rest
 #pragma unroll
       for (int v = 0; v < NV; ++v) WR[v] = Wc[(size_t)R * NV + v];
     } else {
-      ghost_state<DIM>(M.ftag[f], winf, n, WL, WR);
+      ghost_state<DIM>(M.ftag[f], winf + NV * (M.grp ? M.grp[L] : 0), n, WL, WR);
     }
     rface[f] = spectral_radius<DIM, double>(P.gamma, WL, WR, n);
   }
@@ -457,7 +461,8 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
                                                    double* __restrict__ Gout, double* __restrict__ alpha,
                                                    double* __restrict__ Dg, double* __restrict__ gradnew_out,
                                                    double* __restrict__ norm_part, int df_relax,
-                                                   const double* __restrict__ rface) {
+                                                   const double* __restrict__ rface, double* __restrict__ qcell,
+                                                   const int* __restrict__ active) {
   using Dm = Dims<DIM>;
   constexpr int NV = Dm::NV, NFC = Dm::NFC;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -489,20 +494,25 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
       a *= aface[f];
     }
     const double iV = 1.0 / M.vol[c];
+    const bool live = !active || active[M.grp[c]];  // frozen (converged) batch members keep their state
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       R[(size_t)c * NV + v] = r[v];
       const double q = r[v] * iV;
       rl2[v] = q * q;
       rmax[v] = fabs(q);
+      if (qcell) {
+        qcell[(size_t)c * 2 * NV + 2 * v] = q * q;
+        qcell[(size_t)c * 2 * NV + 2 * v + 1] = fabs(q);
+      }
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const double g = gn[v][d] * iV;
         if (gradnew_out) gradnew_out[((size_t)c * NV + v) * DIM + d] = g;
-        if (Gout) Gout[((size_t)c * NV + v) * DIM + d] = a * g;  // slope update with DF
+        if (Gout && live) Gout[((size_t)c * NV + v) * DIM + d] = a * g;  // slope update with DF
       }
     }
-    alpha[c] = a;
+    if (live) alpha[c] = a;
     if (Dg) Dg[c] = lusgs_diag<DIM>(T, c, rface, df_relax ? a : 1.0, dte[c], dti[c]);
   }
   if (norm_part) {
@@ -569,6 +579,45 @@ __global__ void k_norm_final(const double* __restrict__ part, int nblocks, int n
     }
   }
 }
+
+// per-group norms (batched meshes): one block per group, fixed order
+template <int NV>
+__global__ void k_group_norm(const double* __restrict__ qcell, const int* __restrict__ goff,
+                             const int* __restrict__ gidx, double* __restrict__ hist, const int* __restrict__ cycle,
+                             int max_hist, int n_groups, double* __restrict__ last) {
+  __shared__ double s[2 * NV][kBlock];
+  const int g = blockIdx.x;
+  const int lo = goff[g], hi = goff[g + 1];
+  for (int i = 0; i < 2 * NV; ++i) {
+    double acc = 0.0;
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+      const double x = qcell[(size_t)gidx[k] * 2 * NV + i];
+      acc = (i & 1) ? fmax(acc, x) : acc + x;
+    }
+    s[i][threadIdx.x] = acc;
+  }
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int i = 0; i < 2 * NV; ++i)
+        s[i][threadIdx.x] = (i & 1) ? fmax(s[i][threadIdx.x], s[i][threadIdx.x + st])
+                                    : s[i][threadIdx.x] + s[i][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int k = *cycle;
+    for (int v = 0; v < NV; ++v) {
+      const double rms = sqrt(s[2 * v][0] / (double)(hi - lo)), mx = s[2 * v + 1][0];
+      if (hist && k < max_hist) {
+        hist[((size_t)k * n_groups + g) * 2 * NV + 2 * v] = rms;
+        hist[((size_t)k * n_groups + g) * 2 * NV + 2 * v + 1] = mx;
+      }
+      last[(size_t)g * 2 * NV + 2 * v] = rms;
+      last[(size_t)g * 2 * NV + 2 * v + 1] = mx;
+    }
+  }
+}
+__global__ void k_bump(int* __restrict__ cycle) { *cycle += 1; }
 
 // ---------------------------------------------------------------------------
 // K4 / K5: multi-colour LU-SGS sweeps (Eqs. gpu-forward-relaxation and
@@ -667,10 +716,12 @@ __device__ __forceinline__ int guarded_add(double gamma, double* W, const double
 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(kBlock) k_update(int n, double gamma, double* __restrict__ W,
-                                                   const T* __restrict__ dW, Counters* __restrict__ cnt) {
+                                                   const T* __restrict__ dW, Counters* __restrict__ cnt,
+                                                   const int* __restrict__ grp, const int* __restrict__ active) {
   constexpr int NV = DIM + 2;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
+  if (active && !active[grp[c]]) return;
   double w[NV], d[NV];
   bool finite = true;
 #pragma unroll
@@ -694,10 +745,12 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, double gamma, double* 
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_explicit(int n, double gamma, const double* __restrict__ R,
                                                      const double* __restrict__ dte, const double* __restrict__ vol,
-                                                     double* __restrict__ W, Counters* __restrict__ cnt) {
+                                                     double* __restrict__ W, Counters* __restrict__ cnt,
+                                                     const int* __restrict__ grp, const int* __restrict__ active) {
   constexpr int NV = DIM + 2;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
+  if (active && !active[grp[c]]) return;
   const double s = -dte[c] / vol[c];
   double w[NV], d[NV];
 #pragma unroll
@@ -733,7 +786,7 @@ __global__ void __launch_bounds__(kBlock) k_face_kfvs(FaceSet Fs, const double* 
 #pragma unroll
     for (int v = 0; v < NV; ++v) WR[v] = W[(size_t)R * NV + v];
   } else {
-    ghost_state<DIM>(Fs.ftag[f], winf, n, WL, WR);
+    ghost_state<DIM>(Fs.ftag[f], winf + NV * (Fs.grp ? Fs.grp[L] : 0), n, WL, WR);
   }
   if (Fout) {
     const Frame<DIM> fr = make_frame<DIM>(n);
@@ -841,10 +894,12 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_prolong(int nf, const int* __restrict__ parent,
                                                     const double* __restrict__ af, const double* __restrict__ Wc,
                                                     const double* __restrict__ Wc0, double gamma, double* __restrict__ Wf,
-                                                    Counters* __restrict__ cnt) {
+                                                    Counters* __restrict__ cnt, const int* __restrict__ grp,
+                                                    const int* __restrict__ active) {
   constexpr int NV = DIM + 2;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nf) return;
+  if (active && !active[grp[i]]) return;
   const int I = parent[i];
   double w[NV], d[NV];
   const double a = af[i];

@@ -422,3 +422,47 @@ def vortex_state(mesh, gamma: float = 1.4, eps: float = 5.0, order_1d: int = 6,
         grad += fm[:, :, None] * nvec[:, None, :]
     grad /= np.abs(area)[:, None, None]
     return W, grad
+
+
+def concat_meshes(meshes):
+    """Concatenate meshes (same dim, same number of levels) into one
+    disconnected mesh.  Node ids, cells, boundary faces and parent maps are
+    offset per mesh; returns (union mesh, group_of_cell) where group_of_cell[i]
+    is the index of the mesh that fine cell i came from."""
+    dim = meshes[0]["dim"]
+    nlev = len(meshes[0]["parents"]) + 1
+    cn, cx, bn, bt, grp = [], [], [], [], []
+    parents = [[] for _ in range(nlev - 1)]
+    node_off = 0
+    lev_off = [0] * nlev
+    for g, m in enumerate(meshes):
+        assert m["dim"] == dim and len(m["parents"]) + 1 == nlev
+        cn.append(m["cell_nodes"].astype(np.int64) + node_off)
+        cx.append(m["cell_xyz"])
+        if m["bface_nodes"].size:
+            bn.append(m["bface_nodes"].astype(np.int64) + node_off)
+            bt.append(m["bface_tag"])
+        grp.append(np.full(m["cell_nodes"].shape[0], g, np.int32))
+        sizes = [m["cell_nodes"].shape[0]] + [int(p.max()) + 1 for p in m["parents"]]
+        for l, p in enumerate(m["parents"]):
+            parents[l].append(p.astype(np.int64) + lev_off[l + 1])
+        for l in range(nlev):
+            lev_off[l] += sizes[l]
+        node_off += int(max(m["cell_nodes"].max(), m["bface_nodes"].max() if m["bface_nodes"].size else 0)) + 1
+    union = _finish(dim, np.concatenate(cn), np.concatenate(cx),
+                    np.concatenate(bn) if bn else np.zeros((0, dim)),
+                    np.concatenate(bt) if bt else np.zeros(0),
+                    [np.concatenate(p) for p in parents],
+                    name=f"batch{len(meshes)}", level_sizes=lev_off)
+    return union, np.concatenate(grp)
+
+
+def batch_cylinders(specs):
+    """Meshes, free streams and initial states of a batched cylinder sweep."""
+    meshes, winf = [], []
+    for s in specs:
+        meshes.append(cylinder_mesh(n_theta=s["n_theta"], n_r=s["n_r"], ratio=s["ratio"], n_refine=2))
+        winf.append(freestream(s["mach"]))
+    union, grp = concat_meshes(meshes)
+    W = np.asarray(winf)[grp]
+    return union, grp, np.asarray(winf), W
