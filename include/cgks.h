@@ -259,6 +259,27 @@ int cgks_vcycle_groups(cgks_t* h, int mesh_id, int n_cycles, int mode, double* n
  * update).  Captured graphs are rebuilt on the next V-cycle. */
 int cgks_autotune(cgks_t* h, int mesh_id, int* blocks_out);
 
+/*
+ * Coarse-level KFVS residual that allocates nothing.  (The paper has no
+ * counterpart; this is a service to callers.)  Same result as
+ * cgks_residual(h, mesh_id, level, W, R, NULL, NULL, 1) for level >= 1, for
+ * callers that cannot let a call allocate device memory, e.g. an application
+ * that has planned all GPU memory up front, or a latency-critical loop where
+ * cudaMalloc / cudaFree would add an implicit device synchronisation.
+ *   W_dev [n_level][nv] (device, original coarse-cell order, read),
+ *   R_dev [n_level][nv] (device, original order, written): outward KFVS flux
+ *   of each coarse cell.
+ * The per-face fluxes go to a fixed device array of 131,072 faces x 5 FP64
+ * values (5 MiB) that every GPU loading the library holds until process exit;
+ * levels with more faces are rejected with CGKS_ERR_ARG.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make
+ * the first call on each device before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other contexts of
+ * this library) race and must be serialised by the caller.  Work is enqueued on
+ * the context's stream without synchronising.
+ */
+int cgks_residual_coarse_noalloc(cgks_t* h, int mesh_id, int level, const double* W_dev, double* R_dev);
+
 /* Waits for all work of h on its stream. */
 int cgks_synchronize(cgks_t* h);
 

@@ -28,7 +28,7 @@ EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_erro
            "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
            "cgks_gks_points", "cgks_kfvs_points", "cgks_run_stage", "cgks_launch_count",
            "cgks_vcycle_launch", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
-           "cgks_autotune",
+           "cgks_autotune", "cgks_residual_coarse_noalloc",
            "cgks_synchronize"]
 
 
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH):
         "cgks_set_groups": [P, I, I, P, P],
         "cgks_vcycle_groups": [P, I, I, I, P, P, P],
         "cgks_autotune": [P, I, P],
+        "cgks_residual_coarse_noalloc": [P, I, I, P, P],
         "cgks_launch_count": [P, I, I, P],
         "cgks_synchronize": [P],
     }
@@ -280,6 +281,13 @@ class Context:
         out = np.zeros(7, np.int32)
         self._check(self._L.cgks_autotune(self.h, mesh_id, _ptr(out)))
         return out
+
+    def cgks_residual_coarse_noalloc(self, mesh_id: int, level: int, W_dev, R_dev, check: bool = True):
+        """Coarse KFVS residual into a caller device buffer without any allocation."""
+        rc = self._L.cgks_residual_coarse_noalloc(self.h, mesh_id, level, _ptr(W_dev), _ptr(R_dev))
+        if check:
+            self._check(rc)
+        return rc
 
     def cgks_run_stage(self, mesh_id: int, stage: int):
         self._check(self._L.cgks_run_stage(self.h, mesh_id, stage))

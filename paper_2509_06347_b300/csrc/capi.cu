@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -585,6 +586,7 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
   *out = nullptr;
   cgks_t* h = new (std::nothrow) cgks_ctx();
   if (!h) return CGKS_ERR_CUDA;
+  h->err.reserve(512);  // error messages of the no-allocation entry point fit without reallocating
   if (cfg) h->cfg = *cfg;
   else cgks_default_config(&h->cfg);
   if (h->cfg.n_pre != 1 || h->cfg.n_post != 0 || h->cfg.n_sweep_coarse < 1 || !(h->cfg.gamma > 1.0) ||
@@ -1284,3 +1286,132 @@ int cgks_kfvs_points(cgks_t* h, int dim, int64_t n, const double* Wl, const doub
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Coarse KFVS residual without any allocation.
+//
+// Some callers cannot let a library call allocate device memory: for example
+// an application that pre-plans every byte of the GPU before its time loop, or
+// a caller on a latency-critical path where cudaMalloc / cudaFree would add an
+// implicit device-wide synchronisation.  This variant of the coarse residual
+// (cgks_residual with level >= 1) therefore keeps its only scratch buffer, the
+// per-face flux, in a fixed device array that lives in this library from load
+// to process exit, and reads and writes the caller's buffers directly.
+// ===========================================================================
+namespace cgks {
+namespace noalloc {
+
+// Capacity of the face-flux scratch: 131,072 faces x 5 conservative variables
+// of FP64 (5 MiB).  Every GPU that loads the library holds this array.
+constexpr int kNoAllocMaxFaces = 131072;
+static __device__ __align__(256) double g_noalloc_face_flux[kNoAllocMaxFaces * 5];
+
+// device address of g_noalloc_face_flux, looked up once per device
+constexpr int kMaxDevices = 64;
+static double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_noalloc_face(FaceSet Fs, const int* __restrict__ iperm,
+                                                         const double* __restrict__ W_orig,
+                                                         const double* __restrict__ winf, PhysParams P,
+                                                         double* __restrict__ Fout) {
+  constexpr int NV = DIM + 2;
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= Fs.nf) return;
+  const int L = Fs.fL[f], R = Fs.fR[f];
+  double n[DIM], WL[NV], WR[NV];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) n[d] = Fs.fn[(size_t)f * DIM + d];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) WL[v] = W_orig[(size_t)iperm[L] * NV + v];
+  if (R >= 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) WR[v] = W_orig[(size_t)iperm[R] * NV + v];
+  } else {
+    ghost_state<DIM>(Fs.ftag[f], winf + NV * (Fs.grp ? Fs.grp[L] : 0), n, WL, WR);
+  }
+  const Frame<DIM> fr = make_frame<DIM>(n);
+  double wl[NV], wr[NV], Fl[NV], Fg[NV];
+  to_local<DIM>(fr, WL, wl);
+  to_local<DIM>(fr, WR, wr);
+  kfvs_flux<DIM>(P, wl, wr, Fl);
+  to_global<DIM>(fr, Fl, Fg);
+  const double S = Fs.fS[f];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fout[(size_t)f * NV + v] = S * Fg[v];
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_noalloc_cell(Topo Tp, const int* __restrict__ iperm,
+                                                         const double* __restrict__ Fface,
+                                                         double* __restrict__ R_orig) {
+  constexpr int NV = DIM + 2;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Tp.n) return;
+  double r[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) r[v] = 0.0;
+  for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) {
+    const int f = Tp.face[e];
+    const double sd = Tp.side[e];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) r[v] += sd * Fface[(size_t)f * NV + v];
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) R_orig[(size_t)iperm[c] * NV + v] = r[v];
+}
+
+int noalloc_fail(cgks_t* h, int code, const char* msg) {
+  h->err.assign(msg);  // within the capacity reserved at cgks_create
+  return code;
+}
+
+}  // namespace noalloc
+}  // namespace cgks
+
+using namespace cgks::noalloc;
+
+extern "C" int cgks_residual_coarse_noalloc(cgks_t* h, int mesh_id, int level, const double* W_dev,
+                                            double* R_dev) {
+  if (!h) return CGKS_ERR_ARG;
+  auto it = h->meshes.find(mesh_id);
+  if (it == h->meshes.end()) return noalloc_fail(h, CGKS_ERR_ARG, "unknown mesh id");
+  MeshDev& M = *it->second;
+  if (!M.has_hierarchy || M.winf_h.empty())
+    return noalloc_fail(h, CGKS_ERR_STATE, "mesh hierarchy or free stream not set");
+  if (level < 1 || level >= M.nlev || !W_dev || !R_dev)
+    return noalloc_fail(h, CGKS_ERR_ARG, "level must be a coarse level (>= 1) and buffers non-null");
+  LevelDev& L = M.lev[level];
+  if (L.faces.nf > kNoAllocMaxFaces)
+    return noalloc_fail(h, CGKS_ERR_ARG,
+                        "cgks_residual_coarse_noalloc: the level has more than 131072 faces, the capacity "
+                        "of the fixed face-flux buffer; use cgks_residual instead");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return noalloc_fail(h, CGKS_ERR_CUDA, "cudaGetDevice failed or device index too large");
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // first call on this device: resolve the array's device address with the device current
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_face_flux);
+      if (e != cudaSuccess) return noalloc_fail(h, CGKS_ERR_CUDA, "cudaGetSymbolAddress failed");
+      g_noalloc_ptr[dev] = (double*)p;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  // every face entry the cell kernel reads is written by the face kernel first,
+  // so the buffer needs no clearing between calls
+  const PhysParams p = phys(h->cfg, M.dim);
+  if (M.dim == 2) {
+    k_noalloc_face<2><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.iperm, W_dev, M.winf, p, scratch);
+    k_noalloc_cell<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.iperm, scratch, R_dev);
+  } else {
+    k_noalloc_face<3><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.iperm, W_dev, M.winf, p, scratch);
+    k_noalloc_cell<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.iperm, scratch, R_dev);
+  }
+  if (cudaGetLastError() != cudaSuccess) return noalloc_fail(h, CGKS_ERR_CUDA, "kernel launch failed");
+  return CGKS_OK;
+}
