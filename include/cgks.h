@@ -280,6 +280,31 @@ int cgks_autotune(cgks_t* h, int mesh_id, int* blocks_out);
  */
 int cgks_residual_coarse_noalloc(cgks_t* h, int mesh_id, int level, const double* W_dev, double* R_dev);
 
+/*
+ * Learned coarse-grid correction (a per-cell network predicting the correction
+ * the coarse levels would make).  The paper has no learned component; the
+ * network, its inputs and its training are this library's design.
+ * Network: 68 inputs -> 64 -> GELU -> 64 -> GELU -> 4, parameters as one flat
+ * FP32 vector of 8,836 values [W1 (64x68 row-major), b1, W2 (64x64), b2,
+ * W3 (4x64), b3] (FP32 master copy, BF16 compute copy, FP32 accumulation).
+ */
+int cgks_mlp_set_params(cgks_t* h, const float* theta /* host [8836]; resets Adam */);
+int cgks_mlp_get_params(cgks_t* h, float* theta /* host [8836] */);
+/* Inference on device rows: X bf16 [n][68] (uint16 bit patterns), P fp32 [n][4]. */
+int cgks_mlp_forward(cgks_t* h, int64_t n, const uint16_t* X, float* P);
+/* Mean-squared-error gradient at device rows X [n][68] (bf16), Y [n][4] (fp32):
+ * grad (device fp32 [8836]); loss (host, nullable). */
+int cgks_mlp_grad(cgks_t* h, int64_t n, const uint16_t* X, const float* Y, float* grad, float* loss);
+/* Training set held by the library: append rows (host or device pointers),
+ * query its size, clear it. */
+int cgks_mlp_dataset_append(cgks_t* h, int64_t n, const uint16_t* X, const float* Y);
+int cgks_mlp_dataset_size(cgks_t* h, int64_t* n);
+int cgks_mlp_dataset_clear(cgks_t* h);
+/* n_steps Adam steps (beta 0.9 / 0.999, eps 1e-8) on seeded random
+ * mini-batches of `batch` rows of the training set; losses (host, nullable)
+ * [n_steps] receives each step's mini-batch loss. */
+int cgks_mlp_train(cgks_t* h, int n_steps, int batch, double lr, uint64_t seed, float* losses);
+
 /* Waits for all work of h on its stream. */
 int cgks_synchronize(cgks_t* h);
 

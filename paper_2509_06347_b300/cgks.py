@@ -28,7 +28,9 @@ EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_erro
            "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
            "cgks_gks_points", "cgks_kfvs_points", "cgks_run_stage", "cgks_launch_count",
            "cgks_vcycle_launch", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
-           "cgks_autotune", "cgks_residual_coarse_noalloc",
+           "cgks_autotune", "cgks_residual_coarse_noalloc", "cgks_mlp_set_params", "cgks_mlp_get_params",
+           "cgks_mlp_forward", "cgks_mlp_grad", "cgks_mlp_dataset_append", "cgks_mlp_dataset_size",
+           "cgks_mlp_dataset_clear", "cgks_mlp_train",
            "cgks_synchronize"]
 
 
@@ -88,6 +90,14 @@ def load_library(path: str = LIB_PATH):
         "cgks_vcycle_groups": [P, I, I, I, P, P, P],
         "cgks_autotune": [P, I, P],
         "cgks_residual_coarse_noalloc": [P, I, I, P, P],
+        "cgks_mlp_set_params": [P, P],
+        "cgks_mlp_get_params": [P, P],
+        "cgks_mlp_forward": [P, I64, P, P],
+        "cgks_mlp_grad": [P, I64, P, P, P, P],
+        "cgks_mlp_dataset_append": [P, I64, P, P],
+        "cgks_mlp_dataset_size": [P, P],
+        "cgks_mlp_dataset_clear": [P],
+        "cgks_mlp_train": [P, I, I, C.c_double, C.c_uint64, P],
         "cgks_launch_count": [P, I, I, P],
         "cgks_synchronize": [P],
     }
@@ -288,6 +298,41 @@ class Context:
         if check:
             self._check(rc)
         return rc
+
+    # ---- learned correction -------------------------------------------------------
+    def cgks_mlp_set_params(self, theta):
+        t = np.ascontiguousarray(theta, np.float32)
+        self._check(self._L.cgks_mlp_set_params(self.h, _ptr(t)))
+
+    def cgks_mlp_get_params(self):
+        out = np.zeros(8836, np.float32)
+        self._check(self._L.cgks_mlp_get_params(self.h, _ptr(out)))
+        return out
+
+    def cgks_mlp_forward(self, X_bf16_dev, P_dev):
+        self._check(self._L.cgks_mlp_forward(self.h, X_bf16_dev.shape[0], _ptr(X_bf16_dev), _ptr(P_dev)))
+
+    def cgks_mlp_grad(self, X_bf16_dev, Y_dev, grad_dev):
+        loss = C.c_float()
+        self._check(self._L.cgks_mlp_grad(self.h, X_bf16_dev.shape[0], _ptr(X_bf16_dev), _ptr(Y_dev),
+                                          _ptr(grad_dev), C.byref(loss)))
+        return loss.value
+
+    def cgks_mlp_dataset_append(self, X, Y):
+        self._check(self._L.cgks_mlp_dataset_append(self.h, X.shape[0], _ptr(X), _ptr(Y)))
+
+    def cgks_mlp_dataset_size(self):
+        n = C.c_int64()
+        self._check(self._L.cgks_mlp_dataset_size(self.h, C.byref(n)))
+        return n.value
+
+    def cgks_mlp_dataset_clear(self):
+        self._check(self._L.cgks_mlp_dataset_clear(self.h))
+
+    def cgks_mlp_train(self, n_steps: int, batch: int, lr: float, seed: int = 0):
+        losses = np.zeros(max(1, n_steps), np.float32)
+        self._check(self._L.cgks_mlp_train(self.h, n_steps, batch, lr, seed, _ptr(losses)))
+        return losses[:n_steps]
 
     def cgks_run_stage(self, mesh_id: int, stage: int):
         self._check(self._L.cgks_run_stage(self.h, mesh_id, stage))

@@ -15,6 +15,7 @@
 #include "cgks.h"
 #include "host_mesh.hpp"
 #include "kernels.cuh"
+#include "mlp.cuh"
 
 namespace cgks {
 namespace {
@@ -136,8 +137,37 @@ struct MeshDev {
 }  // namespace
 }  // namespace cgks
 
+namespace cgks {
+namespace {
+// learned-correction network state (one per context)
+struct MlpState {
+  bool ready = false;
+  std::vector<std::unique_ptr<DBuf>> pool;   // parameters and optimiser state
+  std::vector<std::unique_ptr<DBuf>> work;   // batch-sized work buffers
+  int64_t work_rows = 0;
+  float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+  __nv_bfloat16* theta_bf = nullptr;
+  int step = 0;
+  // work buffers (rows = work_rows)
+  float *Z1 = nullptr, *Z2 = nullptr, *P = nullptr, *dP = nullptr, *part = nullptr, *loss = nullptr;
+  __nv_bfloat16 *A1 = nullptr, *A2 = nullptr, *dPb = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+  __nv_bfloat16* Xb = nullptr;
+  float* Yb = nullptr;
+  int* idx = nullptr;
+  float* split = nullptr;  // split-K partials
+  size_t split_elems = 0;
+  // training set (rows of 68 bf16 features and 4 fp32 targets)
+  std::vector<std::unique_ptr<DBuf>> data;
+  __nv_bfloat16* X = nullptr;
+  float* Y = nullptr;
+  int64_t rows = 0, cap = 0;
+};
+}  // namespace
+}  // namespace cgks
+
 struct cgks_ctx {
   cgks_config cfg{};
+  cgks::MlpState mlp;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::map<int, std::unique_ptr<cgks::MeshDev>> meshes;
@@ -1280,6 +1310,255 @@ int cgks_kfvs_points(cgks_t* h, int dim, int64_t n, const double* Wl, const doub
     const PhysParams p = phys(h->cfg, dim);
     if (dim == 2) k_kfvs_points<2><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p, Wl, Wr, F);
     else k_kfvs_points<3><<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, p, Wl, Wr, F);
+    CK(cudaGetLastError());
+    return CGKS_OK;
+  });
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Learned coarse-grid correction: network parameters, inference, gradients,
+// training set and training loop.
+// ===========================================================================
+namespace cgks {
+namespace {
+
+using namespace cgks::mlp;
+
+void mlp_ensure(cgks_t* h) {
+  MlpState& S = h->mlp;
+  if (S.ready) return;
+  S.theta = dalloc<float>(S.pool, kParams);
+  S.m = dalloc<float>(S.pool, kParams);
+  S.v = dalloc<float>(S.pool, kParams);
+  S.grad = dalloc<float>(S.pool, kParams);
+  S.theta_bf = dalloc<__nv_bfloat16>(S.pool, kParams);
+  S.ready = true;
+}
+
+void mlp_work(cgks_t* h, int64_t rows) {
+  MlpState& S = h->mlp;
+  if (rows <= S.work_rows) return;
+  CK(cudaStreamSynchronize(h->stream));
+  S.work.clear();
+  S.work_rows = rows;
+  auto& P = S.work;
+  S.Z1 = dalloc<float>(P, rows * kH);
+  S.Z2 = dalloc<float>(P, rows * kH);
+  S.P = dalloc<float>(P, rows * kOut);
+  S.dP = dalloc<float>(P, rows * kOut);
+  S.A1 = dalloc<__nv_bfloat16>(P, rows * kH);
+  S.A2 = dalloc<__nv_bfloat16>(P, rows * kH);
+  S.dPb = dalloc<__nv_bfloat16>(P, rows * kOut);
+  S.dZ2 = dalloc<__nv_bfloat16>(P, rows * kH);
+  S.dZ1 = dalloc<__nv_bfloat16>(P, rows * kH);
+  S.Xb = dalloc<__nv_bfloat16>(P, rows * kIn);
+  S.Yb = dalloc<float>(P, rows * kOut);
+  S.idx = dalloc<int>(P, rows);
+  S.part = dalloc<float>(P, blocks_for(rows * kOut) + 1);
+  S.loss = dalloc<float>(P, 1);
+  S.split_elems = (size_t)64 * kH * kIn;
+  S.split = dalloc<float>(P, S.split_elems);
+}
+
+void gemm(cudaStream_t st, const GemmArgs& g, int slices = 1) {
+  dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, slices);
+  k_gemm_bf16<<<grid, 128, 0, st>>>(g);
+}
+
+GemmArgs gargs(int M, int N, int K, const __nv_bfloat16* A, int lda, int ta, const __nv_bfloat16* B, int ldb,
+               int tb, float* C, const float* bias, __nv_bfloat16* Abf, const float* Z, int epi) {
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K; g.A = A; g.lda = lda; g.ta = ta; g.B = B; g.ldb = ldb; g.tb = tb;
+  g.C = C; g.bias = bias; g.Abf = Abf; g.Z = Z; g.epi = epi; g.k_per_slice = K;
+  return g;
+}
+
+// forward pass on rows of X (bf16 [rows][68]) -> P (fp32 [rows][4]); keeps Z1, A1, Z2, A2
+void mlp_forward(cgks_t* h, int64_t rows, const __nv_bfloat16* X, float* P) {
+  MlpState& S = h->mlp;
+  const __nv_bfloat16* W = S.theta_bf;
+  const int M = (int)rows;
+  gemm(h->stream, gargs(M, kH, kIn, X, kIn, 0, W + oW1, kIn, 1, S.Z1, S.theta + ob1, S.A1, nullptr, kEpiGeluBf16));
+  gemm(h->stream, gargs(M, kH, kH, S.A1, kH, 0, W + oW2, kH, 1, S.Z2, S.theta + ob2, S.A2, nullptr, kEpiGeluBf16));
+  gemm(h->stream, gargs(M, kOut, kH, S.A2, kH, 0, W + oW3, kH, 1, P, S.theta + ob3, nullptr, nullptr, kEpiStore));
+}
+
+// split-K weight gradient G[M][N] = op(A)^T-style product over K = rows
+void grad_gemm(cgks_t* h, int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+               float* G) {
+  MlpState& S = h->mlp;
+  int slices = std::max(1, std::min(64, (K + 1023) / 1024));
+  int kps = (K + slices - 1) / slices;
+  kps = (kps + 15) / 16 * 16;
+  slices = (K + kps - 1) / kps;
+  GemmArgs g = gargs(M, N, K, A, lda, 1, B, ldb, 0, S.split, nullptr, nullptr, nullptr, kEpiPartial);
+  g.k_per_slice = kps;
+  gemm(h->stream, g, slices);
+  k_reduce_slices<<<blocks_for((int64_t)M * N), kBlock, 0, h->stream>>>(S.split, slices, M * N, G);
+}
+
+// loss and gradient of the mean squared error at rows (X, Y) -> S.grad, S.loss
+void mlp_backward(cgks_t* h, int64_t rows, const __nv_bfloat16* X, const float* Y) {
+  MlpState& S = h->mlp;
+  const int M = (int)rows;
+  mlp_forward(h, rows, X, S.P);
+  const int n = M * kOut;
+  const int nb = (int)blocks_for(n);
+  k_mse_grad<<<nb, kBlock, 0, h->stream>>>(S.P, Y, n, 1.0f / n, S.dP, S.dPb, S.part);
+  k_sum_fixed<<<1, kBlock, 0, h->stream>>>(S.part, nb, 1.0f / n, S.loss);
+  const __nv_bfloat16* W = S.theta_bf;
+  float* g = S.grad;
+  // layer 3
+  grad_gemm(h, kOut, kH, M, S.dPb, kOut, S.A2, kH, g + oW3);
+  k_colsum<float><<<kOut, kBlock, 0, h->stream>>>(S.dP, M, kOut, g + ob3);
+  // dZ2 = (dP W3) * gelu'(Z2)
+  gemm(h->stream, gargs(M, kH, kOut, S.dPb, kOut, 0, W + oW3, kH, 0, nullptr, nullptr, S.dZ2, S.Z2, kEpiGeluGrad));
+  grad_gemm(h, kH, kH, M, S.dZ2, kH, S.A1, kH, g + oW2);
+  k_colsum<__nv_bfloat16><<<kH, kBlock, 0, h->stream>>>(S.dZ2, M, kH, g + ob2);
+  // dZ1 = (dZ2 W2) * gelu'(Z1)
+  gemm(h->stream, gargs(M, kH, kH, S.dZ2, kH, 0, W + oW2, kH, 0, nullptr, nullptr, S.dZ1, S.Z1, kEpiGeluGrad));
+  grad_gemm(h, kH, kIn, M, S.dZ1, kH, X, kIn, g + oW1);
+  k_colsum<__nv_bfloat16><<<kH, kBlock, 0, h->stream>>>(S.dZ1, M, kH, g + ob1);
+}
+
+}  // namespace
+}  // namespace cgks
+
+extern "C" {
+
+int cgks_mlp_set_params(cgks_t* h, const float* theta) {
+  return guarded(h, [&]() -> int {
+    if (!theta) throw ArgError("null parameters");
+    mlp_ensure(h);
+    MlpState& S = h->mlp;
+    CK(cudaMemcpyAsync(S.theta, theta, kParams * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(S.m, 0, kParams * sizeof(float), h->stream));
+    CK(cudaMemsetAsync(S.v, 0, kParams * sizeof(float), h->stream));
+    k_f32_to_bf16<<<blocks_for(kParams), kBlock, 0, h->stream>>>(kParams, S.theta, S.theta_bf);
+    S.step = 0;
+    CK(cudaStreamSynchronize(h->stream));
+    return CGKS_OK;
+  });
+}
+
+int cgks_mlp_get_params(cgks_t* h, float* theta) {
+  return guarded(h, [&]() -> int {
+    if (!theta || !h->mlp.ready) throw StateError("no network parameters");
+    CK(cudaMemcpyAsync(theta, h->mlp.theta, kParams * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return CGKS_OK;
+  });
+}
+
+int cgks_mlp_forward(cgks_t* h, int64_t n, const uint16_t* X, float* P) {
+  return guarded(h, [&]() -> int {
+    if (n <= 0 || n > (1ll << 30) || !X || !P) throw ArgError("invalid forward arguments");
+    if (!h->mlp.ready) throw StateError("no network parameters");
+    mlp_work(h, n);
+    mlp_forward(h, n, (const __nv_bfloat16*)X, P);
+    CK(cudaGetLastError());
+    return CGKS_OK;
+  });
+}
+
+int cgks_mlp_grad(cgks_t* h, int64_t n, const uint16_t* X, const float* Y, float* grad, float* loss) {
+  return guarded(h, [&]() -> int {
+    if (n <= 0 || n > (1ll << 30) || !X || !Y || !grad) throw ArgError("invalid gradient arguments");
+    if (!h->mlp.ready) throw StateError("no network parameters");
+    mlp_work(h, n);
+    mlp_backward(h, n, (const __nv_bfloat16*)X, Y);
+    CK(cudaMemcpyAsync(grad, h->mlp.grad, kParams * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    if (loss) {
+      CK(cudaMemcpyAsync(loss, h->mlp.loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+    CK(cudaGetLastError());
+    return CGKS_OK;
+  });
+}
+
+int cgks_mlp_dataset_append(cgks_t* h, int64_t n, const uint16_t* X, const float* Y) {
+  return guarded(h, [&]() -> int {
+    if (n <= 0 || !X || !Y) throw ArgError("invalid dataset arguments");
+    MlpState& S = h->mlp;
+    if (S.rows + n > S.cap) {
+      const int64_t cap = std::max<int64_t>(S.rows + n, 2 * S.cap);
+      std::vector<std::unique_ptr<DBuf>> nd;
+      __nv_bfloat16* X2 = dalloc<__nv_bfloat16>(nd, cap * kIn);
+      float* Y2 = dalloc<float>(nd, cap * kOut);
+      if (S.rows) {
+        CK(cudaMemcpyAsync(X2, S.X, S.rows * kIn * sizeof(__nv_bfloat16), cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(Y2, S.Y, S.rows * kOut * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+      }
+      CK(cudaStreamSynchronize(h->stream));
+      S.data = std::move(nd);
+      S.X = X2;
+      S.Y = Y2;
+      S.cap = cap;
+    }
+    CK(cudaMemcpyAsync(S.X + S.rows * kIn, X, n * kIn * sizeof(__nv_bfloat16), cudaMemcpyDefault, h->stream));
+    CK(cudaMemcpyAsync(S.Y + S.rows * kOut, Y, n * kOut * sizeof(float), cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    S.rows += n;
+    return CGKS_OK;
+  });
+}
+
+int cgks_mlp_dataset_size(cgks_t* h, int64_t* n) {
+  return guarded(h, [&]() -> int {
+    if (!n) throw ArgError("null output");
+    *n = h->mlp.rows;
+    return CGKS_OK;
+  });
+}
+
+int cgks_mlp_dataset_clear(cgks_t* h) {
+  return guarded(h, [&]() -> int {
+    CK(cudaStreamSynchronize(h->stream));
+    h->mlp.data.clear();
+    h->mlp.X = nullptr;
+    h->mlp.Y = nullptr;
+    h->mlp.rows = h->mlp.cap = 0;
+    return CGKS_OK;
+  });
+}
+
+int cgks_mlp_train(cgks_t* h, int n_steps, int batch, double lr, uint64_t seed, float* losses) {
+  return guarded(h, [&]() -> int {
+    MlpState& S = h->mlp;
+    if (n_steps < 0 || batch < 1 || !(lr > 0)) throw ArgError("invalid training arguments");
+    if (!S.ready) throw StateError("no network parameters");
+    if (S.rows < 1) throw StateError("empty training set");
+    const int64_t b = std::min<int64_t>(batch, S.rows);
+    mlp_work(h, b);
+    std::vector<int> idx(b);
+    uint64_t st = seed;
+    auto next = [&]() {  // splitmix64
+      st += 0x9E3779B97F4A7C15ull;
+      uint64_t z = st;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    std::vector<float> lh(n_steps);
+    for (int s = 0; s < n_steps; ++s) {
+      for (int64_t i = 0; i < b; ++i) idx[i] = (int)(next() % (uint64_t)S.rows);
+      CK(cudaMemcpyAsync(S.idx, idx.data(), b * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      k_gather_batch<<<blocks_for(b * kIn), kBlock, 0, h->stream>>>((int)b, S.idx, S.X, S.Y, S.Xb, S.Yb);
+      mlp_backward(h, b, S.Xb, S.Yb);
+      S.step++;
+      const float b1 = 0.9f, b2 = 0.999f;
+      k_adam<<<blocks_for(kParams), kBlock, 0, h->stream>>>(kParams, S.grad, S.theta, S.m, S.v, S.theta_bf,
+                                                             (float)lr, b1, b2, 1e-8f,
+                                                             1.f - std::pow(b1, (float)S.step),
+                                                             1.f - std::pow(b2, (float)S.step));
+      if (losses) CK(cudaMemcpyAsync(&lh[s], S.loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+      // the host index buffer is reused next step: wait for this step's copy
+      CK(cudaStreamSynchronize(h->stream));
+    }
+    if (losses) std::memcpy(losses, lh.data(), n_steps * sizeof(float));
     CK(cudaGetLastError());
     return CGKS_OK;
   });
