@@ -247,6 +247,8 @@ static void solve_slope(const Maxw* g, int dim, const double* b, double* a) {
   for (int i = 0; i < nv; ++i) a[i] = B[i];
 }
 
+static void kfvs_point(int dim, double gamma, const double* Wl, const double* Wr, double* F);
+
 /* ------------------------------------------------------------------------ */
 /* gas-kinetic interface flux at one Gauss point, local frame (Sec 2.3)      */
 /* ------------------------------------------------------------------------ */
@@ -297,6 +299,19 @@ static void gks_point(int dim, double gamma, double c1, double c2, const double*
   /* equilibrium state at the interface from half-space moments (Eq. compatibility2) */
   double Wc[MAXV], pc[MAXV];
   for (int i = 0; i < nv; ++i) Wc[i] = poly_mom(&glp, &psi[i]) + poly_mom(&grm, &psi[i]);
+  {
+    /* reading (vacuum, not treated by the paper): when both sides move apart so
+     * fast that the half-space moments give no admissible equilibrium, the
+     * point takes the collisionless limit: KFVS flux, point value W^c */
+    double pwl = pressure(dim, gamma, Wl), pwr = pressure(dim, gamma, Wr);
+    double pwc = pressure(dim, gamma, Wc);
+    if (!(Wc[0] > 1e-10 * (Wl[0] + Wr[0])) || !(pwc > 1e-10 * (pwl + pwr))) {
+      kfvs_point(dim, gamma, Wl, Wr, Fbar);
+      for (int i = 0; i < nv; ++i) Wt[i] = Wc[i];
+      if (dbg) memset(dbg, 0, sizeof(*dbg));
+      return;
+    }
+  }
   to_prim(dim, gamma, Wc, pc);
   Maxw gc;
   maxw_init(&gc, dim, K, pc, 0);

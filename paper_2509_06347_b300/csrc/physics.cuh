@@ -234,6 +234,26 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
   psi_mom<DIM, 0, 0, 0>(mr, t);
 #pragma unroll
   for (int i = 0; i < NV; ++i) Wc[i] = pl.rho * Wc[i] + pr.rho * t[i];
+  {
+    // vacuum (both sides moving apart): no admissible interface equilibrium;
+    // take the collisionless limit, i.e. the KFVS flux, point value W^c
+    double kc = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) kc += Wc[1 + d] * Wc[1 + d];
+    const double pwc = (P.gamma - 1.0) * (Wc[DIM + 1] - 0.5 * kc / Wc[0]);
+    const double pwl = pl.rho * pl.h, pwr = pr.rho * pr.h;  // p = rho / (2 lambda)
+    if (!(Wc[0] > 1e-10 * (pl.rho + pr.rho)) || !(pwc > 1e-10 * (pwl + pwr))) {
+      double a[NV], b[NV];
+      psi_mom<DIM, 1, 0, 0>(ml, a);
+      psi_mom<DIM, 1, 0, 0>(mr, b);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        F[i] = pl.rho * a[i] + pr.rho * b[i];
+        Wt[i] = Wc[i];
+      }
+      return;
+    }
+  }
   const Prim<DIM> pc = to_prim<DIM>(Wc, P);
   Mom<DIM> mc;
   tang_moments<DIM>(pc, K, mc);

@@ -266,3 +266,23 @@ def test_df_closed_form(dim):
     pr, mr = prim(Wr)
     D = abs(pl - pr) / pl + abs(pl - pr) / pr + (ml[0] - mr[0]) ** 2 + np.sum((ml[1:] - mr[1:]) ** 2)
     assert abs(oracle.df_point(dim, GAMMA, Wl, Wr) - 1 / (1 + D * D)) < 1e-15
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_vacuum_interface_takes_collisionless_limit(dim):
+    """Two states rushing apart (|u_n| sqrt(lambda) ~ 12): the half-space
+    moments leave no admissible interface equilibrium, and the point falls back
+    to the collisionless limit: finite, equal to the KFVS flux, and nearly zero
+    (nothing crosses the face)."""
+    nv = dim + 2
+    rho, p = 1e-3, 1e-4
+    u = np.zeros(dim)
+    u[0] = -4.0
+    Wl = np.concatenate([[rho], rho * u, [p / (GAMMA - 1) + 0.5 * rho * 16.0]])
+    Wr = Wl.copy()
+    Wr[1] = -Wl[1]
+    G = np.zeros((dim, nv))
+    F, Wt, _ = oracle.gks_point(dim, oracle.cfg_vector(dim), Wl, G, Wr, G, 0.1)
+    assert np.all(np.isfinite(F)) and np.all(np.isfinite(Wt))
+    np.testing.assert_allclose(F, oracle.kfvs_point(dim, GAMMA, Wl, Wr), rtol=0, atol=1e-30)
+    assert np.max(np.abs(F)) < 1e-30
