@@ -48,8 +48,11 @@ enum {
 /* V-cycle precision modes */
 enum {
   CGKS_PLAIN_FP64 = 0, /* everything in FP64 */
-  CGKS_MIXED = 1       /* LU-SGS sweeps and their corrections in FP32; residuals,
+  CGKS_MIXED = 1,      /* LU-SGS sweeps and their corrections in FP32; residuals,
                           DF factor and state updates in FP64 */
+  CGKS_LEARNED = 2     /* MIXED fine steps, then the network's predicted coarse
+                          correction where the DF factor >= cfg.df_gate instead
+                          of the coarse levels; plain V-cycle fallback (2-D) */
 };
 
 /* boundary tags */
@@ -75,6 +78,9 @@ typedef struct cgks_config {
                              implicit LU-SGS, DF ignored (ablation) (1) */
   int df_prolong;         /* 1: prolongation scaled by DF (Eq. prolongation); 0: plain
                              injection (ablation) (1) */
+  double df_gate;         /* learned correction applied only where DF >= df_gate (0.9) */
+  int learned_judge_every;   /* plain judge cycle every this many learned-mode cycles; 0 = never (20) */
+  double learned_max_error;  /* judge relative RMS error above which the network is disabled (0.5) */
 } cgks_config;
 
 typedef struct cgks_ctx cgks_t;
@@ -304,6 +310,21 @@ int cgks_mlp_dataset_clear(cgks_t* h);
  * mini-batches of `batch` rows of the training set; losses (host, nullable)
  * [n_steps] receives each step's mini-batch loss. */
 int cgks_mlp_train(cgks_t* h, int n_steps, int batch, double lr, uint64_t seed, float* losses);
+
+/* Runs n_cycles plain V-cycles of a 2-D mesh (advancing its state) and
+ * appends, for every cycle and fine cell, the network input (taken after the
+ * fine smoothing step) and the coarse correction the cycle then applied
+ * (scaled by the free stream) to the training set. */
+int cgks_mlp_collect(cgks_t* h, int mesh_id, int n_cycles, int mode);
+
+/* Learned-cycle statistics of the last cgks_vcycle(..., CGKS_LEARNED, ...):
+ * out[6] = learned cycles, plain cycles, judge cycles, stall fallbacks,
+ * network disabled (0/1), last judge relative RMS error (-1 if none).
+ * Policy: every 20th cycle (0, 20, 40, ...) is a plain "judge" cycle that also measures the
+ * network's error against the plain correction over gated cells (disabled
+ * above 0.5); a drop below 1 % over 5 learned cycles, or growth above 1.5x
+ * over one cycle, switches to 10 plain cycles. */
+int cgks_learned_stats(cgks_t* h, int mesh_id, double* out);
 
 /* Waits for all work of h on its stream. */
 int cgks_synchronize(cgks_t* h);

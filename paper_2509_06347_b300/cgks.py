@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libcgks.so")
 CGKS_OK = 0
 ERRORS = {-1: "CGKS_ERR_ARG", -2: "CGKS_ERR_MESH", -3: "CGKS_ERR_CUDA", -4: "CGKS_ERR_DIVERGED",
           -5: "CGKS_ERR_NONPOSITIVE", -6: "CGKS_ERR_TIMEOUT", -7: "CGKS_ERR_STATE"}
-PLAIN_FP64, MIXED = 0, 1
+PLAIN_FP64, MIXED, LEARNED = 0, 1, 2
 TAG_WALL, TAG_FARFIELD = 1, 2
 
 # every entry point declared in include/cgks.h
@@ -30,7 +30,7 @@ EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_erro
            "cgks_vcycle_launch", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
            "cgks_autotune", "cgks_residual_coarse_noalloc", "cgks_mlp_set_params", "cgks_mlp_get_params",
            "cgks_mlp_forward", "cgks_mlp_grad", "cgks_mlp_dataset_append", "cgks_mlp_dataset_size",
-           "cgks_mlp_dataset_clear", "cgks_mlp_train",
+           "cgks_mlp_dataset_clear", "cgks_mlp_train", "cgks_mlp_collect", "cgks_learned_stats",
            "cgks_synchronize"]
 
 
@@ -46,7 +46,8 @@ class Config(C.Structure):
                 ("weno_eps", C.c_double), ("r_safety", C.c_double), ("n_sweep_coarse", C.c_int),
                 ("n_pre", C.c_int), ("n_post", C.c_int), ("check_every", C.c_int), ("tol", C.c_double),
                 ("diverge_factor", C.c_double), ("fine_smoother", C.c_int), ("df_relax", C.c_int),
-                ("df_prolong", C.c_int)]
+                ("df_prolong", C.c_int), ("df_gate", C.c_double), ("learned_judge_every", C.c_int),
+                ("learned_max_error", C.c_double)]
 
 
 _lib = None
@@ -98,6 +99,8 @@ def load_library(path: str = LIB_PATH):
         "cgks_mlp_dataset_size": [P, P],
         "cgks_mlp_dataset_clear": [P],
         "cgks_mlp_train": [P, I, I, C.c_double, C.c_uint64, P],
+        "cgks_mlp_collect": [P, I, I, I],
+        "cgks_learned_stats": [P, I, P],
         "cgks_launch_count": [P, I, I, P],
         "cgks_synchronize": [P],
     }
@@ -333,6 +336,15 @@ class Context:
         losses = np.zeros(max(1, n_steps), np.float32)
         self._check(self._L.cgks_mlp_train(self.h, n_steps, batch, lr, seed, _ptr(losses)))
         return losses[:n_steps]
+
+    def cgks_mlp_collect(self, mesh_id: int, n_cycles: int, mode: int = PLAIN_FP64):
+        self._check(self._L.cgks_mlp_collect(self.h, mesh_id, n_cycles, mode))
+
+    def cgks_learned_stats(self, mesh_id: int):
+        out = np.zeros(6)
+        self._check(self._L.cgks_learned_stats(self.h, mesh_id, _ptr(out)))
+        return dict(learned=int(out[0]), plain=int(out[1]), judge=int(out[2]), fallbacks=int(out[3]),
+                    disabled=bool(out[4]), judge_error=float(out[5]))
 
     def cgks_run_stage(self, mesh_id: int, stage: int):
         self._check(self._L.cgks_run_stage(self.h, mesh_id, stage))

@@ -116,8 +116,15 @@ struct MeshDev {
   std::vector<double> winf_h;
   Counters* cnt = nullptr;
   std::vector<LevelDev> lev;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  int graph_kernels[2] = {0, 0};
+  cudaGraphExec_t graph[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};  // [plain, learned, judge][prec]
+  int graph_kernels[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  // learned correction buffers (fine level, colour order)
+  std::vector<std::unique_ptr<DBuf>> lpool;
+  __nv_bfloat16* X = nullptr;
+  float *Pl = nullptr, *Yl = nullptr;
+  double *Wsave = nullptr, *judge_part = nullptr, *judge_out = nullptr;
+  // learned-cycle policy statistics
+  double lstats[6] = {0, 0, 0, 0, 0, -1};  // learned, plain, judge, fallbacks, disabled, last judge error
   // batched members (groups of cells with their own free stream)
   int n_groups = 1;
   std::vector<std::unique_ptr<DBuf>> gpool;
@@ -128,10 +135,12 @@ struct MeshDev {
   std::vector<int> gcount;
   // launch block sizes per kernel class (autotuned)
   int blk[7] = {256, 256, 256, 256, 128, 128, 256};
-  ~MeshDev() {
-    for (auto& g : graph)
-      if (g) cudaGraphExecDestroy(g);
+  void drop_graphs() {
+    for (auto& k : graph)
+      for (auto& g : k)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   }
+  ~MeshDev() { drop_graphs(); }
 };
 
 }  // namespace
@@ -446,10 +455,10 @@ void coarse_forcing(cgks_t* h, MeshDev& M, LevelDev& L) {
                                                                     L.alpha, h->cfg.gamma, 0.0, 0.0, L.P, nullptr);
 }
 
+// steps 1-3 of the V-cycle: residual + slope update, fine smoothing, residual
 template <int DIM, typename T>
-void vcycle_body(cgks_t* h, MeshDev& M) {
+void vcycle_pre(cgks_t* h, MeshDev& M) {
   LevelDev& L0 = M.lev[0];
-  const PhysParams p = phys(h->cfg, DIM);
   // 1. residual, norms, slope update with DF, LU-SGS diagonal
   fine_residual<DIM>(h, M, true, true, true, true, nullptr, nullptr);
   // 2. pre-smoothing: one DF-relaxed LU-SGS step on -R, or the explicit update
@@ -462,7 +471,12 @@ void vcycle_body(cgks_t* h, MeshDev& M) {
   if (M.nlev == 1) return;
   // 3. residual at the smoothed state (no slope update); its DF is kept
   fine_residual<DIM>(h, M, false, false, false, false, nullptr, nullptr);
-  // 4-7. restriction, forcing, coarse smoothing
+}
+
+// steps 4-8: restriction, forcing, coarse smoothing, prolongation
+template <int DIM, typename T>
+void vcycle_coarse(cgks_t* h, MeshDev& M) {
+  if (M.nlev == 1) return;
   for (int l = 1; l < M.nlev; ++l) {
     LevelDev& F = M.lev[l - 1];
     LevelDev& C = M.lev[l];
@@ -475,7 +489,6 @@ void vcycle_body(cgks_t* h, MeshDev& M) {
     }
     if (l + 1 < M.nlev) coarse_prep<DIM>(h, M, C, C.P, false);  // R~ = R(W) + P to restrict
   }
-  // 8. prolongation, coarsest to fine
   for (int l = M.nlev - 1; l >= 1; --l) {
     LevelDev& F = M.lev[l - 1];
     LevelDev& C = M.lev[l];
@@ -487,23 +500,22 @@ void vcycle_body(cgks_t* h, MeshDev& M) {
   }
 }
 
-template <int DIM>
-void run_vcycle_body(cgks_t* h, MeshDev& M, int mode) {
-  if (mode == CGKS_MIXED) vcycle_body<DIM, float>(h, M);
-  else vcycle_body<DIM, double>(h, M);
+template <int DIM, typename T>
+void vcycle_body(cgks_t* h, MeshDev& M) {
+  vcycle_pre<DIM, T>(h, M);
+  vcycle_coarse<DIM, T>(h, M);
 }
 
-void enqueue_vcycle(cgks_t* h, MeshDev& M, int mode) {
-  if (M.dim == 2) run_vcycle_body<2>(h, M, mode);
-  else run_vcycle_body<3>(h, M, mode);
-}
+void enqueue_kind(cgks_t* h, MeshDev& M, int kind, int prec);
+void ensure_learned(cgks_t* h, MeshDev& M);
 
-cudaGraphExec_t get_graph(cgks_t* h, MeshDev& M, int mode) {
-  if (M.graph[mode]) return M.graph[mode];
+cudaGraphExec_t get_graph_kind(cgks_t* h, MeshDev& M, int kind, int prec) {
+  if (M.graph[kind][prec]) return M.graph[kind][prec];
+  if (kind > 0) ensure_learned(h, M);  // allocations are not allowed during capture
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   try {
-    enqueue_vcycle(h, M, mode);
+    enqueue_kind(h, M, kind, prec);
   } catch (...) {
     cudaStreamEndCapture(h->stream, &g);
     if (g) cudaGraphDestroy(g);
@@ -520,14 +532,16 @@ cudaGraphExec_t get_graph(cgks_t* h, MeshDev& M, int mode) {
     CK(cudaGraphNodeGetType(nd, &t));
     nk += t == cudaGraphNodeTypeKernel;
   }
-  M.graph_kernels[mode] = nk;
+  M.graph_kernels[kind][prec] = nk;
   cudaGraphExec_t ge;
   cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
   cudaGraphDestroy(g);
   CK(e);
-  M.graph[mode] = ge;
+  M.graph[kind][prec] = ge;
   return ge;
 }
+
+cudaGraphExec_t get_graph(cgks_t* h, MeshDev& M, int mode) { return get_graph_kind(h, M, 0, mode); }
 
 // ---- I/O with permutation ------------------------------------------------
 // copy caller rows (original order) into dst (device colour order)
@@ -582,6 +596,80 @@ int guarded(cgks_t* h, F&& f) {
   }
 }
 
+void enqueue_kind(cgks_t* h, MeshDev& M, int kind, int prec);
+
+// learned V-cycles with the fallback policy (host-side state machine)
+int run_learned(cgks_t* h, MeshDev& M, int n_cycles, double* norms_out, int* cycles_done) {
+  const int nv = M.nv;
+  cudaGraphExec_t gp = get_graph_kind(h, M, 0, CGKS_MIXED);
+  cudaGraphExec_t gl = get_graph_kind(h, M, 1, CGKS_MIXED);
+  cudaGraphExec_t gj = get_graph_kind(h, M, 2, CGKS_MIXED);
+  int start = 0;
+  CK(cudaMemcpyAsync(&start, M.cycle, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (double& x : M.lstats) x = 0;
+  M.lstats[5] = -1;
+  bool disabled = false;
+  int fallback = 0, done = 0, status = CGKS_OK;
+  std::vector<double> rho;      // RMS density residual per cycle
+  std::vector<char> learned;    // whether the cycle applied the network
+  double ref = -1.0;
+  for (int k = 0; k < n_cycles; ++k) {
+    const int je_every = h->cfg.learned_judge_every;
+    const bool judge = !disabled && fallback == 0 && je_every > 0 && k % je_every == 0;  // cycles 0, J, 2J, ...
+    const bool use_net = !disabled && fallback == 0 && !judge;
+    CK(cudaGraphLaunch(judge ? gj : (use_net ? gl : gp), h->stream));
+    double r = 0.0, je[2] = {0, 0};
+    const int idx = start + k;
+    if (idx < M.max_hist)
+      CK(cudaMemcpyAsync(&r, M.hist + (size_t)idx * 2 * nv, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (judge) CK(cudaMemcpyAsync(je, M.judge_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    done++;
+    rho.push_back(r);
+    learned.push_back(use_net);
+    if (ref < 0) ref = r;
+    M.lstats[use_net ? 0 : 1] += 1;
+    if (judge) {
+      M.lstats[2] += 1;
+      const double err = je[1] > 0 ? std::sqrt(je[0] / je[1]) : 0.0;
+      M.lstats[5] = err;
+      if (err > h->cfg.learned_max_error) disabled = true;
+    }
+    if (fallback > 0) fallback--;
+    // stall: the last five cycles all learned and less than 1 % drop, or 1.5x growth
+    const int n = (int)rho.size();
+    if (use_net && n >= 2 && rho[n - 1] > 1.5 * rho[n - 2]) {
+      fallback = 10;
+      M.lstats[3] += 1;
+    } else if (use_net && n >= 6) {
+      bool all = true;
+      for (int i = n - 5; i < n; ++i) all = all && learned[i];
+      if (all && rho[n - 1] > 0.99 * rho[n - 6]) {
+        fallback = 10;
+        M.lstats[3] += 1;
+      }
+    }
+    if (!std::isfinite(r) || (ref > 0 && r > h->cfg.diverge_factor * ref)) {
+      status = CGKS_ERR_DIVERGED;
+      break;
+    }
+    if (ref > 0 && r <= h->cfg.tol * ref) break;
+  }
+  M.lstats[4] = disabled ? 1 : 0;
+  if (norms_out) {
+    std::vector<double> hist((size_t)done * 2 * nv);
+    if (done)
+      CK(cudaMemcpy(hist.data(), M.hist + (size_t)start * 2 * nv, hist.size() * sizeof(double),
+                    cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n_cycles; ++i)
+      for (int j = 0; j < 2 * nv; ++j)
+        norms_out[(size_t)i * 2 * nv + j] = i < done ? hist[(size_t)i * 2 * nv + j] : -1.0;
+  }
+  if (cycles_done) *cycles_done = done;
+  return status;
+}
+
 }  // namespace
 }  // namespace cgks
 
@@ -608,6 +696,9 @@ int cgks_default_config(cgks_config* c) {
   c->fine_smoother = 0;
   c->df_relax = 1;
   c->df_prolong = 1;
+  c->df_gate = 0.9;
+  c->learned_judge_every = 20;
+  c->learned_max_error = 0.5;
   return CGKS_OK;
 }
 
@@ -686,8 +777,7 @@ int cgks_upload_hierarchy(cgks_t* h, int mesh_id, int n_levels, const int32_t* c
     MeshDev& M = get_mesh(h, mesh_id);
     if (n_levels < 1 || n_levels > 8 || (n_levels > 1 && !parent)) throw ArgError("invalid level count");
     M.H.coarse.clear();
-    for (auto& g : M.graph)
-      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    M.drop_graphs();
     try {
       for (int l = 1; l < n_levels; ++l) {
         if (!parent[l - 1]) throw ArgError("null parent array");
@@ -937,9 +1027,21 @@ int cgks_smooth(cgks_t* h, int mesh_id, int level, int n_sweeps) {
 int cgks_vcycle(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int mode, double* norms_out,
                 int* cycles_done) {
   return guarded(h, [&]() -> int {
-    if (!mesh_ids || n_meshes < 1 || n_cycles < 0 || (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED))
+    if (!mesh_ids || n_meshes < 1 || n_cycles < 0 ||
+        (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED && mode != CGKS_LEARNED))
       throw ArgError("invalid V-cycle arguments");
     int status = CGKS_OK;
+    if (mode == CGKS_LEARNED) {
+      for (int k = 0; k < n_meshes; ++k) {
+        MeshDev& M = get_mesh(h, mesh_ids[k]);
+        require_ready(M, true);
+        const int rc = run_learned(h, M, n_cycles, norms_out ? norms_out + (size_t)k * n_cycles * 2 * M.nv : nullptr,
+                                   cycles_done ? cycles_done + k : nullptr);
+        if (rc != CGKS_OK) status = rc;
+      }
+      if (status != CGKS_OK) h->err = "residual diverged or became non-finite";
+      return status;
+    }
     for (int k = 0; k < n_meshes; ++k) {
       MeshDev& M = get_mesh(h, mesh_ids[k]);
       require_ready(M, true);
@@ -1106,7 +1208,7 @@ int cgks_launch_count(cgks_t* h, int mesh_id, int mode, int* count) {
     require_ready(M, true);
     if (!count || (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED)) throw ArgError("invalid arguments");
     get_graph(h, M, mode);
-    *count = M.graph_kernels[mode];
+    *count = M.graph_kernels[0][mode];
     return CGKS_OK;
   });
 }
@@ -1166,8 +1268,7 @@ int cgks_set_groups(cgks_t* h, int mesh_id, int n_groups, const int32_t* group_o
     wb->alloc((size_t)n_groups * nv * sizeof(double));
     CK(cudaMemcpy(wb->p, winf, (size_t)n_groups * nv * sizeof(double), cudaMemcpyHostToDevice));
     M.winf = wb->as<double>();
-    for (auto& g : M.graph)
-      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    M.drop_graphs();
     CK(cudaDeviceSynchronize());
     return CGKS_OK;
   });
@@ -1295,8 +1396,7 @@ int cgks_autotune(cgks_t* h, int mesh_id, int* blocks_out) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaGetLastError());
-    for (auto& g : M.graph)
-      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    M.drop_graphs();
     if (blocks_out)
       for (int i = 0; i < 7; ++i) blocks_out[i] = M.blk[i];
     return CGKS_OK;
@@ -1423,8 +1523,104 @@ void mlp_backward(cgks_t* h, int64_t rows, const __nv_bfloat16* X, const float* 
   k_colsum<__nv_bfloat16><<<kH, kBlock, 0, h->stream>>>(S.dZ1, M, kH, g + ob1);
 }
 
+void ensure_learned(cgks_t* h, MeshDev& M) {
+  if (M.dim != 2) throw ArgError("the learned correction is implemented for 2-D meshes");
+  if (!h->mlp.ready) throw StateError("cgks_mlp_set_params has not been called");
+  const int64_t n = M.lev[0].n;
+  if (!M.X) {
+    M.X = dalloc<__nv_bfloat16>(M.lpool, n * kIn);
+    M.Pl = dalloc<float>(M.lpool, n * kOut);
+    M.Yl = dalloc<float>(M.lpool, n * kOut);
+    M.Wsave = dalloc<double>(M.lpool, n * M.nv);
+    M.judge_part = dalloc<double>(M.lpool, 2 * blocks_for(n));
+    M.judge_out = dalloc<double>(M.lpool, 2);
+  }
+  mlp_work(h, n);
+}
+
+void features(cgks_t* h, MeshDev& M) {
+  LevelDev& L = M.lev[0];
+  k_features2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.W, M.G, L.R, L.dti, L.alpha, M.winf, h->cfg.gamma,
+                                                          M.X);
+}
+
+template <typename T>
+void enqueue_learned(cgks_t* h, MeshDev& M, bool judge) {
+  LevelDev& L = M.lev[0];
+  vcycle_pre<2, T>(h, M);
+  features(h, M);
+  mlp_forward(h, L.n, M.X, M.Pl);
+  const int* grp = M.lgrp.empty() ? nullptr : M.lgrp[0];
+  if (!judge) {
+    k_apply_learned2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, M.Pl, L.alpha, h->cfg.df_gate, grp, M.winf,
+                                                                 M.lgrp.empty() ? nullptr : M.active, h->cfg.gamma,
+                                                                 L.W, M.cnt);
+    return;
+  }
+  CK(cudaMemcpyAsync(M.Wsave, L.W, (size_t)L.n * M.nv * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  vcycle_coarse<2, T>(h, M);
+  const int nb = (int)blocks_for(L.n);
+  k_judge2<<<nb, kBlock, 0, h->stream>>>(L.n, M.Pl, L.W, M.Wsave, L.alpha, h->cfg.df_gate, grp, M.winf, h->cfg.gamma,
+                                         M.judge_part);
+  k_judge_final<<<1, 1, 0, h->stream>>>(M.judge_part, nb, M.judge_out);
+}
+
+void enqueue_kind(cgks_t* h, MeshDev& M, int kind, int prec) {
+  if (kind == 0) {
+    if (M.dim == 2) {
+      if (prec == CGKS_MIXED) vcycle_body<2, float>(h, M);
+      else vcycle_body<2, double>(h, M);
+    } else {
+      if (prec == CGKS_MIXED) vcycle_body<3, float>(h, M);
+      else vcycle_body<3, double>(h, M);
+    }
+    return;
+  }
+  if (!M.X || h->mlp.work_rows < M.lev[0].n) throw StateError("learned buffers missing");
+  if (prec == CGKS_MIXED) enqueue_learned<float>(h, M, kind == 2);
+  else enqueue_learned<double>(h, M, kind == 2);
+}
+
 }  // namespace
 }  // namespace cgks
+
+extern "C" {
+
+int cgks_mlp_collect(cgks_t* h, int mesh_id, int n_cycles, int mode) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    if (n_cycles < 0 || (mode != CGKS_PLAIN_FP64 && mode != CGKS_MIXED)) throw ArgError("invalid arguments");
+    if (M.nlev < 2) throw StateError("a coarse level is needed to produce corrections");
+    ensure_learned(h, M);
+    LevelDev& L = M.lev[0];
+    const int* grp = M.lgrp.empty() ? nullptr : M.lgrp[0];
+    for (int k = 0; k < n_cycles; ++k) {
+      if (mode == CGKS_MIXED) vcycle_pre<2, float>(h, M);
+      else vcycle_pre<2, double>(h, M);
+      features(h, M);
+      CK(cudaMemcpyAsync(M.Wsave, L.W, (size_t)L.n * M.nv * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      if (mode == CGKS_MIXED) vcycle_coarse<2, float>(h, M);
+      else vcycle_coarse<2, double>(h, M);
+      k_target2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, L.W, M.Wsave, grp, M.winf, h->cfg.gamma, M.Yl);
+      CK(cudaGetLastError());
+      const int rc = cgks_mlp_dataset_append(h, L.n, (const uint16_t*)M.X, M.Yl);
+      if (rc != CGKS_OK) return rc;
+    }
+    return CGKS_OK;
+  });
+}
+
+int cgks_learned_stats(cgks_t* h, int mesh_id, double* out) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    if (!out) throw ArgError("null output");
+    for (int i = 0; i < 6; ++i) out[i] = M.lstats[i];
+    return CGKS_OK;
+  });
+}
+
+}  // extern "C"
 
 extern "C" {
 

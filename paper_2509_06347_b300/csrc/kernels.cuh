@@ -11,6 +11,8 @@
 // gather their faces in a fixed order, so residual sums are deterministic and
 // need no atomics.
 #pragma once
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "physics.cuh"
@@ -956,6 +958,165 @@ __global__ void __launch_bounds__(kBlock) k_diag(Topo Tp, const double* __restri
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= Tp.n) return;
   Dg[c] = lusgs_diag<DIM>(Tp, c, rface, alpha[c], dte[c], dti[c]);
+}
+
+// ---------------------------------------------------------------------------
+// Learned coarse-grid correction (2-D): per-cell features, training targets,
+// gated application and the judge error.
+// Features of a cell (17, scaled by the free stream's rho, rho c, rho c^2):
+// W, slopes times h = |Omega|^(1/2), R dt_imp / |Omega|, DF; the network input
+// is the cell's 17 followed by its three face neighbours' (ghosts across
+// boundary faces: mirrored / free-stream state, zero residual, own DF and h).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fs_scales(const double* w, double gamma, double* sc) {
+  const double rho = w[0];
+  const double ke = 0.5 * (w[1] * w[1] + w[2] * w[2]) / rho;
+  const double p = (gamma - 1.0) * (w[3] - ke);
+  const double c = sqrt(gamma * p / rho);
+  sc[0] = rho;
+  sc[1] = rho * c;
+  sc[2] = rho * c;
+  sc[3] = rho * c * c;
+}
+
+__device__ __forceinline__ void cell_features(const double* W, const double (*g)[2], double rterm_scale,
+                                              const double* R, double a, double h, const double* sc,
+                                              __nv_bfloat16* out) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) out[v] = __float2bfloat16((float)(W[v] / sc[v]));
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int d = 0; d < 2; ++d) out[4 + 2 * v + d] = __float2bfloat16((float)(g[v][d] * h / sc[v]));
+#pragma unroll
+  for (int v = 0; v < 4; ++v) out[12 + v] = __float2bfloat16((float)(R ? R[v] * rterm_scale / sc[v] : 0.0));
+  out[16] = __float2bfloat16((float)a);
+}
+
+__global__ void __launch_bounds__(kBlock) k_features2(DevFine M, const double* __restrict__ W,
+                                                      const double* __restrict__ G, const double* __restrict__ R,
+                                                      const double* __restrict__ dti, const double* __restrict__ alpha,
+                                                      const double* __restrict__ winf, double gamma,
+                                                      __nv_bfloat16* __restrict__ X) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= M.n) return;
+  const double* wi = winf + 4 * (M.grp ? M.grp[c] : 0);
+  double sc[4];
+  fs_scales(wi, gamma, sc);
+  __nv_bfloat16* out = X + (size_t)c * 68;
+  double Wc[4], gc[4][2];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    Wc[v] = W[(size_t)c * 4 + v];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) gc[v][d] = G[((size_t)c * 4 + v) * 2 + d];
+  }
+  const double hc = sqrt(M.vol[c]);
+  cell_features(Wc, gc, dti[c] / M.vol[c], R + (size_t)c * 4, alpha[c], hc, sc, out);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int j = M.cnbr[(size_t)c * 3 + m];
+    __nv_bfloat16* o = out + 17 * (m + 1);
+    if (j >= 0) {
+      double Wj[4], gj[4][2];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        Wj[v] = W[(size_t)j * 4 + v];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) gj[v][d] = G[((size_t)j * 4 + v) * 2 + d];
+      }
+      cell_features(Wj, gj, dti[j] / M.vol[j], R + (size_t)j * 4, alpha[j], sqrt(M.vol[j]), sc, o);
+    } else {
+      const int f = M.cface[(size_t)c * 3 + m];
+      const double sd = M.cside[(size_t)c * 3 + m];
+      double n[2] = {sd * M.fn[(size_t)f * 2], sd * M.fn[(size_t)f * 2 + 1]};
+      double Wg[4], gg[4][2];
+      ghost_state<2>(M.ftag[f], wi, n, Wc, Wg);
+      ghost_grad<2>(M.ftag[f], wi, n, gc, gg);
+      cell_features(Wg, gg, 0.0, nullptr, alpha[c], hc, sc, o);
+    }
+  }
+}
+
+// training target: the applied fine correction, scaled like W
+__global__ void k_target2(int n, const double* __restrict__ W, const double* __restrict__ Wsave,
+                          const int* __restrict__ grp, const double* __restrict__ winf, double gamma,
+                          float* __restrict__ Y) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double sc[4];
+  fs_scales(winf + 4 * (grp ? grp[c] : 0), gamma, sc);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) Y[(size_t)c * 4 + v] = (float)((W[(size_t)c * 4 + v] - Wsave[(size_t)c * 4 + v]) / sc[v]);
+}
+
+// learned correction applied where the DF factor is at least the gate
+__global__ void __launch_bounds__(kBlock) k_apply_learned2(int n, const float* __restrict__ P,
+                                                           const double* __restrict__ alpha, double gate,
+                                                           const int* __restrict__ grp, const double* __restrict__ winf,
+                                                           const int* __restrict__ active, double gamma,
+                                                           double* __restrict__ W, Counters* __restrict__ cnt) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  if (active && !active[grp[c]]) return;
+  if (!(alpha[c] >= gate)) return;
+  double sc[4], w[4], d[4];
+  fs_scales(winf + 4 * (grp ? grp[c] : 0), gamma, sc);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    w[v] = W[(size_t)c * 4 + v];
+    d[v] = (double)P[(size_t)c * 4 + v] * sc[v];
+  }
+  const int r = guarded_add<2>(gamma, w, d);
+  if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
+  if (r < 0) atomicAdd(&cnt->update_zeroed, 1ull);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) W[(size_t)c * 4 + v] = w[v];
+}
+
+// judge: squared error of the prediction against the applied plain correction
+// and squared size of that correction, over gated cells (per-block partials)
+__global__ void __launch_bounds__(kBlock) k_judge2(int n, const float* __restrict__ P, const double* __restrict__ W,
+                                                   const double* __restrict__ Wsave, const double* __restrict__ alpha,
+                                                   double gate, const int* __restrict__ grp,
+                                                   const double* __restrict__ winf, double gamma,
+                                                   double* __restrict__ part) {
+  __shared__ double se[kBlock], sr[kBlock];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0, r = 0.0;
+  if (c < n && alpha[c] >= gate) {
+    double sc[4];
+    fs_scales(winf + 4 * (grp ? grp[c] : 0), gamma, sc);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const double t = (W[(size_t)c * 4 + v] - Wsave[(size_t)c * 4 + v]) / sc[v];
+      const double d = (double)P[(size_t)c * 4 + v] - t;
+      e += d * d;
+      r += t * t;
+    }
+  }
+  se[threadIdx.x] = e;
+  sr[threadIdx.x] = r;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      se[threadIdx.x] += se[threadIdx.x + st];
+      sr[threadIdx.x] += sr[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = se[0];
+    part[2 * blockIdx.x + 1] = sr[0];
+  }
+}
+
+__global__ void k_judge_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double e = 0.0, r = 0.0;
+  for (int b = 0; b < nb; ++b) { e += part[2 * b]; r += part[2 * b + 1]; }
+  out[0] = e;
+  out[1] = r;
 }
 
 // FMA-throughput probe: CH independent chains per thread

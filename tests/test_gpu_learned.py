@@ -1,0 +1,130 @@
+"""GPU tests of the learned coarse-grid correction inside the V-cycle:
+trajectory collection, the DF gate, the judge and fallback policy, and a
+measurement of what a trained network gains over the plain V-cycle."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2509_06347_b300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GAMMA = 1.4
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_06347_b300 import build, cgks
+    build.build()
+    return cgks
+
+
+def mesh():
+    return synth.cylinder_mesh(16, 8, 1.05 ** 4, n_refine=2)
+
+
+def run(cg, mach, ncyc, mode, levels=None, theta=None, **cfg):
+    m = mesh()
+    w = synth.freestream(mach)
+    ctx = cg.Context(cg.default_config(**cfg))
+    if theta is not None:
+        ctx.cgks_mlp_set_params(theta)
+    ctx.setup(1, m, w, synth.uniform_state(m, w), levels=levels)
+    norms = np.zeros((ncyc, 4, 2))
+    done = np.zeros(1, np.int32)
+    rc = ctx.cgks_vcycle([1], ncyc, mode, norms, done, check=False)
+    W = np.zeros((m["cell_nodes"].shape[0], 4))
+    ctx.cgks_get_state(1, W)
+    stats = ctx.cgks_learned_stats(1) if mode == cg.LEARNED else None
+    ctx.close()
+    return rc, W, norms[:done[0]], stats
+
+
+def constant_net(delta):
+    """Network whose output is the constant delta (last layer weights zero)."""
+    th = mlp.init_params(3)
+    th[-4:] = delta
+    th[-4 - 4 * 64:-4] = 0.0
+    return th
+
+
+def test_collect_fills_training_set(cg):
+    m = mesh()
+    w = synth.freestream(3.0)
+    ctx = cg.Context()
+    ctx.cgks_mlp_set_params(mlp.init_params(0))
+    ctx.setup(1, m, w, synth.uniform_state(m, w))
+    ctx.cgks_mlp_dataset_clear()
+    ctx.cgks_mlp_collect(1, 3, 1)
+    assert ctx.cgks_mlp_dataset_size() == 3 * m["cell_nodes"].shape[0]
+    ctx.close()
+
+
+def test_closed_gate_is_fine_smoothing_only(cg):
+    """With the gate above any DF value and no judge cycles, the first learned
+    cycle changes the state exactly as a one-level V-cycle (fine steps only).
+    (Later cycles differ: the learned cycle also evaluates the residual after
+    smoothing, whose DF factor feeds the next cycle's sub-stencil.)"""
+    th = constant_net(np.array([0.1, 0.0, 0.0, 0.1]))
+    _, Wl, _, st = run(cg, 3.0, 1, cg.LEARNED, theta=th, df_gate=2.0, learned_judge_every=0)
+    _, W1, _, _ = run(cg, 3.0, 1, cg.MIXED, levels=1)
+    np.testing.assert_array_equal(Wl, W1)
+    assert st["learned"] == 1 and st["judge"] == 0
+
+
+def test_open_gate_adds_the_prediction(cg):
+    """With every cell gated in, one learned cycle adds the (constant)
+    prediction times the free-stream scales to the one-level result."""
+    d = np.array([1e-3, 2e-3, -1e-3, 3e-3])
+    th = constant_net(d)
+    _, Wl, _, _ = run(cg, 3.0, 1, cg.LEARNED, theta=th, df_gate=-1.0, learned_judge_every=0)
+    _, W1, _, _ = run(cg, 3.0, 1, cg.MIXED, levels=1)
+    w = synth.freestream(3.0)
+    rho, c = w[0], 1.0
+    sc = np.array([rho, rho * c, rho * c, rho * c * c])
+    np.testing.assert_allclose(Wl - W1, np.tile(d * sc, (len(W1), 1)), rtol=1e-2, atol=1e-7)
+
+
+def test_bad_network_is_disabled_by_the_judge(cg):
+    """A network predicting nonsense fails the first judge cycle and the run
+    then follows the plain V-cycle exactly."""
+    th = constant_net(np.array([0.5, -0.5, 0.5, 2.0]))
+    rc, Wl, nl, st = run(cg, 3.0, 6, cg.LEARNED, theta=th)
+    _, Wp, np_, _ = run(cg, 3.0, 6, cg.MIXED)
+    assert rc == 0 and st["disabled"] and st["learned"] == 0 and st["judge"] == 1
+    np.testing.assert_array_equal(Wl, Wp)
+    np.testing.assert_array_equal(nl, np_)
+
+
+def test_trained_network_gain_is_measured(cg, capsys):
+    """Train on trajectories at Mach 2 and 4, evaluate at the held-out Mach 3:
+    report the network's judge error and the residual / time of learned versus
+    plain cycles.  The fallback policy must keep the learned run at least as
+    good as 2x the plain residual."""
+    import time
+    m = mesh()
+    ctx = cg.Context()
+    ctx.cgks_mlp_set_params(mlp.init_params(1))
+    ctx.cgks_mlp_dataset_clear()
+    for i, mach in enumerate((2.0, 4.0)):
+        w = synth.freestream(mach)
+        ctx.setup(10 + i, m, w, synth.uniform_state(m, w))
+        ctx.cgks_mlp_collect(10 + i, 60, 1)
+    losses = ctx.cgks_mlp_train(1500, 4096, 1e-3, seed=5)
+    assert losses[-50:].mean() < losses[:5].mean()
+    theta = ctx.cgks_mlp_get_params()
+    ctx.close()
+    out = {}
+    for mode in (cg.MIXED, cg.LEARNED):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        rc, W, norms, st = run(cg, 3.0, 200, mode, theta=theta)
+        out[mode] = (time.time() - t0, norms[-1, 0, 0] / norms[0, 0, 0], st)
+        assert rc == 0
+    with capsys.disabled():
+        print(f"\nlearned-correction gain at held-out Mach 3: plain {out[cg.MIXED][:2]}, "
+              f"learned {out[cg.LEARNED]}")
+    assert out[cg.LEARNED][1] <= 2.0 * out[cg.MIXED][1]
