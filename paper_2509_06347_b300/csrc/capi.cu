@@ -369,12 +369,13 @@ void launch_recon(cgks_t* h, MeshDev& M) {
 }
 
 template <int DIM>
-void launch_flux(cgks_t* h, MeshDev& M) {
+void launch_flux(cgks_t* h, MeshDev& M, bool point = true) {
   LevelDev& L = M.lev[0];
   constexpr int NGP = Dims<DIM>::NGP, FPW = 32 / NGP;
   const int64_t warps = (M.fine.nf + FPW - 1) / FPW;
   const int64_t threads = warps * 32;
-  k_flux<DIM><<<blocks_for(threads, M.blk[B_FLUX]), M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, phys(h->cfg, DIM),
+  auto kern = point ? k_flux<DIM, true> : k_flux<DIM, false>;
+  kern<<<blocks_for(threads, M.blk[B_FLUX]), M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, phys(h->cfg, DIM),
                                                                M.Fface, M.Wface, M.aface, L.W, L.rface);
 }
 
@@ -385,7 +386,8 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
                    double* alpha_out_dev, double* gradnew_dev) {
   LevelDev& L = M.lev[0];
   launch_recon<DIM>(h, M);
-  launch_flux<DIM>(h, M);
+  // the time-evolved point values only feed the slopes
+  launch_flux<DIM>(h, M, slopes_update || gradnew_dev != nullptr);
   const bool grouped = !M.lgrp.empty();
   // norm partials need whole blocks of kBlock threads
   const int gb = (want_norm && !grouped) ? kBlock : M.blk[B_GATHER];

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
 #pragma unroll
     for (int b = 0; b < DIM; ++b) mom[a][b] = M.m2[(size_t)(a * DIM + b) * n + c];
   double P[NV][NC];
-#pragma unroll 1
+#pragma unroll
   for (int v = 0; v < NV; ++v) {
     double e[NFC];
 #pragma unroll
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
 // ---------------------------------------------------------------------------
 // K2: gas-kinetic flux, one lane per (face, Gauss point)
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, bool POINT>
 __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __restrict__ coef,
                                                  const double* __restrict__ dte, const double* __restrict__ winf,
                                                  PhysParams P, double* __restrict__ Fface, double* __restrict__ Wface,
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __rest
     to_local<DIM>(fr, Wr, wr);
     grad_to_local<DIM>(fr, gl, Gl);
     grad_to_local<DIM>(fr, gr, Gr);
-    gks_flux<DIM>(P, wl, Gl, wr, Gr, dt, Fl, Wt);
+    gks_flux<DIM, POINT>(P, wl, Gl, wr, Gr, dt, Fl, Wt);
     af = df_factor<DIM>(P.gamma, wl, wr);
     double Fg[NV], Wg[NV];
     to_global<DIM>(fr, Fl, Fg);
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __rest
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       Fface[(size_t)f * NV + v] = Fs[v];
-      Wface[(size_t)f * NV + v] = Ws[v];
+      if (POINT) Wface[(size_t)f * NV + v] = Ws[v];
     }
     aface[f] = af;
     // spectral radius of the LU-SGS splitting at the mean of the cell means

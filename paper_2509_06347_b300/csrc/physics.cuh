@@ -214,9 +214,60 @@ __device__ __forceinline__ void au_mom(const Mom<DIM>& m, const double (*a)[DIM 
   if (DIM == 3) add_psi_s_mom<DIM, KU, 0, 1>(m, a[DIM - 1], scale, acc);
 }
 
+// Sum over directions d of (dF_d/dW) . dW_d for the Euler fluxes F_d along the
+// local axes: for a Maxwellian g(W(x)), int u_d psi dg/dx_d = d/dx_d F_d(W), so
+// this equals <psi (a.u)> of the full-space Maxwellian (times rho) without
+// forming the velocity moments.
+template <int DIM>
+__device__ __forceinline__ void euler_flux_divergence(double gamma, const double* W, const double (*dW)[DIM + 2],
+                                                      double* out) {
+  constexpr int NV = DIM + 2;
+  const double ir = 1.0 / W[0];
+  double u[DIM], q2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    u[i] = W[1 + i] * ir;
+    q2 += u[i] * u[i];
+  }
+  const double p = (gamma - 1.0) * (W[NV - 1] - 0.5 * W[0] * q2);
+  const double H = (W[NV - 1] + p) * ir;  // total enthalpy
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double* g = dW[d];
+    // derivatives of primitive quantities along this direction
+    double du[DIM], udu = 0.0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      du[i] = (g[1 + i] - u[i] * g[0]) * ir;
+      udu += u[i] * du[i];
+    }
+    const double dp = (gamma - 1.0) * (g[NV - 1] - 0.5 * g[0] * q2 - W[0] * udu);
+    out[0] += g[1 + d];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) out[1 + i] += g[1 + d] * u[i] + W[1 + d] * du[i];
+    out[1 + d] += dp;
+    const double dH = (g[NV - 1] + dp - H * g[0]) * ir;
+    out[NV - 1] += g[1 + d] * H + W[1 + d] * dH;
+  }
+}
+
+// (dF_n/dW) . v for the Euler flux through the local normal (first axis)
+template <int DIM>
+__device__ __forceinline__ void euler_flux_jvp_normal(double gamma, const double* W, const double* v, double* out) {
+  constexpr int NV = DIM + 2;
+  double g[DIM][NV];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) g[d][i] = d == 0 ? v[i] : 0.0;
+  euler_flux_divergence<DIM>(gamma, W, g, out);
+}
+
 // Gas-kinetic flux (time average over [0, dt]) and point value at t = dt in
 // the local frame (u normal).  G?[d][v] = derivative along local direction d.
-template <int DIM>
+template <int DIM, bool POINT = true>
 __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*Gl)[DIM + 2], const double* Wr,
                          const double (*Gr)[DIM + 2], double dt, double* F, double* Wt) {
   constexpr int NV = DIM + 2;
@@ -273,32 +324,39 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
     for (int i = 0; i < NV; ++i) b[i] = 0.5 * (Gl[d][i] + Gr[d][i]) * ic;
     slope_solve<DIM>(pc, P, b, ac[d]);
   }
-  // time slopes from <A + a.u> = 0 (full-space moments of each Maxwellian)
+  // time slopes from <A + a.u> = 0, with <psi (a.u)> of a full-space
+  // Maxwellian given by the Euler-flux divergence of its slopes
   double Al[NV], Ar[NV], Ac[NV];
   {
-    Mom<DIM> fl = ml, fr = mr;
-    normal_moments<DIM>(pl, 0, fl);
-    normal_moments<DIM>(pr, 0, fr);
     double s[NV];
+    euler_flux_divergence<DIM>(P.gamma, Wl, Gl, s);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) s[i] = 0.0;
-    au_mom<DIM, 0>(fl, al, -1.0, s);
+    for (int i = 0; i < NV; ++i) s[i] *= -pl.irho;
     slope_solve<DIM>(pl, P, s, Al);
+    euler_flux_divergence<DIM>(P.gamma, Wr, Gr, s);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) s[i] = 0.0;
-    au_mom<DIM, 0>(fr, ar, -1.0, s);
+    for (int i = 0; i < NV; ++i) s[i] *= -pr.irho;
     slope_solve<DIM>(pr, P, s, Ar);
   }
-  double PAc[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) PAc[i] = 0.0;
-  au_mom<DIM, 0>(mc, ac, 1.0, PAc);
+  // interface Maxwellian: <psi (a_c.u)> = Euler-flux divergence; its time slope
+  // gives <psi (A_c.psi)> = W_t = -<psi (a_c.u)> and <u psi (A_c.psi)> = J_n W_t
+  double PAc[NV], UAc[NV];
   {
-    double s[NV];
+    double gc[DIM][NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) s[i] = -PAc[i];
-    slope_solve<DIM>(pc, P, s, Ac);
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) gc[d][i] = 0.5 * (Gl[d][i] + Gr[d][i]);
+    euler_flux_divergence<DIM>(P.gamma, Wc, gc, PAc);
+    double wt[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      PAc[i] *= pc.irho;
+      wt[i] = -PAc[i];
+    }
+    euler_flux_jvp_normal<DIM>(P.gamma, Wc, wt, UAc);
   }
+  (void)Ac;
   // collision time and time integrals
   const double pL = pl.rho * pl.h, pR = pr.rho * pr.h;
   const double tau = P.c1 * dt + P.c2 * fabs(pL - pR) / (pL + pR) * dt;
@@ -317,11 +375,13 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
 #pragma unroll
   for (int i = 0; i < NV; ++i) fx[i] += T1 * t[i];
   au_mom<DIM, 1>(mc, ac, T2, fx);
-  add_psi_s_mom<DIM, 1, 0, 0>(mc, Ac, T3, fx);
-  psi_mom<DIM, 0, 0, 0>(mc, t);
 #pragma unroll
-  for (int i = 0; i < NV; ++i) wx[i] += C1 * t[i] + C2 * PAc[i];
-  add_psi_s_mom<DIM, 0, 0, 0>(mc, Ac, C3, wx);
+  for (int i = 0; i < NV; ++i) fx[i] += T3 * UAc[i];
+  if (POINT) {
+    psi_mom<DIM, 0, 0, 0>(mc, t);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) wx[i] += C1 * t[i] + (C2 - C3) * PAc[i];
+  }
 #pragma unroll
   for (int i = 0; i < NV; ++i) { F[i] = pc.rho * fx[i]; Wt[i] = pc.rho * wx[i]; }
   // --- kinetic part (g^l on u > 0, g^r on u < 0)
@@ -338,11 +398,13 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
     for (int i = 0; i < NV; ++i) fx[i] += T4 * t[i];
     au_mom<DIM, 1>(m, a, -(tau * T4 + T5), fx);
     add_psi_s_mom<DIM, 1, 0, 0>(m, Ak, -tau * T4, fx);
-    psi_mom<DIM, 0, 0, 0>(m, t);
+    if (POINT) {
+      psi_mom<DIM, 0, 0, 0>(m, t);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) wx[i] += e * t[i];
-    au_mom<DIM, 0>(m, a, -e * (tau + dt), wx);
-    add_psi_s_mom<DIM, 0, 0, 0>(m, Ak, -e * tau, wx);
+      for (int i = 0; i < NV; ++i) wx[i] += e * t[i];
+      au_mom<DIM, 0>(m, a, -e * (tau + dt), wx);
+      add_psi_s_mom<DIM, 0, 0, 0>(m, Ak, -e * tau, wx);
+    }
 #pragma unroll
     for (int i = 0; i < NV; ++i) { F[i] += rho * fx[i]; Wt[i] += rho * wx[i]; }
   }
