@@ -35,10 +35,11 @@ METRIC = "fine-cell V-cycles/s"
 UNIT = "cell-cycles/s"
 WORKLOAD = "cylinder_mach5_65536tri_3level"
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
-# FP64 operations per Gauss point of the gas-kinetic flux kernel (2-D): from
-# the ncu instruction counts of k_flux<2> (2 x DFMA + DADD + DMUL per launch
-# divided by the launch's Gauss points); see profiles/k_flux_cylinder65k.md.
-FLUX_FLOP_PER_GP_2D = 3406.0
+# FP64 operations per Gauss point of the point-value variant of the 2-D
+# gas-kinetic flux kernel, k_flux<2,1>: ncu instruction counts of one launch on
+# this workload, (2 x DFMA + DADD + DMUL) / 197,120 Gauss points
+# (profiles/k_flux_cylinder65k.md).
+FLUX_FLOP_PER_GP_2D = 2947.1
 
 
 def parse():
@@ -52,6 +53,8 @@ def parse():
                     help="cylinder: one 65,536-cell Mach-5 cylinder; batch: 64 cylinders of "
                          "16k-262k cells at Mach 1.5-8 solved together")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-convergence", action="store_true",
+                    help="skip the wall-time-to-drop leg (vortex to 1e-10, cylinder plateau)")
     ap.add_argument("--profile-steps", action="store_true",
                     help="only warm-up + steps, for ncu launch lists")
     return ap.parse_args()
@@ -297,6 +300,9 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
+    conv = None
+    if not args.no_convergence:
+        conv = convergence_leg(cgks, stream)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(mesh, w, W0)
@@ -310,7 +316,7 @@ def run_ours(args):
                    "colors": [lv["colors"] for lv in info], "mode": args.mode, "mach": 5.0,
                    "cfl_imp": 10.0, "coarse_sweeps": 6, "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "k_flux<2> (gas-kinetic face flux)", "bound": "alu",
+        "roofline": {"kernel": "k_flux<2,1> (gas-kinetic face flux + point values)", "bound": "alu",
                      "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s (FP64)",
                      "frac": achieved / fp64_peak, "traffic": None,
                      "peak_source": "FP64 FMA-chain probe of this library on this GPU (cgks_fma_probe)",
@@ -320,6 +326,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches_per_cycle * args.steps,
         "clocks": clocks,
+        "convergence": conv,
         "residual_rms_rho_last": float(rn[0, 0]),
         "counters": {"recon_fallback": int(counters[0]), "update_halved": int(counters[1]),
                      "update_zeroed": int(counters[2]), "nonfinite": int(counters[3])},
@@ -328,6 +335,65 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _solve_to_drop(cgks, mesh, w, W0, G0, mode, max_cycles, stream, **cfg):
+    """Whole solve from the initial state through cgks_vcycle (stops at the
+    1e-10 drop of the density residual norm); the graphs are captured by one
+    untimed cycle before the state is reset."""
+    import torch
+    ctx = cgks.Context(stream=stream.cuda_stream, **cfg)
+    ctx.setup(1, mesh, w, W0, G0)
+    ctx.cgks_vcycle([1], 1, mode, np.zeros((1, 4, 2)))
+    ctx.cgks_init_state(1, W0, G0)
+    norms = np.zeros((max_cycles, 4, 2))
+    done = np.zeros(1, np.int32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = ctx.cgks_vcycle([1], max_cycles, mode, norms, done, check=False)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    W = np.zeros_like(W0)
+    ctx.cgks_get_state(1, W)
+    ctx.close()
+    ncyc = int(done[0])
+    drop = norms[:ncyc, 0, 0] / norms[0, 0, 0]
+    out = {"rc": int(rc), "cycles": ncyc, "wall_s": wall, "final_drop": float(drop[-1]),
+           "min_drop": float(drop.min())}
+    for k in range(1, 11):
+        hit = np.nonzero(drop <= 10.0 ** -k)[0]
+        if not hit.size:
+            break
+        out[f"cycles_to_1e-{k}"] = int(hit[0]) + 1
+        out[f"wall_s_to_1e-{k}"] = wall * (int(hit[0]) + 1) / ncyc
+    return out, W
+
+
+def convergence_leg(cgks, stream):
+    """Wall time to a residual drop, all-FP64 against MIXED, on two cases:
+    the stationary isentropic vortex on the jittered periodic 2,048-cell mesh
+    (reaches the 1e-10 drop) and the Mach-5 cylinder of the timed workload
+    (a shocked inviscid flow whose residual plateaus; drops reached reported)."""
+    res = {}
+    mv = synth.vortex_mesh(n_coarse=8, n_refine=2)
+    Wv, Gv = synth.vortex_state(mv)
+    wv = np.array([1.0, 0.0, 0.0, 1.0 / 0.4])
+    cases = [("vortex_2048tri_3level", mv, wv, Wv, Gv, 3000, {"tau_c1": 1.0}),
+             (WORKLOAD, *workload(), None, 3000, {})]
+    for name, mesh, w, W0, G0, cap, cfg in cases:
+        fp64, W64 = _solve_to_drop(cgks, mesh, w, W0, G0, cgks.PLAIN_FP64, cap, stream, **cfg)
+        mixed, Wmx = _solve_to_drop(cgks, mesh, w, W0, G0, cgks.MIXED, cap, stream, **cfg)
+        scale = np.max(np.abs(W64), axis=0)
+        entry = {"cells": len(W0), "max_cycles": cap, "config": cfg or {"tau_c1": 0.01},
+                 "fp64": fp64, "mixed": mixed,
+                 "mixed_vs_fp64_state_max_rel_diff": float(np.max(np.abs(Wmx - W64) / scale))}
+        deepest = max(k for k in range(0, 11) if k == 0 or (f"cycles_to_1e-{k}" in fp64
+                                                            and f"cycles_to_1e-{k}" in mixed))
+        if deepest:
+            entry["common_drop"] = f"1e-{deepest}"
+            entry["wall_ratio_fp64_over_mixed"] = fp64[f"wall_s_to_1e-{deepest}"] / mixed[f"wall_s_to_1e-{deepest}"]
+        res[name] = entry
+    return res
 
 
 def lpt_partition(sizes, n_parts):
