@@ -40,6 +40,9 @@ L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 # this workload, (2 x DFMA + DADD + DMUL) / 197,120 Gauss points
 # (profiles/k_flux_cylinder65k.md).
 FLUX_FLOP_PER_GP_2D = 2947.1
+# DRAM bytes (read + write) of one k_flux<2,1> launch on this workload, from the
+# same ncu capture (cold-cache replay).
+FLUX_DRAM_BYTES_PER_LAUNCH = 24825856
 
 
 def parse():
@@ -318,7 +321,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"kernel": "k_flux<2,1> (gas-kinetic face flux + point values)", "bound": "alu",
                      "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s (FP64)",
-                     "frac": achieved / fp64_peak, "traffic": None,
+                     "frac": achieved / fp64_peak, "traffic": FLUX_DRAM_BYTES_PER_LAUNCH,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_source": "FP64 FMA-chain probe of this library on this GPU (cgks_fma_probe)",
                      "flop_per_gp": FLUX_FLOP_PER_GP_2D, "gauss_points": n_gp,
                      "ms_per_launch": t_flux * 1e3},
