@@ -43,6 +43,12 @@ FLUX_FLOP_PER_GP_2D = 2947.1
 # DRAM bytes (read + write) of one k_flux<2,1> launch on this workload, from the
 # same ncu capture (cold-cache replay).
 FLUX_DRAM_BYTES_PER_LAUNCH = 24825856
+# The same figures for k_flux<3,1> (3 Gauss points per triangular face),
+# measured on the 16 x 16 x 16 sphere shell (147,456 tets, 297,984 faces:
+# 4,738.9 MFLOP and 153.2 MB of DRAM traffic per launch); the traffic is
+# scaled to the full shell by its number of faces (profiles/k_flux_sphere.md).
+FLUX_FLOP_PER_GP_3D = 5301.1
+FLUX_DRAM_BYTES_PER_FACE_3D = 514.0
 
 
 def parse():
@@ -52,9 +58,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "batch"],
-                    help="cylinder: one 65,536-cell Mach-5 cylinder; batch: 64 cylinders of "
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "sphere", "batch"],
+                    help="cylinder: one 65,536-cell Mach-5 cylinder; sphere: the Mach-6 cubed-sphere "
+                         "tet shell (1,179,648 tets at --sphere-n 32); batch: 64 cylinders of "
                          "16k-262k cells at Mach 1.5-8 solved together")
+    ap.add_argument("--sphere-n", type=int, default=32,
+                    help="panels per cube-face edge and radial layers of the sphere shell")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the wall-time-to-drop leg (vortex to 1e-10, cylinder plateau)")
@@ -67,6 +76,16 @@ def workload():
     mesh = synth.cylinder_mesh(n_theta=64, n_r=32, ratio=1.05, n_refine=2)
     w = synth.freestream(5.0)
     return mesh, w, synth.uniform_state(mesh, w)
+
+
+def sphere_workload(n: int):
+    mesh = synth.sphere_mesh(n_panel=n, n_r=n, ratio=1.08)
+    w = synth.freestream(6.0, dim=3)
+    return mesh, w, synth.uniform_state(mesh, w)
+
+
+def sphere_name(n: int) -> str:
+    return f"sphere_mach6_{6 * n ** 3 * 6}tet_3level"
 
 
 # ----------------------------------------------------------------------------
@@ -134,16 +153,16 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------
-def cpu_baseline(mesh, w, W0, budget_s: float = 25.0):
+def cpu_baseline(mesh, w, W0, budget_s: float = 25.0, what: str = "the"):
     """The oracle as it stands, single-threaded on the host: whole V-cycles of
-    the same workload until about budget_s seconds have been spent."""
+    the workload until about budget_s seconds have been spent."""
     import oracle
     t0 = time.perf_counter()
     om = oracle.OracleMesh(mesh)
     setup = time.perf_counter() - t0
-    n = len(W0)
-    cfg = oracle.cfg_vector(2, winf=w)
-    W, G, a = W0.copy(), np.zeros((n, 4, 2)), np.ones(n)
+    n, dim = len(W0), int(mesh["dim"])
+    cfg = oracle.cfg_vector(dim, winf=w)
+    W, G, a = W0.copy(), np.zeros((n, dim + 2, dim)), np.ones(n)
     cycles, spent = 0, 0.0
     while cycles == 0 or spent < budget_s * 0.5:
         t0 = time.perf_counter()
@@ -152,7 +171,7 @@ def cpu_baseline(mesh, w, W0, budget_s: float = 25.0):
         W, G, a = out["W"], out["grad"], out["alpha"]
         cycles += 1
     return {"value": n * cycles / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{cycles} whole V-cycle(s) of the {n}-cell workload from the free stream "
+            "sample": f"{cycles} whole V-cycle(s) of {what} {n}-cell workload from the free stream "
                       f"(FP64, single thread; mesh setup {setup:.1f} s not timed)"}
 
 
@@ -210,8 +229,15 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     build.build()
     mode = cgks.MIXED if args.mode == "mixed" else cgks.PLAIN_FP64
-    mesh, w, W0 = workload()
-    n = len(W0)
+    sphere = args.workload == "sphere"
+    if sphere:
+        mesh, w, W0 = sphere_workload(args.sphere_n)
+        wname, mach = sphere_name(args.sphere_n), 6.0
+    else:
+        mesh, w, W0 = workload()
+        wname, mach = WORKLOAD, 5.0
+    n, dim = len(W0), int(mesh["dim"])
+    nv = dim + 2
     stream = torch.cuda.Stream(device=dev)
     ctx = cgks.Context(stream=stream.cuda_stream)
     ctx.setup(1, mesh, w, W0)
@@ -269,16 +295,21 @@ def run_ours(args):
             kev[k][1].record(stream)
     torch.cuda.synchronize()
     t_flux = sum(a.elapsed_time(b) for a, b in kev) / args.steps * 1e-3
-    n_gp = info[0]["faces"] * 2
+    n_gp = info[0]["faces"] * (2 if dim == 2 else 3)
     fp64_peak = ctx.cgks_fma_probe(0) * 1e12
-    achieved = FLUX_FLOP_PER_GP_2D * n_gp / t_flux
+    flop_per_gp = FLUX_FLOP_PER_GP_2D if dim == 2 else FLUX_FLOP_PER_GP_3D
+    if dim == 2:
+        traffic = FLUX_DRAM_BYTES_PER_LAUNCH
+    else:
+        traffic = None if FLUX_DRAM_BYTES_PER_FACE_3D is None else FLUX_DRAM_BYTES_PER_FACE_3D * info[0]["faces"]
+    achieved = None if flop_per_gp is None else flop_per_gp * n_gp / t_flux
 
     # end to end through the public API with host buffers: state in, one
     # V-cycle, residual norms and state out, every step
-    Wh = torch.empty((n, 4), dtype=torch.float64).pin_memory().numpy()
+    Wh = torch.empty((n, nv), dtype=torch.float64).pin_memory().numpy()
     Wh[:] = W0
     ctx.cgks_get_state(1, Wh)
-    norms = torch.empty((1, 4, 2), dtype=torch.float64).pin_memory().numpy()
+    norms = torch.empty((1, nv, 2), dtype=torch.float64).pin_memory().numpy()
     e2e_steps = min(args.steps, 20)
     barrier()
     t0 = time.perf_counter()
@@ -292,11 +323,9 @@ def run_ours(args):
         tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_e2e = float(tt.item())
-    e2e = {"value": world * n * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * 4 * 8,
-           "d2h_bytes_per_step": n * 4 * 8 + 4 * 2 * 8}
+    e2e = {"value": world * n * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * nv * 8,
+           "d2h_bytes_per_step": n * nv * 8 + nv * 2 * 8}
 
-    # convergence of the timed run
-    hist = np.zeros((1, 4, 2))
     rn = ctx.cgks_residual_norms(1, 0)
     counters = ctx.cgks_counters(1)
     if rank != 0:
@@ -304,27 +333,33 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     conv = None
-    if not args.no_convergence:
+    if not args.no_convergence and not sphere:
         conv = convergence_leg(cgks, stream)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(mesh, w, W0)
+        if sphere:
+            # bounded sample: the same scheme on the 8 x 8 x 8 shell (18,432
+            # tets); whole V-cycles of the full shell take minutes each
+            cpu = cpu_baseline(*sphere_workload(8), what="the 8x8x8 sphere shell (same per-cell work),")
+        else:
+            cpu = cpu_baseline(mesh, w, W0)
     peaks = measured_peaks()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if mode == cgks.MIXED else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": n, "levels": [lv["cells"] for lv in info],
-                   "colors": [lv["colors"] for lv in info], "mode": args.mode, "mach": 5.0,
+        "config": {"workload": wname, "cells": n, "levels": [lv["cells"] for lv in info],
+                   "colors": [lv["colors"] for lv in info], "mode": args.mode, "mach": mach,
                    "cfl_imp": 10.0, "coarse_sweeps": 6, "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "k_flux<2,1> (gas-kinetic face flux + point values)", "bound": "alu",
-                     "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s (FP64)",
-                     "frac": achieved / fp64_peak, "traffic": FLUX_DRAM_BYTES_PER_LAUNCH,
+        "roofline": {"kernel": f"k_flux<{dim},1> (gas-kinetic face flux + point values)", "bound": "alu",
+                     "achieved": None if achieved is None else achieved / 1e12, "peak": fp64_peak / 1e12,
+                     "unit": "TFLOP/s (FP64)",
+                     "frac": None if achieved is None else achieved / fp64_peak, "traffic": traffic,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_source": "FP64 FMA-chain probe of this library on this GPU (cgks_fma_probe)",
-                     "flop_per_gp": FLUX_FLOP_PER_GP_2D, "gauss_points": n_gp,
+                     "flop_per_gp": flop_per_gp, "gauss_points": n_gp,
                      "ms_per_launch": t_flux * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -64,3 +64,110 @@ def small_meshes():
         "cylinder": synth.cylinder_mesh(n_theta=16, n_r=8, n_refine=2),
         "sphere": synth.sphere_mesh(n_panel=4, n_r=4),
     }
+
+
+def face_neighbours(cell_nodes):
+    """Face adjacency of a simplex mesh from its node ids: nb [n, dim+1] with
+    nb[c, k] the cell across the face opposite vertex k (-1 on the boundary),
+    and the sorted node key of every cell face [n, dim+1, dim]."""
+    n, nvtx = cell_nodes.shape
+    faces = np.stack([np.delete(cell_nodes, k, axis=1) for k in range(nvtx)], 1)
+    faces = np.sort(faces, axis=2)
+    base = int(cell_nodes.max()) + 1
+    key = np.zeros(faces.shape[:2], np.int64)
+    for d in range(nvtx - 1):
+        key = key * base + faces[..., d]
+    flat = key.reshape(-1)
+    order = np.argsort(flat, kind="stable")
+    sk = flat[order]
+    nb = -np.ones(n * nvtx, np.int64)
+    same = np.nonzero(sk[1:] == sk[:-1])[0]
+    a, b = order[same], order[same + 1]
+    nb[a] = b // nvtx
+    nb[b] = a // nvtx
+    return nb.reshape(n, nvtx), faces
+
+
+def ring_submesh(mesh, seeds, rings=3):
+    """The cells within `rings` face-neighbour steps of the seed cells, as a
+    stand-alone mesh: nodes renumbered, original boundary faces kept with their
+    tags and cut faces tagged far field.  Returns (submesh, cell ids in the
+    original mesh, positions of the seeds in the submesh).  A cell's fine
+    residual depends on two rings only, so the seeds' residuals are those of
+    the full mesh."""
+    cn = np.asarray(mesh["cell_nodes"], np.int64)
+    nb, faces = face_neighbours(cn)
+    keep = np.zeros(len(cn), bool)
+    keep[seeds] = True
+    front = np.asarray(seeds)
+    for _ in range(rings):
+        nxt = nb[front].reshape(-1)
+        nxt = nxt[nxt >= 0]
+        nxt = nxt[~keep[nxt]]
+        keep[nxt] = True
+        front = np.unique(nxt)
+    cells = np.nonzero(keep)[0]
+    pos = -np.ones(len(cn), np.int64)
+    pos[cells] = np.arange(len(cells))
+    nodes = np.unique(cn[cells])
+    nmap = -np.ones(int(cn.max()) + 1, np.int64)
+    nmap[nodes] = np.arange(len(nodes))
+    # original boundary tags by sorted face key
+    bn = np.sort(np.asarray(mesh["bface_nodes"], np.int64), axis=1)
+    btag = {tuple(r): int(t) for r, t in zip(bn, mesh["bface_tag"])}
+    sub_bn, sub_bt = [], []
+    for c in cells:
+        for k in range(cn.shape[1]):
+            j = nb[c, k]
+            if j >= 0 and keep[j]:
+                continue
+            key = tuple(faces[c, k])
+            sub_bn.append([nmap[v] for v in key])
+            sub_bt.append(btag.get(key, synth.TAG_FARFIELD) if j < 0 else synth.TAG_FARFIELD)
+    sub = dict(dim=mesh["dim"], cell_nodes=np.ascontiguousarray(nmap[cn[cells]], np.int32),
+               cell_xyz=np.ascontiguousarray(mesh["cell_xyz"][cells]),
+               bface_nodes=np.ascontiguousarray(np.array(sub_bn, np.int32).reshape(-1, mesh["dim"])),
+               bface_tag=np.ascontiguousarray(np.array(sub_bt, np.int32)), parents=[])
+    return sub, cells, pos[np.asarray(seeds)]
+
+
+def coarse_ring_submesh(mesh, level, seeds, rings=1):
+    """The coarse cells of `level` within `rings` steps of the seeds, with all
+    their fine descendants, as a stand-alone mesh with a `level`-deep
+    hierarchy.  The first-order coarse residual of a cell depends on its face
+    neighbours only, so one ring gives the seeds' full-mesh residuals.
+    Returns (submesh, the kept coarse cell ids in the submesh's order, the
+    positions of the seeds among them)."""
+    cn = np.asarray(mesh["cell_nodes"], np.int64)
+    nb, _ = face_neighbours(cn)
+    par = [np.asarray(p, np.int64) for p in mesh["parents"][:level]]
+    anc = np.arange(len(cn))
+    for p in par:
+        anc = p[anc]  # fine cell -> its ancestor on `level`
+    ncoarse = int(anc.max()) + 1
+    fi = np.repeat(np.arange(len(cn)), cn.shape[1])
+    fj = nb.reshape(-1)
+    ok = fj >= 0
+    a, b = anc[fi[ok]], anc[fj[ok]]
+    cross = a != b
+    a, b = a[cross], b[cross]
+    keep = np.zeros(ncoarse, bool)
+    keep[seeds] = True
+    front = np.asarray(seeds)
+    for _ in range(rings):
+        sel = np.isin(a, front)
+        nxt = np.unique(b[sel])
+        nxt = nxt[~keep[nxt]]
+        keep[nxt] = True
+        front = nxt
+    fine = np.nonzero(keep[anc])[0]
+    sub, cells, _ = ring_submesh(mesh, fine, rings=0)
+    assert np.array_equal(cells, fine)
+    parents, cur = [], fine
+    for p in par:
+        up = p[cur]
+        ids = np.unique(up)
+        parents.append(np.ascontiguousarray(np.searchsorted(ids, up), np.int32))
+        cur = ids
+    sub["parents"] = parents
+    return sub, cur, np.searchsorted(cur, np.asarray(seeds))
