@@ -35,20 +35,22 @@ METRIC = "fine-cell V-cycles/s"
 UNIT = "cell-cycles/s"
 WORKLOAD = "cylinder_mach5_65536tri_3level"
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
-# FP64 operations per Gauss point of the point-value variant of the 2-D
-# gas-kinetic flux kernel, k_flux<2,1>: ncu instruction counts of one launch on
-# this workload, (2 x DFMA + DADD + DMUL) / 197,120 Gauss points
-# (profiles/k_flux_cylinder65k.md).
+# Roofline work unit of the gas-kinetic flux kernel k_flux<dim,1> (flux and
+# point values): FP64 flops per Gauss point of its direct formulation, one
+# moment product per slope vector, as ncu counted them on this workload
+# ((2 x DFMA + DADD + DMUL) / Gauss points).  The current kernel expands the
+# distribution polynomial once per side and executes fewer (second figures,
+# same ncu counters); achieved = unit x Gauss points / event time.
+# (profiles/k_flux_cylinder65k.md, profiles/k_flux_sphere.md)
 FLUX_FLOP_PER_GP_2D = 2947.1
-# DRAM bytes (read + write) of one k_flux<2,1> launch on this workload, from the
-# same ncu capture (cold-cache replay).
-FLUX_DRAM_BYTES_PER_LAUNCH = 24825856
-# The same figures for k_flux<3,1> (3 Gauss points per triangular face),
-# measured on the 16 x 16 x 16 sphere shell (147,456 tets, 297,984 faces:
-# 4,738.9 MFLOP and 153.2 MB of DRAM traffic per launch); the traffic is
-# scaled to the full shell by its number of faces (profiles/k_flux_sphere.md).
+FLUX_EXEC_FLOP_PER_GP_2D = 2631.1
 FLUX_FLOP_PER_GP_3D = 5301.1
-FLUX_DRAM_BYTES_PER_FACE_3D = 514.0
+FLUX_EXEC_FLOP_PER_GP_3D = 4670.4
+# DRAM bytes (read + write) of one k_flux<2,1> launch on this workload, and per
+# face of k_flux<3,1> on the 16 x 16 x 16 sphere shell (297,984 faces), scaled
+# to the full shell by its number of faces; ncu, cold-cache replay.
+FLUX_DRAM_BYTES_PER_LAUNCH = 24812800
+FLUX_DRAM_BYTES_PER_FACE_3D = 510.1
 
 
 def parse():
@@ -67,6 +69,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the wall-time-to-drop leg (vortex to 1e-10, cylinder plateau)")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-correction leg (train on batch cylinders, held-out Mach runs)")
     ap.add_argument("--profile-steps", action="store_true",
                     help="only warm-up + steps, for ncu launch lists")
     return ap.parse_args()
@@ -298,6 +302,7 @@ def run_ours(args):
     n_gp = info[0]["faces"] * (2 if dim == 2 else 3)
     fp64_peak = ctx.cgks_fma_probe(0) * 1e12
     flop_per_gp = FLUX_FLOP_PER_GP_2D if dim == 2 else FLUX_FLOP_PER_GP_3D
+    exec_per_gp = FLUX_EXEC_FLOP_PER_GP_2D if dim == 2 else FLUX_EXEC_FLOP_PER_GP_3D
     if dim == 2:
         traffic = FLUX_DRAM_BYTES_PER_LAUNCH
     else:
@@ -335,6 +340,9 @@ def run_ours(args):
     conv = None
     if not args.no_convergence and not sphere:
         conv = convergence_leg(cgks, stream)
+    learned = None
+    if not args.no_learned and not sphere:
+        learned = learned_leg(cgks, stream)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         if sphere:
@@ -360,12 +368,15 @@ def run_ours(args):
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_source": "FP64 FMA-chain probe of this library on this GPU (cgks_fma_probe)",
                      "flop_per_gp": flop_per_gp, "gauss_points": n_gp,
+                     "executed_flop_per_gp": exec_per_gp,
+                     "executed_tflops": exec_per_gp * n_gp / t_flux / 1e12,
                      "ms_per_launch": t_flux * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_cycle * args.steps,
         "clocks": clocks,
         "convergence": conv,
+        "learned": learned,
         "residual_rms_rho_last": float(rn[0, 0]),
         "counters": {"recon_fallback": int(counters[0]), "update_halved": int(counters[1]),
                      "update_zeroed": int(counters[2]), "nonfinite": int(counters[3])},
@@ -380,8 +391,14 @@ def _solve_to_drop(cgks, mesh, w, W0, G0, mode, max_cycles, stream, **cfg):
     """Whole solve from the initial state through cgks_vcycle (stops at the
     1e-10 drop of the density residual norm); the graphs are captured by one
     untimed cycle before the state is reset."""
-    import torch
     ctx = cgks.Context(stream=stream.cuda_stream, **cfg)
+    out = _solve_to_drop_ctx(ctx, mesh, w, W0, G0, mode, max_cycles)
+    ctx.close()
+    return out
+
+
+def _solve_to_drop_ctx(ctx, mesh, w, W0, G0, mode, max_cycles):
+    import torch
     ctx.setup(1, mesh, w, W0, G0)
     ctx.cgks_vcycle([1], 1, mode, np.zeros((1, 4, 2)))
     ctx.cgks_init_state(1, W0, G0)
@@ -394,7 +411,6 @@ def _solve_to_drop(cgks, mesh, w, W0, G0, mode, max_cycles, stream, **cfg):
     wall = time.perf_counter() - t0
     W = np.zeros_like(W0)
     ctx.cgks_get_state(1, W)
-    ctx.close()
     ncyc = int(done[0])
     drop = norms[:ncyc, 0, 0] / norms[0, 0, 0]
     out = {"rc": int(rc), "cycles": ncyc, "wall_s": wall, "final_drop": float(drop[-1]),
@@ -433,6 +449,63 @@ def convergence_leg(cgks, stream):
             entry["wall_ratio_fp64_over_mixed"] = fp64[f"wall_s_to_1e-{deepest}"] / mixed[f"wall_s_to_1e-{deepest}"]
         res[name] = entry
     return res
+
+
+HELD_OUT_MACH = (2.5, 5.5, 7.5)
+
+
+def learned_leg(cgks, stream, n_train_meshes=8, collect_cycles=30, eval_cycles=600):
+    """Learned coarse-grid correction against FP64 and MIXED, bounded so that
+    the default run stays within minutes: the network is trained on GPU
+    trajectories of the first n_train_meshes batch cylinders whose Mach number
+    is more than 0.1 away from 2.5, 5.5 and 7.5, then each mode runs
+    eval_cycles V-cycles at those held-out Mach numbers on the 65,536-cell
+    cylinder."""
+    import torch
+    t0 = time.perf_counter()
+    specs = [s for s in synth.batch_cylinder_specs()
+             if min(abs(s["mach"] - m) for m in HELD_OUT_MACH) > 0.1][:n_train_meshes]
+    union, grp, winf, W0 = synth.batch_cylinders(specs)
+    ctx = cgks.Context(stream=stream.cuda_stream)
+    ctx.cgks_mlp_set_params(synth.mlp_init_params())
+    ctx.setup(2, union, winf[0], W0)
+    ctx.cgks_set_groups(2, grp, winf)
+    t_setup = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.cgks_mlp_collect(2, collect_cycles, cgks.MIXED)
+    torch.cuda.synchronize()
+    t_collect = time.perf_counter() - t0
+    rows = ctx.cgks_mlp_dataset_size()
+    t0 = time.perf_counter()
+    l1 = ctx.cgks_mlp_train(6000, 16384, 1e-3, seed=1)
+    l2 = ctx.cgks_mlp_train(3000, 16384, 3e-4, seed=2)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    theta = ctx.cgks_mlp_get_params()
+    ctx.close()
+    out = {"train": {"meshes": len(specs), "mach": [round(s["mach"], 3) for s in specs],
+                     "cells": len(W0), "rows": int(rows), "setup_s": t_setup, "collect_s": t_collect,
+                     "train_s": t_train, "steps": 9000, "batch": 16384,
+                     "loss_first": float(np.mean(l1[:10])), "loss_last": float(np.mean(l2[-50:]))},
+           "eval_cycles": eval_cycles}
+    mesh = synth.cylinder_mesh(n_theta=64, n_r=32, ratio=1.05, n_refine=2)
+    for mach in HELD_OUT_MACH:
+        w = synth.freestream(mach)
+        W = synth.uniform_state(mesh, w)
+        res = {}
+        for name, mode in (("fp64", cgks.PLAIN_FP64), ("mixed", cgks.MIXED), ("learned", cgks.LEARNED)):
+            c = cgks.Context(stream=stream.cuda_stream)
+            c.cgks_mlp_set_params(theta)
+            r, _ = _solve_to_drop_ctx(c, mesh, w, W, None, mode, eval_cycles)
+            if mode == cgks.LEARNED:
+                r["learned_stats"] = c.cgks_learned_stats(1)
+            c.close()
+            res[name] = r
+        res["learned_vs_fp64_wall_ratio"] = res["fp64"]["wall_s"] / res["learned"]["wall_s"]
+        res["learned_vs_fp64_final_drop_ratio"] = res["learned"]["final_drop"] / res["fp64"]["final_drop"]
+        out[f"mach_{mach}"] = res
+    return out
 
 
 def lpt_partition(sizes, n_parts):

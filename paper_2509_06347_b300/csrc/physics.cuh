@@ -136,54 +136,6 @@ __device__ __forceinline__ void psi_mom(const Mom<DIM>& m, double* out) {
                         (DIM == 3 ? G<DIM, A, B, C + 2>(m) : 0.0) + m.xi2 * G<DIM, A, B, C>(m));
 }
 
-// <u^a v^b w^c xi^2 psi>
-template <int DIM, int A, int B, int C>
-__device__ __forceinline__ void psi_xi_mom(const Mom<DIM>& m, double* out) {
-  out[0] = m.xi2 * G<DIM, A, B, C>(m);
-  out[1] = m.xi2 * G<DIM, A + 1, B, C>(m);
-  if (DIM >= 2) out[2] = m.xi2 * G<DIM, A, B + 1, C>(m);
-  if (DIM == 3) out[3] = m.xi2 * G<DIM, A, B, C + 1>(m);
-  out[DIM + 1] = 0.5 * (m.xi2 * (G<DIM, A + 2, B, C>(m) + G<DIM, A, B + 2, C>(m) +
-                                 (DIM == 3 ? G<DIM, A, B, C + 2>(m) : 0.0)) +
-                        m.xi4 * G<DIM, A, B, C>(m));
-}
-
-// acc += <u^a v^b w^c psi (s . psi)>
-template <int DIM, int A, int B, int C>
-__device__ __forceinline__ void add_psi_s_mom(const Mom<DIM>& m, const double* s, double scale, double* acc) {
-  constexpr int NV = DIM + 2;
-  double t[NV];
-  psi_mom<DIM, A, B, C>(m, t);
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] += scale * s[0] * t[i];
-  psi_mom<DIM, A + 1, B, C>(m, t);
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] += scale * s[1] * t[i];
-  psi_mom<DIM, A, B + 1, C>(m, t);
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] += scale * s[2] * t[i];
-  if (DIM == 3) {
-    psi_mom<DIM, A, B, C + 1>(m, t);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] += scale * s[3] * t[i];
-  }
-  const double h = 0.5 * scale * s[DIM + 1];
-  psi_mom<DIM, A + 2, B, C>(m, t);
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] += h * t[i];
-  psi_mom<DIM, A, B + 2, C>(m, t);
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] += h * t[i];
-  if (DIM == 3) {
-    psi_mom<DIM, A, B, C + 2>(m, t);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] += h * t[i];
-  }
-  psi_xi_mom<DIM, A, B, C>(m, t);
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] += h * t[i];
-}
-
 // Solve <psi (a . psi)> = b for a (b normalised by density): explicit inverse
 // of the Maxwellian moment matrix.
 template <int DIM>
@@ -206,12 +158,80 @@ __device__ __forceinline__ void slope_solve(const Prim<DIM>& p, const PhysParams
   a[0] = b[0] - s - 0.5 * aE * e;
 }
 
-// <psi (a_n u + a_t1 v + a_t2 w)> with slopes a[DIM][NV], raised by u^KU
-template <int DIM, int KU>
-__device__ __forceinline__ void au_mom(const Mom<DIM>& m, const double (*a)[DIM + 2], double scale, double* acc) {
-  add_psi_s_mom<DIM, KU + 1, 0, 0>(m, a[0], scale, acc);
-  add_psi_s_mom<DIM, KU, 1, 0>(m, a[1], scale, acc);
-  if (DIM == 3) add_psi_s_mom<DIM, KU, 0, 1>(m, a[DIM - 1], scale, acc);
+// The part of the distribution that multiplies a Maxwellian in the flux and
+// point-value integrals is a polynomial in the velocity x = (u, v[, w]) and
+// xi^2:  c0 + cA sum_d (a_d . psi) x_d + cT (A . psi), with psi = (1, x,
+// (|x|^2 + xi^2) / 2).  Expanded once per side it reads
+//   P = p0 + pl.x + x^T pq x + h xi^2 + sum_d qc_d x_d (|x|^2 + xi^2),
+// so every moment <x^alpha psi P> is a short sum of products of the 1-D
+// moments instead of one matrix-vector product per slope vector.
+template <int DIM>
+struct Poly {
+  double p0, h;
+  double pl[DIM], qc[DIM];
+  double pq[DIM][DIM];  // upper triangle used
+};
+
+// A == nullptr: no time-slope term
+template <int DIM>
+__device__ __forceinline__ Poly<DIM> make_poly(double c0, double cA, double cT, const double (*a)[DIM + 2],
+                                               const double* A) {
+  constexpr int E = DIM + 1;
+  Poly<DIM> P;
+  const double hT = A ? 0.5 * cT * A[E] : 0.0;
+  P.p0 = A ? c0 + cT * A[0] : c0;
+  P.h = hT;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    P.pl[d] = A ? cA * a[d][0] + cT * A[1 + d] : cA * a[d][0];
+    P.qc[d] = 0.5 * cA * a[d][E];
+    P.pq[d][d] = cA * a[d][1 + d] + hT;
+#pragma unroll
+    for (int e = d + 1; e < DIM; ++e) P.pq[d][e] = cA * (a[d][1 + e] + a[e][1 + d]);
+  }
+  return P;
+}
+
+// <x^(a,b,c) P>  (XI = false)  or  <x^(a,b,c) xi^2 P>  (XI = true)
+template <int DIM, int A, int B, int C, bool XI>
+__device__ __forceinline__ double poly_mom(const Mom<DIM>& m, const Poly<DIM>& P) {
+  // velocity part without the xi^2 terms of P
+  double s = P.p0 * G<DIM, A, B, C>(m);
+  s += P.pl[0] * G<DIM, A + 1, B, C>(m) + P.pl[1] * G<DIM, A, B + 1, C>(m);
+  s += P.pq[0][0] * G<DIM, A + 2, B, C>(m) + P.pq[0][1] * G<DIM, A + 1, B + 1, C>(m) +
+       P.pq[1][1] * G<DIM, A, B + 2, C>(m);
+  double q0 = G<DIM, A + 3, B, C>(m) + G<DIM, A + 1, B + 2, C>(m);
+  double q1 = G<DIM, A + 2, B + 1, C>(m) + G<DIM, A, B + 3, C>(m);
+  if constexpr (DIM == 3) {
+    s += P.pl[2] * G<DIM, A, B, C + 1>(m);
+    s += P.pq[0][2] * G<DIM, A + 1, B, C + 1>(m) + P.pq[1][2] * G<DIM, A, B + 1, C + 1>(m) +
+         P.pq[2][2] * G<DIM, A, B, C + 2>(m);
+    q0 += G<DIM, A + 1, B, C + 2>(m);
+    q1 += G<DIM, A, B + 1, C + 2>(m);
+    const double q2 = G<DIM, A + 2, B, C + 1>(m) + G<DIM, A, B + 2, C + 1>(m) + G<DIM, A, B, C + 3>(m);
+    s += P.qc[2] * q2;
+  }
+  s += P.qc[0] * q0 + P.qc[1] * q1;
+  // terms of P carrying xi^2: h xi^2 + sum_d qc_d x_d xi^2
+  double t = P.h * G<DIM, A, B, C>(m) + P.qc[0] * G<DIM, A + 1, B, C>(m) + P.qc[1] * G<DIM, A, B + 1, C>(m);
+  if constexpr (DIM == 3) t += P.qc[2] * G<DIM, A, B, C + 1>(m);
+  if constexpr (XI) return m.xi2 * s + m.xi4 * t;
+  return s + m.xi2 * t;
+}
+
+// out = <u^A0 psi P>
+template <int DIM, int A0>
+__device__ __forceinline__ void poly_psi_mom(const Mom<DIM>& m, const Poly<DIM>& P, double* out) {
+  out[0] = poly_mom<DIM, A0, 0, 0, false>(m, P);
+  out[1] = poly_mom<DIM, A0 + 1, 0, 0, false>(m, P);
+  out[2] = poly_mom<DIM, A0, 1, 0, false>(m, P);
+  double e = poly_mom<DIM, A0 + 2, 0, 0, false>(m, P) + poly_mom<DIM, A0, 2, 0, false>(m, P) +
+             poly_mom<DIM, A0, 0, 0, true>(m, P);
+  if constexpr (DIM == 3) {
+    out[3] = poly_mom<DIM, A0, 0, 1, false>(m, P);
+    e += poly_mom<DIM, A0, 0, 2, false>(m, P);
+  }
+  out[DIM + 1] = 0.5 * e;
 }
 
 // Sum over directions d of (dF_d/dW) . dW_d for the Euler fluxes F_d along the
@@ -367,14 +387,11 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
   const double T4 = tau * (1.0 - e);
   const double T5 = tau * tau - tau * (dt + tau) * e;
   const double C1 = 1.0 - e, C2 = (dt + tau) * e - tau, C3 = dt - tau + tau * e;
-  // --- equilibrium part (g^c, full space)
+  // --- equilibrium part (g^c, full space): T1 + T2 (a_c . u) moments
   double fx[NV], wx[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) { fx[i] = 0.0; wx[i] = 0.0; }
-  psi_mom<DIM, 1, 0, 0>(mc, t);
-#pragma unroll
-  for (int i = 0; i < NV; ++i) fx[i] += T1 * t[i];
-  au_mom<DIM, 1>(mc, ac, T2, fx);
+  for (int i = 0; i < NV; ++i) wx[i] = 0.0;
+  poly_psi_mom<DIM, 1>(mc, make_poly<DIM>(T1, T2, 0.0, ac, nullptr), fx);
 #pragma unroll
   for (int i = 0; i < NV; ++i) fx[i] += T3 * UAc[i];
   if (POINT) {
@@ -391,20 +408,10 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
     const double(*a)[NV] = side == 0 ? al : ar;
     const double* Ak = side == 0 ? Al : Ar;
     const double rho = side == 0 ? pl.rho : pr.rho;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) { fx[i] = 0.0; wx[i] = 0.0; }
-    psi_mom<DIM, 1, 0, 0>(m, t);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) fx[i] += T4 * t[i];
-    au_mom<DIM, 1>(m, a, -(tau * T4 + T5), fx);
-    add_psi_s_mom<DIM, 1, 0, 0>(m, Ak, -tau * T4, fx);
-    if (POINT) {
-      psi_mom<DIM, 0, 0, 0>(m, t);
-#pragma unroll
-      for (int i = 0; i < NV; ++i) wx[i] += e * t[i];
-      au_mom<DIM, 0>(m, a, -e * (tau + dt), wx);
-      add_psi_s_mom<DIM, 0, 0, 0>(m, Ak, -e * tau, wx);
-    }
+    // flux: T4 - (tau T4 + T5) (a . u) - tau T4 (A . psi); point value at dt:
+    // e - e (tau + dt) (a . u) - e tau (A . psi)
+    poly_psi_mom<DIM, 1>(m, make_poly<DIM>(T4, -(tau * T4 + T5), -tau * T4, a, Ak), fx);
+    if (POINT) poly_psi_mom<DIM, 0>(m, make_poly<DIM>(e, -e * (tau + dt), -e * tau, a, Ak), wx);
 #pragma unroll
     for (int i = 0; i < NV; ++i) { F[i] += rho * fx[i]; Wt[i] += rho * wx[i]; }
   }
