@@ -88,15 +88,15 @@ def face_neighbours(cell_nodes):
     return nb.reshape(n, nvtx), faces
 
 
-def ring_submesh(mesh, seeds, rings=3):
+def ring_submesh(mesh, seeds, rings=3, adjacency=None):
     """The cells within `rings` face-neighbour steps of the seed cells, as a
     stand-alone mesh: nodes renumbered, original boundary faces kept with their
     tags and cut faces tagged far field.  Returns (submesh, cell ids in the
     original mesh, positions of the seeds in the submesh).  A cell's fine
     residual depends on two rings only, so the seeds' residuals are those of
-    the full mesh."""
+    the full mesh.  adjacency: face_neighbours(cell_nodes), if already known."""
     cn = np.asarray(mesh["cell_nodes"], np.int64)
-    nb, faces = face_neighbours(cn)
+    nb, faces = face_neighbours(cn) if adjacency is None else adjacency
     keep = np.zeros(len(cn), bool)
     keep[seeds] = True
     front = np.asarray(seeds)

@@ -8,7 +8,9 @@ cells are checked against the oracle on each sample's 3-ring submesh; the
 coarse KFVS residuals of sampled coarse cells against the oracle on their
 1-ring submeshes (both exact by locality, pinned in test_oracle_submesh.py).
 Whole V-cycles at full size are checked by a property that holds at any size:
-a uniform free stream stays unchanged, in FP64 and in MIXED."""
+a uniform free stream stays unchanged, in FP64 and in MIXED.  The batched
+sweep (64 cylinders, 7.1M cells in one union mesh, a free stream per member)
+is checked on sampled cells of every kind of member."""
 import numpy as np
 import pytest
 
@@ -198,3 +200,41 @@ def test_freestream_through_vcycles(case, lib, mode):
     finally:
         ctx.close()
     assert np.max(np.abs(W - W0)) <= 1e-12 * np.max(np.abs(W0))
+
+
+def test_batch_fine_residual_sampled(lib):
+    """The 64-cylinder batch at full size: residuals of sampled cells of the
+    union mesh, each against the oracle on its 3-ring submesh with its own
+    member's free stream."""
+    specs = synth.batch_cylinder_specs()
+    union, grp, winf, _ = synth.batch_cylinders(specs)
+    rng = np.random.default_rng(2509063470 + 4)
+    n = len(grp)
+    W = np.empty((n, 4))
+    G = np.empty((n, 4, 2))
+    for g in range(len(specs)):
+        sel = grp == g
+        W[sel], G[sel] = smooth_physical_state(rng, {"dim": 2, "cell_xyz": union["cell_xyz"][sel]}, winf[g])
+    ctx = lib.Context()
+    try:
+        ctx.setup(1, union, winf[0], W, G)
+        ctx.cgks_set_groups(1, grp, winf)
+        R, Gn, al = np.zeros((n, 4)), np.zeros((n, 4, 2)), np.zeros(n)
+        ctx.cgks_residual(1, 0, None, R, Gn, al)
+    finally:
+        ctx.close()
+    assert np.all(np.isfinite(R))
+    adj = face_neighbours(np.asarray(union["cell_nodes"], np.int64))
+    seeds = np.unique(rng.choice(n, 48, replace=False))
+    for g in np.unique(grp[seeds]):
+        sg = seeds[grp[seeds] == g]
+        sub, cells, sp = ring_submesh(union, sg, rings=3, adjacency=adj)
+        om = oracle.OracleMesh(sub, levels=1)
+        ro = om.residual(oracle.cfg_vector(2, winf=winf[g]), W[cells], G[cells], np.ones(len(cells)))
+        Fs = flux_scale(W[cells], 2)
+        Smax = float(np.max(om.faces(0)["S"]))
+        np.testing.assert_allclose(R[sg], ro["R"][sp], rtol=0, atol=1e-12 * Fs * Smax)
+        vol = om.cells(0)[0][sp]
+        np.testing.assert_allclose(Gn[sg] * vol[:, None, None], ro["grad"][sp] * vol[:, None, None], rtol=0,
+                                   atol=1e-12 * np.max(np.abs(W[cells])) * Smax)
+        np.testing.assert_allclose(al[sg], ro["alpha"][sp], rtol=1e-12, atol=1e-14)
