@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--flux-precision", default="fp64", choices=["fp64", "dword"],
+                    help="fine gas-kinetic flux in FP64 or in double-word on the FP32 pipes")
     ap.add_argument("--workload", default="cylinder", choices=["cylinder", "sphere", "batch"],
                     help="cylinder: one 65,536-cell Mach-5 cylinder; sphere: the Mach-6 cubed-sphere "
                          "tet shell (1,179,648 tets at --sphere-n 32); batch: 64 cylinders of "
@@ -243,7 +245,8 @@ def run_ours(args):
     n, dim = len(W0), int(mesh["dim"])
     nv = dim + 2
     stream = torch.cuda.Stream(device=dev)
-    ctx = cgks.Context(stream=stream.cuda_stream)
+    fprec = 1 if args.flux_precision == "dword" else 0
+    ctx = cgks.Context(stream=stream.cuda_stream, flux_precision=fprec)
     ctx.setup(1, mesh, w, W0)
     info = ctx.cgks_mesh_info(1)
     launches_per_cycle = ctx.cgks_launch_count(1, mode)
@@ -309,6 +312,37 @@ def run_ours(args):
         traffic = None if FLUX_DRAM_BYTES_PER_FACE_3D is None else FLUX_DRAM_BYTES_PER_FACE_3D * info[0]["faces"]
     achieved = None if flop_per_gp is None else flop_per_gp * n_gp / t_flux
 
+    # the same V-cycle with the fine gas-kinetic flux in double-word on the
+    # FP32 pipes (flux_precision 1), timed the same way
+    variant = None
+    if fprec == 0:
+        cv = cgks.Context(stream=stream.cuda_stream, flux_precision=1)
+        cv.setup(1, mesh, w, W0)
+        cv.cgks_vcycle_launch([1], max(3, args.warmup), mode)
+        barrier()
+        vev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                vev[k][0].record(stream)
+                cv.cgks_vcycle_launch([1], 1, mode)
+                vev[k][1].record(stream)
+            for k in range(args.steps):
+                cv.cgks_run_stage(1, 0)
+                flush.fill_(float(k))
+                fev[k][0].record(stream)
+                cv.cgks_run_stage(1, 1)
+                fev[k][1].record(stream)
+        barrier()
+        tv = sum(a.elapsed_time(b) for a, b in vev)
+        tf = sum(a.elapsed_time(b) for a, b in fev) / args.steps
+        variant = {"flux_precision": "dword (two-float words on the FP32 pipes, 2^-48 unit roundoff)",
+                   "value": n * args.steps / (tv * 1e-3), "unit": UNIT, "ms_per_step": tv / args.steps,
+                   "flux_ms_per_launch": tf,
+                   "flux_work_unit_tflops": flop_per_gp * n_gp / (tf * 1e-3) / 1e12 if flop_per_gp else None}
+        cv.close()
+
     # end to end through the public API with host buffers: state in, one
     # V-cycle, residual norms and state out, every step
     Wh = torch.empty((n, nv), dtype=torch.float64).pin_memory().numpy()
@@ -356,7 +390,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32" if mode == cgks.MIXED else "f64", "data": "synthetic",
+        "dtype": ("f64+f32" if mode == cgks.MIXED else "f64") + ("" if fprec == 0 else " (flux dword)"),
+        "data": "synthetic",
         "config": {"workload": wname, "cells": n, "levels": [lv["cells"] for lv in info],
                    "colors": [lv["colors"] for lv in info], "mode": args.mode, "mach": mach,
                    "cfl_imp": 10.0, "coarse_sweeps": 6, "l2": "flushed between timed steps (512 MB write)",
@@ -375,6 +410,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches_per_cycle * args.steps,
         "clocks": clocks,
+        "variant_dword_flux": variant,
         "convergence": conv,
         "learned": learned,
         "residual_rms_rho_last": float(rn[0, 0]),
@@ -438,15 +474,18 @@ def convergence_leg(cgks, stream):
     for name, mesh, w, W0, G0, cap, cfg in cases:
         fp64, W64 = _solve_to_drop(cgks, mesh, w, W0, G0, cgks.PLAIN_FP64, cap, stream, **cfg)
         mixed, Wmx = _solve_to_drop(cgks, mesh, w, W0, G0, cgks.MIXED, cap, stream, **cfg)
+        mdw, Wdw = _solve_to_drop(cgks, mesh, w, W0, G0, cgks.MIXED, cap, stream, flux_precision=1, **cfg)
         scale = np.max(np.abs(W64), axis=0)
         entry = {"cells": len(W0), "max_cycles": cap, "config": cfg or {"tau_c1": 0.01},
-                 "fp64": fp64, "mixed": mixed,
-                 "mixed_vs_fp64_state_max_rel_diff": float(np.max(np.abs(Wmx - W64) / scale))}
-        deepest = max(k for k in range(0, 11) if k == 0 or (f"cycles_to_1e-{k}" in fp64
-                                                            and f"cycles_to_1e-{k}" in mixed))
+                 "fp64": fp64, "mixed": mixed, "mixed_dword_flux": mdw,
+                 "mixed_vs_fp64_state_max_rel_diff": float(np.max(np.abs(Wmx - W64) / scale)),
+                 "mixed_dword_vs_fp64_state_max_rel_diff": float(np.max(np.abs(Wdw - W64) / scale))}
+        deepest = max(k for k in range(0, 11) if k == 0 or all(f"cycles_to_1e-{k}" in r for r in (fp64, mixed, mdw)))
         if deepest:
+            key = f"wall_s_to_1e-{deepest}"
             entry["common_drop"] = f"1e-{deepest}"
-            entry["wall_ratio_fp64_over_mixed"] = fp64[f"wall_s_to_1e-{deepest}"] / mixed[f"wall_s_to_1e-{deepest}"]
+            entry["wall_ratio_fp64_over_mixed"] = fp64[key] / mixed[key]
+            entry["wall_ratio_fp64_over_mixed_dword_flux"] = fp64[key] / mdw[key]
         res[name] = entry
     return res
 
@@ -595,7 +634,8 @@ def run_batch(args):
             "metric": METRIC, "value": N * args.steps / (t_tuned * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": t_tuned / args.steps,
             "higher_is_better": True, "scaling": "weak" if world > 1 else "strong", "vs_baseline": None,
-            "dtype": "f64+f32" if mode == cgks.MIXED else "f64", "data": "synthetic",
+            "dtype": ("f64+f32" if mode == cgks.MIXED else "f64") + ("" if fprec == 0 else " (flux dword)"),
+        "data": "synthetic",
             "config": {"workload": "batch64_cylinders_mach1.5-8", "meshes": len(specs), "cells_total": N,
                        "cells_this_rank": n, "levels_this_rank": [lv["cells"] for lv in info], "mode": args.mode,
                        "l2": "working set (GBs) far above L2", "parallelism": f"meshes split over {world} rank(s) "

@@ -81,6 +81,8 @@ typedef struct cgks_config {
   double df_gate;         /* learned correction applied only where DF >= df_gate (0.9) */
   int learned_judge_every;   /* plain judge cycle every this many learned-mode cycles; 0 = never (20) */
   double learned_max_error;  /* judge relative RMS error above which the network is disabled (0.5) */
+  int flux_precision;        /* fine gas-kinetic flux: 0 FP64; 1 double-word (two floats, ~48-bit
+                                significand, about 3.6e-15 unit roundoff) on the FP32 pipes (0) */
 } cgks_config;
 
 typedef struct cgks_ctx cgks_t;

@@ -106,6 +106,7 @@ struct MeshDev {
   std::vector<std::unique_ptr<DBuf>> pool;
   DevFine fine{};
   double *G = nullptr, *coef = nullptr, *Fface = nullptr, *Wface = nullptr, *aface = nullptr;
+  dword* coef_dw = nullptr;  // double-word copy of coef for the FP32-pipe flux (flux_precision 1)
   double *gradnew = nullptr, *norm_part = nullptr, *last_norm = nullptr, *hist = nullptr;
   double* stage = nullptr;  // staging for permuted I/O, size n * max(nv*dim, ncoef*nv)
   size_t stage_elems = 0;
@@ -272,7 +273,7 @@ void alloc_level_state(MeshDev& M, LevelDev& L) {
   L.dW32 = dalloc<float>(P, (size_t)L.n * nv);
 }
 
-void build_levels_device(MeshDev& M) {
+void build_levels_device(MeshDev& M, const cgks_config& cfg) {
   const FineLevel& F = M.H.fine;
   const int dim = F.dim, nfc = F.nfc;
   M.lev.clear();
@@ -342,6 +343,7 @@ void build_levels_device(MeshDev& M) {
   auto& P = M.pool;
   M.G = dalloc<double>(P, (size_t)F.n * nv * dim);
   M.coef = dalloc<double>(P, (size_t)F.n * nv * nc);
+  if (cfg.flux_precision == 1) M.coef_dw = dalloc<dword>(P, (size_t)F.n * nv * nc);
   M.Fface = dalloc<double>(P, (size_t)F.nf * nv);
   M.Wface = dalloc<double>(P, (size_t)F.nf * nv);
   M.aface = dalloc<double>(P, F.nf);
@@ -365,7 +367,7 @@ void launch_recon(cgks_t* h, MeshDev& M) {
   LevelDev& L = M.lev[0];
   k_recon<DIM><<<blocks_for(L.n, M.blk[B_RECON]), M.blk[B_RECON], 0, h->stream>>>(
       M.fine, L.W, M.G, L.alpha, M.winf, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, h->cfg.weno_gamma_high,
-      h->cfg.weno_eps, M.coef, L.dte, L.dti, M.cnt);
+      h->cfg.weno_eps, M.coef, L.dte, L.dti, M.cnt, M.coef_dw);
 }
 
 template <int DIM>
@@ -374,9 +376,17 @@ void launch_flux(cgks_t* h, MeshDev& M, bool point = true) {
   constexpr int NGP = Dims<DIM>::NGP, FPW = 32 / NGP;
   const int64_t warps = (M.fine.nf + FPW - 1) / FPW;
   const int64_t threads = warps * 32;
-  auto kern = point ? k_flux<DIM, true> : k_flux<DIM, false>;
-  kern<<<blocks_for(threads, M.blk[B_FLUX]), M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, phys(h->cfg, DIM),
-                                                               M.Fface, M.Wface, M.aface, L.W, L.rface);
+  const int nb = blocks_for(threads, M.blk[B_FLUX]);
+  const PhysParams P = phys(h->cfg, DIM);
+  if (h->cfg.flux_precision == 1) {
+    auto kern = point ? k_flux<DIM, true, dword> : k_flux<DIM, false, dword>;
+    kern<<<nb, M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef_dw, L.dte, M.winf, phys_dword(P), P.gamma, M.Fface,
+                                              M.Wface, M.aface, L.W, L.rface);
+  } else {
+    auto kern = point ? k_flux<DIM, true, double> : k_flux<DIM, false, double>;
+    kern<<<nb, M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, P, P.gamma, M.Fface, M.Wface, M.aface,
+                                              L.W, L.rface);
+  }
 }
 
 // fine residual: slopes_update -> G <- alpha * grad_new; want_diag -> LU-SGS D;
@@ -701,6 +711,7 @@ int cgks_default_config(cgks_config* c) {
   c->df_gate = 0.9;
   c->learned_judge_every = 20;
   c->learned_max_error = 0.5;
+  c->flux_precision = 0;
   return CGKS_OK;
 }
 
@@ -715,6 +726,7 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
   if (h->cfg.n_pre != 1 || h->cfg.n_post != 0 || h->cfg.n_sweep_coarse < 1 || !(h->cfg.gamma > 1.0) ||
       h->cfg.r_safety != 1.0 || !(h->cfg.weno_gamma_high > 0.0 && h->cfg.weno_gamma_high <= 1.0) ||
       h->cfg.check_every < 1 || (h->cfg.fine_smoother != 0 && h->cfg.fine_smoother != 1) ||
+      (h->cfg.flux_precision != 0 && h->cfg.flux_precision != 1) ||
       (h->cfg.df_relax != 0 && h->cfg.df_relax != 1) || (h->cfg.df_prolong != 0 && h->cfg.df_prolong != 1)) {
     delete h;
     return CGKS_ERR_ARG;
@@ -801,7 +813,7 @@ int cgks_upload_hierarchy(cgks_t* h, int mesh_id, int n_levels, const int32_t* c
     M.pool.clear();
     M.nlev = n_levels;
     build_fine_device(M);
-    build_levels_device(M);
+    build_levels_device(M, h->cfg);
     M.has_hierarchy = true;
     M.has_state = false;
     CK(cudaDeviceSynchronize());

@@ -101,10 +101,10 @@ __device__ __forceinline__ void quad_pq(int q, int& a, int& b) {
   }
 }
 
-template <int DIM>
-__device__ __forceinline__ double eval_poly(const double* c, const double* X) {
+template <int DIM, typename S = double>
+__device__ __forceinline__ S eval_poly(const S* c, const S* X) {
   using D = Dims<DIM>;
-  double s = c[0];
+  S s = c[0];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) s += c[1 + d] * X[d];
 #pragma unroll
@@ -115,8 +115,8 @@ __device__ __forceinline__ double eval_poly(const double* c, const double* X) {
   }
   return s;
 }
-template <int DIM>
-__device__ __forceinline__ void grad_poly(const double* c, const double* X, double* g) {
+template <int DIM, typename S = double>
+__device__ __forceinline__ void grad_poly(const S* c, const S* X, S* g) {
   using D = Dims<DIM>;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) g[d] = c[1 + d];
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
                                                   const double* __restrict__ winf, double gamma, double cfl_exp,
                                                   double cfl_imp, double gam_hi, double weps, double* __restrict__ coef,
                                                   double* __restrict__ dte, double* __restrict__ dti,
-                                                  Counters* __restrict__ cnt) {
+                                                  Counters* __restrict__ cnt, dword* __restrict__ coef_dw) {
   using D = Dims<DIM>;
   constexpr int NV = D::NV, NFC = D::NFC, NK = D::NK, NC = D::NC, NCOL = D::NCOL;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -320,17 +320,54 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
   for (int v = 0; v < NV; ++v)
 #pragma unroll
     for (int k = 0; k < NC; ++k) out[v * NC + k] = P[v][k];
+  if (coef_dw) {  // the same coefficients as double-words for the FP32-pipe flux
+    dword* od = coef_dw + (size_t)c * NV * NC;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) od[v * NC + k] = dword(P[v][k]);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // K2: gas-kinetic flux, one lane per (face, Gauss point)
 // ---------------------------------------------------------------------------
-template <int DIM, bool POINT>
-__global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __restrict__ coef,
+// value and gradient of one variable's polynomial at a Gauss point; a shared
+// call in the double-word flux (see OutOfLine)
+template <int DIM, typename S>
+__device__ __forceinline__ void eval_grad(const S* c, const S* x, S& W, S* g) {
+  using D = Dims<DIM>;
+  S cc[D::NC];
+#pragma unroll
+  for (int k = 0; k < D::NC; ++k) cc[k] = c[k];
+  W = eval_poly<DIM, S>(cc, x);
+  grad_poly<DIM, S>(cc, x, g);
+}
+template <int DIM, typename S>
+__device__ __noinline__ void eval_grad_ool(const S* c, const S* x, S& W, S* g) {
+  eval_grad<DIM, S>(c, x, W, g);
+}
+template <int DIM, typename S>
+__device__ __forceinline__ void eval_grad_c(const S* c, const S* x, S& W, S* g) {
+  if constexpr (OutOfLine<S>::value) eval_grad_ool<DIM, S>(c, x, W, g);
+  else eval_grad<DIM, S>(c, x, W, g);
+}
+
+// warp shuffle of a flux-code scalar
+__device__ __forceinline__ double shfl_s(double x, int src) { return __shfl_sync(0xffffffffu, x, src); }
+__device__ __forceinline__ dword shfl_s(dword x, int src) {
+  return dword(__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src));
+}
+
+// Gas-kinetic face flux.  S = double: FP64; S = dword: the same arithmetic in
+// double-word on the FP32 pipes (coefficients read as double-word, geometry and
+// time step converted once per Gauss point, results returned in FP64).
+template <int DIM, bool POINT, typename S = double>
+__global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(DevFine M, const S* __restrict__ coef,
                                                  const double* __restrict__ dte, const double* __restrict__ winf,
-                                                 PhysParams P, double* __restrict__ Fface, double* __restrict__ Wface,
-                                                 double* __restrict__ aface, const double* __restrict__ Wc,
-                                                 double* __restrict__ rface) {
+                                                 PhysT<S> P, double gamma, double* __restrict__ Fface,
+                                                 double* __restrict__ Wface, double* __restrict__ aface,
+                                                 const double* __restrict__ Wc, double* __restrict__ rface) {
   using D = Dims<DIM>;
   constexpr int NV = D::NV, NC = D::NC, NGP = D::NGP;
   constexpr int FPW = 32 / NGP;  // faces per warp
@@ -339,64 +376,55 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __rest
   const int g = lane % NGP;
   const int f = warp * FPW + lane / NGP;
   const bool active = lane < FPW * NGP && f < M.nf;
-  double Fs[NV], Ws[NV], af = 1.0;
+  S Fs[NV], Ws[NV], af = S(1.0);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) { Fs[v] = 0.0; Ws[v] = 0.0; }
+  for (int v = 0; v < NV; ++v) { Fs[v] = S(0.0); Ws[v] = S(0.0); }
   if (active) {
     const int L = M.fL[f], R = M.fR[f];
-    double n[DIM];
+    S n[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) n[d] = M.fn[(size_t)f * DIM + d];
-    const Frame<DIM> fr = make_frame<DIM>(n);
-    double Wl[NV], gl[NV][DIM], Wr[NV], gr[NV][DIM];
+    for (int d = 0; d < DIM; ++d) n[d] = S(M.fn[(size_t)f * DIM + d]);
+    const Frame<DIM, S> fr = make_frame<DIM, S>(n);
+    S Wl[NV], gl[NV][DIM], Wr[NV], gr[NV][DIM];
     {
       const double* X = M.XL + ((size_t)f * NGP + g) * DIM;
-      double x[DIM];
+      S x[DIM];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) x[d] = X[d];
-      const double* c = coef + (size_t)L * NV * NC;
+      for (int d = 0; d < DIM; ++d) x[d] = S(X[d]);
+      const S* c = coef + (size_t)L * NV * NC;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        double cc[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) cc[k] = c[v * NC + k];
-        Wl[v] = eval_poly<DIM>(cc, x);
-        grad_poly<DIM>(cc, x, gl[v]);
-      }
+      for (int v = 0; v < NV; ++v) eval_grad_c<DIM, S>(c + v * NC, x, Wl[v], gl[v]);
     }
     double dt = dte[L];
     if (R >= 0) {
       const double* X = M.XR + ((size_t)f * NGP + g) * DIM;
-      double x[DIM];
+      S x[DIM];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) x[d] = X[d];
-      const double* c = coef + (size_t)R * NV * NC;
+      for (int d = 0; d < DIM; ++d) x[d] = S(X[d]);
+      const S* c = coef + (size_t)R * NV * NC;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        double cc[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) cc[k] = c[v * NC + k];
-        Wr[v] = eval_poly<DIM>(cc, x);
-        grad_poly<DIM>(cc, x, gr[v]);
-      }
+      for (int v = 0; v < NV; ++v) eval_grad_c<DIM, S>(c + v * NC, x, Wr[v], gr[v]);
       dt = fmin(dt, dte[R]);
     } else {
       const int tag = M.ftag[f];
-      const double* wi = winf + NV * (M.grp ? M.grp[L] : 0);
-      ghost_state<DIM>(tag, wi, n, Wl, Wr);
-      ghost_grad<DIM>(tag, wi, n, gl, gr);
+      const double* wd = winf + NV * (M.grp ? M.grp[L] : 0);
+      S wi[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) wi[v] = S(wd[v]);
+      ghost_state<DIM, S>(tag, wi, n, Wl, Wr);
+      ghost_grad<DIM, S>(tag, wi, n, gl, gr);
     }
-    double wl[NV], wr[NV], Gl[DIM][NV], Gr[DIM][NV], Fl[NV], Wt[NV];
-    to_local<DIM>(fr, Wl, wl);
-    to_local<DIM>(fr, Wr, wr);
-    grad_to_local<DIM>(fr, gl, Gl);
-    grad_to_local<DIM>(fr, gr, Gr);
-    gks_flux<DIM, POINT>(P, wl, Gl, wr, Gr, dt, Fl, Wt);
-    af = df_factor<DIM>(P.gamma, wl, wr);
-    double Fg[NV], Wg[NV];
-    to_global<DIM>(fr, Fl, Fg);
-    to_global<DIM>(fr, Wt, Wg);
-    const double w = M.fS[f] * (1.0 / NGP);  // equal Gauss weights on every face
+    S wl[NV], wr[NV], Gl[DIM][NV], Gr[DIM][NV], Fl[NV], Wt[NV];
+    to_local<DIM, S>(fr, Wl, wl);
+    to_local<DIM, S>(fr, Wr, wr);
+    grad_to_local<DIM, S>(fr, gl, Gl);
+    grad_to_local<DIM, S>(fr, gr, Gr);
+    gks_flux<DIM, POINT, S>(P, wl, Gl, wr, Gr, S(dt), Fl, Wt);
+    af = df_factor<DIM, S>(P.gamma, wl, wr);
+    S Fg[NV], Wg[NV];
+    to_global<DIM, S>(fr, Fl, Fg);
+    to_global<DIM, S>(fr, Wt, Wg);
+    const S w = S(M.fS[f] * (1.0 / NGP));  // equal Gauss weights on every face
 #pragma unroll
     for (int v = 0; v < NV; ++v) { Fs[v] = w * Fg[v]; Ws[v] = w * Wg[v]; }
   }
@@ -407,20 +435,20 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __rest
     const int src = leader + k;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double fo = __shfl_sync(0xffffffffu, Fs[v], src < 32 ? src : lane);
-      const double wo = __shfl_sync(0xffffffffu, Ws[v], src < 32 ? src : lane);
+      const S fo = shfl_s(Fs[v], src < 32 ? src : lane);
+      const S wo = shfl_s(Ws[v], src < 32 ? src : lane);
       if (g == 0) { Fs[v] += fo; Ws[v] += wo; }
     }
-    const double ao = __shfl_sync(0xffffffffu, af, src < 32 ? src : lane);
+    const S ao = shfl_s(af, src < 32 ? src : lane);
     if (g == 0) af *= ao;
   }
   if (active && g == 0) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      Fface[(size_t)f * NV + v] = Fs[v];
-      if (POINT) Wface[(size_t)f * NV + v] = Ws[v];
+      Fface[(size_t)f * NV + v] = static_cast<double>(Fs[v]);
+      if (POINT) Wface[(size_t)f * NV + v] = static_cast<double>(Ws[v]);
     }
-    aface[f] = af;
+    aface[f] = static_cast<double>(af);
     // spectral radius of the LU-SGS splitting at the mean of the cell means
     const int L = M.fL[f], R = M.fR[f];
     double n[DIM], WL[NV], WR[NV];
@@ -434,7 +462,7 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevFine M, const double* __rest
     } else {
       ghost_state<DIM>(M.ftag[f], winf + NV * (M.grp ? M.grp[L] : 0), n, WL, WR);
     }
-    rface[f] = spectral_radius<DIM, double>(P.gamma, WL, WR, n);
+    rface[f] = spectral_radius<DIM, double>(gamma, WL, WR, n);
   }
 }
 

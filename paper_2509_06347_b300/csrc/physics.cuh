@@ -19,15 +19,21 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "dword.cuh"
+
 namespace cgks {
 
-struct PhysParams {
-  double gamma;   // ratio of specific heats
-  double K;       // internal degrees of freedom
-  double c1, c2;  // collision-time coefficients
+// Parameters of the gas-kinetic flux in the scalar type S of the flux code
+// (double, or double-word for the FP32-pipe variant).
+template <typename S>
+struct PhysT {
+  S gamma;   // ratio of specific heats
+  S K;       // internal degrees of freedom
+  S c1, c2;  // collision-time coefficients
   // derived on the host: N = K + dim, 2/N, 4/N
-  double N, twoOverN, fourOverN;
+  S N, twoOverN, fourOverN;
 };
+using PhysParams = PhysT<double>;
 
 inline PhysParams make_phys(double gamma, int dim, double c1, double c2) {
   PhysParams p;
@@ -41,76 +47,88 @@ inline PhysParams make_phys(double gamma, int dim, double c1, double c2) {
   return p;
 }
 
+inline PhysT<dword> phys_dword(const PhysParams& p) {
+  PhysT<dword> q;
+  q.gamma = dword(p.gamma);
+  q.K = dword(p.K);
+  q.c1 = dword(p.c1);
+  q.c2 = dword(p.c2);
+  q.N = dword(p.N);
+  q.twoOverN = dword(p.twoOverN);
+  q.fourOverN = dword(p.fourOverN);
+  return q;
+}
+
 // Moments of a (half-)Maxwellian normalised by density: mu[n] = <u^n> in the
 // normal direction over the chosen half line (or full line), mv/mw over the
 // tangential lines, xi2/xi4 the internal-energy moments.
-template <int DIM>
+template <int DIM, typename S = double>
 struct Mom {
-  double mu[7];
-  double mv[6];
-  double mw[6];
-  double xi2, xi4;
+  S mu[7];
+  S mv[6];
+  S mw[6];
+  S xi2, xi4;
 };
 
 // primitive: rho, U[DIM], lambda = rho / (2 p)
-template <int DIM>
+template <int DIM, typename S = double>
 struct Prim {
-  double rho, irho, lam, h;  // h = 1 / (2 lambda)
-  double U[DIM];
+  S rho, irho, lam, h;  // h = 1 / (2 lambda)
+  S U[DIM];
 };
 
-template <int DIM>
-__device__ __forceinline__ Prim<DIM> to_prim(const double* W, const PhysParams& P) {
-  Prim<DIM> p;
+template <int DIM, typename S>
+__device__ __forceinline__ Prim<DIM, S> to_prim(const S* W, const PhysT<S>& P) {
+  Prim<DIM, S> p;
   p.rho = W[0];
-  p.irho = 1.0 / W[0];
-  double ke = 0.0;
+  p.irho = S(1.0) / W[0];
+  S ke = S(0.0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     p.U[d] = W[1 + d] * p.irho;
     ke += p.U[d] * W[1 + d];
   }
   // E - rho|U|^2/2 = (K + DIM) rho / (4 lambda) = (K + DIM) rho h / 2
-  p.h = (W[DIM + 1] - 0.5 * ke) * p.irho * P.twoOverN;
-  p.lam = 0.5 / p.h;
+  p.h = (W[DIM + 1] - S(0.5) * ke) * p.irho * P.twoOverN;
+  p.lam = S(0.5) / p.h;
   return p;
 }
 
 // tangential and internal-energy moments (shared by full and half spaces)
-template <int DIM>
-__device__ __forceinline__ void tang_moments(const Prim<DIM>& p, double K, Mom<DIM>& m) {
-  const double h = p.h;
-  const double V = DIM > 1 ? p.U[1 % DIM] : 0.0;
-  m.mv[0] = 1.0;
+template <int DIM, typename S>
+__device__ __forceinline__ void tang_moments(const Prim<DIM, S>& p, S K, Mom<DIM, S>& m) {
+  const S h = p.h;
+  const S V = p.U[1];
+  m.mv[0] = S(1.0);
   m.mv[1] = V;
 #pragma unroll
   for (int n = 0; n < 4; ++n) m.mv[n + 2] = V * m.mv[n + 1] + (n + 1) * h * m.mv[n];
   if constexpr (DIM == 3) {
-    const double Wv = p.U[DIM - 1];
-    m.mw[0] = 1.0;
+    const S Wv = p.U[DIM - 1];
+    m.mw[0] = S(1.0);
     m.mw[1] = Wv;
 #pragma unroll
     for (int n = 0; n < 4; ++n) m.mw[n + 2] = Wv * m.mw[n + 1] + (n + 1) * h * m.mw[n];
   } else {
 #pragma unroll
-    for (int n = 0; n < 6; ++n) m.mw[n] = n == 0 ? 1.0 : 0.0;
+    for (int n = 0; n < 6; ++n) m.mw[n] = n == 0 ? S(1.0) : S(0.0);
   }
   m.xi2 = K * h;
-  m.xi4 = (K * K + 2.0 * K) * h * h;
+  m.xi4 = (K * K + S(2.0) * K) * h * h;
 }
 
 // normal moments: half = 0 full line, +1 u > 0, -1 u < 0
-template <int DIM>
-__device__ __forceinline__ void normal_moments(const Prim<DIM>& p, int half, Mom<DIM>& m) {
-  const double U = p.U[0];
-  const double h = p.h;
+template <int DIM, typename S>
+__device__ __forceinline__ void normal_moments(const Prim<DIM, S>& p, int half, Mom<DIM, S>& m) {
+  const S U = p.U[0];
+  const S h = p.h;
   if (half == 0) {
-    m.mu[0] = 1.0;
+    m.mu[0] = S(1.0);
     m.mu[1] = U;
   } else {
-    const double sl = sqrt(p.lam);
-    const double te = exp(-p.lam * U * U) * (0.5 * M_2_SQRTPI) * (sl * h);  // e^{-lam U^2} / (2 sqrt(pi lam))
-    const double hs = 0.5 * erfc(-half * sl * U);
+    const S sl = sqrt(p.lam);
+    const S te = exp(-p.lam * U * U) * S(0.5 * M_2_SQRTPI) * (sl * h);  // e^{-lam U^2} / (2 sqrt(pi lam))
+    const S hs = S(0.5) * erfc(S(-half) * sl * U);
     m.mu[0] = hs;
     m.mu[1] = U * hs + half * te;
   }
@@ -119,43 +137,48 @@ __device__ __forceinline__ void normal_moments(const Prim<DIM>& p, int half, Mom
 }
 
 // G(a, b, c) = <u^a v^b w^c>
-template <int DIM, int A, int B, int C>
-__device__ __forceinline__ double G(const Mom<DIM>& m) {
-  if (DIM == 2 && C > 0) return 0.0;
-  return m.mu[A] * m.mv[B] * (DIM == 3 ? m.mw[C] : 1.0);
+template <int DIM, int A, int B, int C, typename S>
+__device__ __forceinline__ S G(const Mom<DIM, S>& m) {
+  if constexpr (DIM == 2 && C > 0) return S(0.0);
+  if constexpr (DIM == 3) return m.mu[A] * m.mv[B] * m.mw[C];
+  else return m.mu[A] * m.mv[B];
 }
 
 // <u^a v^b w^c psi>
-template <int DIM, int A, int B, int C>
-__device__ __forceinline__ void psi_mom(const Mom<DIM>& m, double* out) {
+template <int DIM, int A, int B, int C, typename S>
+__device__ __forceinline__ void psi_mom(const Mom<DIM, S>& m, S* out) {
   out[0] = G<DIM, A, B, C>(m);
   out[1] = G<DIM, A + 1, B, C>(m);
-  if (DIM >= 2) out[2] = G<DIM, A, B + 1, C>(m);
-  if (DIM == 3) out[3] = G<DIM, A, B, C + 1>(m);
-  out[DIM + 1] = 0.5 * (G<DIM, A + 2, B, C>(m) + G<DIM, A, B + 2, C>(m) +
-                        (DIM == 3 ? G<DIM, A, B, C + 2>(m) : 0.0) + m.xi2 * G<DIM, A, B, C>(m));
+  out[2] = G<DIM, A, B + 1, C>(m);
+  if constexpr (DIM == 3) {
+    out[3] = G<DIM, A, B, C + 1>(m);
+    out[DIM + 1] = S(0.5) * (G<DIM, A + 2, B, C>(m) + G<DIM, A, B + 2, C>(m) + G<DIM, A, B, C + 2>(m) +
+                             m.xi2 * G<DIM, A, B, C>(m));
+  } else {
+    out[DIM + 1] = S(0.5) * (G<DIM, A + 2, B, C>(m) + G<DIM, A, B + 2, C>(m) + m.xi2 * G<DIM, A, B, C>(m));
+  }
 }
 
 // Solve <psi (a . psi)> = b for a (b normalised by density): explicit inverse
 // of the Maxwellian moment matrix.
-template <int DIM>
-__device__ __forceinline__ void slope_solve(const Prim<DIM>& p, const PhysParams& P, const double* b, double* a) {
-  double q2 = 0.0, ub = 0.0;
+template <int DIM, typename S>
+__device__ __forceinline__ void slope_solve(const Prim<DIM, S>& p, const PhysT<S>& P, const S* b, S* a) {
+  S q2 = S(0.0), ub = S(0.0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     q2 += p.U[d] * p.U[d];
     ub += p.U[d] * (b[1 + d] - p.U[d] * b[0]);
   }
-  const double e = q2 + P.N * p.h;
-  const double aE = (P.fourOverN * p.lam * p.lam) * (2.0 * b[DIM + 1] - e * b[0] - 2.0 * ub);
-  double s = 0.0;
+  const S e = q2 + P.N * p.h;
+  const S aE = (P.fourOverN * p.lam * p.lam) * (S(2.0) * b[DIM + 1] - e * b[0] - S(2.0) * ub);
+  S s = S(0.0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    a[1 + d] = 2.0 * p.lam * (b[1 + d] - p.U[d] * b[0]) - p.U[d] * aE;
+    a[1 + d] = S(2.0) * p.lam * (b[1 + d] - p.U[d] * b[0]) - p.U[d] * aE;
     s += p.U[d] * a[1 + d];
   }
   a[DIM + 1] = aE;
-  a[0] = b[0] - s - 0.5 * aE * e;
+  a[0] = b[0] - s - S(0.5) * aE * e;
 }
 
 // The part of the distribution that multiplies a Maxwellian in the flux and
@@ -165,26 +188,25 @@ __device__ __forceinline__ void slope_solve(const Prim<DIM>& p, const PhysParams
 //   P = p0 + pl.x + x^T pq x + h xi^2 + sum_d qc_d x_d (|x|^2 + xi^2),
 // so every moment <x^alpha psi P> is a short sum of products of the 1-D
 // moments instead of one matrix-vector product per slope vector.
-template <int DIM>
+template <int DIM, typename S = double>
 struct Poly {
-  double p0, h;
-  double pl[DIM], qc[DIM];
-  double pq[DIM][DIM];  // upper triangle used
+  S p0, h;
+  S pl[DIM], qc[DIM];
+  S pq[DIM][DIM];  // upper triangle used
 };
 
 // A == nullptr: no time-slope term
-template <int DIM>
-__device__ __forceinline__ Poly<DIM> make_poly(double c0, double cA, double cT, const double (*a)[DIM + 2],
-                                               const double* A) {
+template <int DIM, typename S>
+__device__ __forceinline__ Poly<DIM, S> make_poly(S c0, S cA, S cT, const S (*a)[DIM + 2], const S* A) {
   constexpr int E = DIM + 1;
-  Poly<DIM> P;
-  const double hT = A ? 0.5 * cT * A[E] : 0.0;
+  Poly<DIM, S> P;
+  const S hT = A ? S(0.5) * cT * A[E] : S(0.0);
   P.p0 = A ? c0 + cT * A[0] : c0;
   P.h = hT;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     P.pl[d] = A ? cA * a[d][0] + cT * A[1 + d] : cA * a[d][0];
-    P.qc[d] = 0.5 * cA * a[d][E];
+    P.qc[d] = S(0.5) * cA * a[d][E];
     P.pq[d][d] = cA * a[d][1 + d] + hT;
 #pragma unroll
     for (int e = d + 1; e < DIM; ++e) P.pq[d][e] = cA * (a[d][1 + e] + a[e][1 + d]);
@@ -193,114 +215,170 @@ __device__ __forceinline__ Poly<DIM> make_poly(double c0, double cA, double cT, 
 }
 
 // <x^(a,b,c) P>  (XI = false)  or  <x^(a,b,c) xi^2 P>  (XI = true)
-template <int DIM, int A, int B, int C, bool XI>
-__device__ __forceinline__ double poly_mom(const Mom<DIM>& m, const Poly<DIM>& P) {
+template <int DIM, int A, int B, int C, bool XI, typename S>
+__device__ __forceinline__ S poly_mom(const Mom<DIM, S>& m, const Poly<DIM, S>& P) {
   // velocity part without the xi^2 terms of P
-  double s = P.p0 * G<DIM, A, B, C>(m);
+  S s = P.p0 * G<DIM, A, B, C>(m);
   s += P.pl[0] * G<DIM, A + 1, B, C>(m) + P.pl[1] * G<DIM, A, B + 1, C>(m);
   s += P.pq[0][0] * G<DIM, A + 2, B, C>(m) + P.pq[0][1] * G<DIM, A + 1, B + 1, C>(m) +
        P.pq[1][1] * G<DIM, A, B + 2, C>(m);
-  double q0 = G<DIM, A + 3, B, C>(m) + G<DIM, A + 1, B + 2, C>(m);
-  double q1 = G<DIM, A + 2, B + 1, C>(m) + G<DIM, A, B + 3, C>(m);
+  S q0 = G<DIM, A + 3, B, C>(m) + G<DIM, A + 1, B + 2, C>(m);
+  S q1 = G<DIM, A + 2, B + 1, C>(m) + G<DIM, A, B + 3, C>(m);
   if constexpr (DIM == 3) {
     s += P.pl[2] * G<DIM, A, B, C + 1>(m);
     s += P.pq[0][2] * G<DIM, A + 1, B, C + 1>(m) + P.pq[1][2] * G<DIM, A, B + 1, C + 1>(m) +
          P.pq[2][2] * G<DIM, A, B, C + 2>(m);
     q0 += G<DIM, A + 1, B, C + 2>(m);
     q1 += G<DIM, A, B + 1, C + 2>(m);
-    const double q2 = G<DIM, A + 2, B, C + 1>(m) + G<DIM, A, B + 2, C + 1>(m) + G<DIM, A, B, C + 3>(m);
+    const S q2 = G<DIM, A + 2, B, C + 1>(m) + G<DIM, A, B + 2, C + 1>(m) + G<DIM, A, B, C + 3>(m);
     s += P.qc[2] * q2;
   }
   s += P.qc[0] * q0 + P.qc[1] * q1;
   // terms of P carrying xi^2: h xi^2 + sum_d qc_d x_d xi^2
-  double t = P.h * G<DIM, A, B, C>(m) + P.qc[0] * G<DIM, A + 1, B, C>(m) + P.qc[1] * G<DIM, A, B + 1, C>(m);
+  S t = P.h * G<DIM, A, B, C>(m) + P.qc[0] * G<DIM, A + 1, B, C>(m) + P.qc[1] * G<DIM, A, B + 1, C>(m);
   if constexpr (DIM == 3) t += P.qc[2] * G<DIM, A, B, C + 1>(m);
   if constexpr (XI) return m.xi2 * s + m.xi4 * t;
   return s + m.xi2 * t;
 }
 
 // out = <u^A0 psi P>
-template <int DIM, int A0>
-__device__ __forceinline__ void poly_psi_mom(const Mom<DIM>& m, const Poly<DIM>& P, double* out) {
+template <int DIM, int A0, typename S>
+__device__ __forceinline__ void poly_psi_mom(const Mom<DIM, S>& m, const Poly<DIM, S>& P, S* out) {
   out[0] = poly_mom<DIM, A0, 0, 0, false>(m, P);
   out[1] = poly_mom<DIM, A0 + 1, 0, 0, false>(m, P);
   out[2] = poly_mom<DIM, A0, 1, 0, false>(m, P);
-  double e = poly_mom<DIM, A0 + 2, 0, 0, false>(m, P) + poly_mom<DIM, A0, 2, 0, false>(m, P) +
-             poly_mom<DIM, A0, 0, 0, true>(m, P);
+  S e = poly_mom<DIM, A0 + 2, 0, 0, false>(m, P) + poly_mom<DIM, A0, 2, 0, false>(m, P) +
+        poly_mom<DIM, A0, 0, 0, true>(m, P);
   if constexpr (DIM == 3) {
     out[3] = poly_mom<DIM, A0, 0, 1, false>(m, P);
     e += poly_mom<DIM, A0, 0, 2, false>(m, P);
   }
-  out[DIM + 1] = 0.5 * e;
+  out[DIM + 1] = S(0.5) * e;
 }
 
 // Sum over directions d of (dF_d/dW) . dW_d for the Euler fluxes F_d along the
 // local axes: for a Maxwellian g(W(x)), int u_d psi dg/dx_d = d/dx_d F_d(W), so
 // this equals <psi (a.u)> of the full-space Maxwellian (times rho) without
 // forming the velocity moments.
-template <int DIM>
-__device__ __forceinline__ void euler_flux_divergence(double gamma, const double* W, const double (*dW)[DIM + 2],
-                                                      double* out) {
+template <int DIM, typename S>
+__device__ __forceinline__ void euler_flux_divergence(S gamma, const S* W, const S (*dW)[DIM + 2], S* out) {
   constexpr int NV = DIM + 2;
-  const double ir = 1.0 / W[0];
-  double u[DIM], q2 = 0.0;
+  const S ir = S(1.0) / W[0];
+  S u[DIM], q2 = S(0.0);
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
     u[i] = W[1 + i] * ir;
     q2 += u[i] * u[i];
   }
-  const double p = (gamma - 1.0) * (W[NV - 1] - 0.5 * W[0] * q2);
-  const double H = (W[NV - 1] + p) * ir;  // total enthalpy
+  const S p = (gamma - S(1.0)) * (W[NV - 1] - S(0.5) * W[0] * q2);
+  const S H = (W[NV - 1] + p) * ir;  // total enthalpy
 #pragma unroll
-  for (int v = 0; v < NV; ++v) out[v] = 0.0;
+  for (int v = 0; v < NV; ++v) out[v] = S(0.0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const double* g = dW[d];
+    const S* g = dW[d];
     // derivatives of primitive quantities along this direction
-    double du[DIM], udu = 0.0;
+    S du[DIM], udu = S(0.0);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
       du[i] = (g[1 + i] - u[i] * g[0]) * ir;
       udu += u[i] * du[i];
     }
-    const double dp = (gamma - 1.0) * (g[NV - 1] - 0.5 * g[0] * q2 - W[0] * udu);
+    const S dp = (gamma - S(1.0)) * (g[NV - 1] - S(0.5) * g[0] * q2 - W[0] * udu);
     out[0] += g[1 + d];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) out[1 + i] += g[1 + d] * u[i] + W[1 + d] * du[i];
     out[1 + d] += dp;
-    const double dH = (g[NV - 1] + dp - H * g[0]) * ir;
+    const S dH = (g[NV - 1] + dp - H * g[0]) * ir;
     out[NV - 1] += g[1 + d] * H + W[1 + d] * dH;
   }
 }
 
 // (dF_n/dW) . v for the Euler flux through the local normal (first axis)
-template <int DIM>
-__device__ __forceinline__ void euler_flux_jvp_normal(double gamma, const double* W, const double* v, double* out) {
+template <int DIM, typename S>
+__device__ __forceinline__ void euler_flux_jvp_normal(S gamma, const S* W, const S* v, S* out) {
   constexpr int NV = DIM + 2;
-  double g[DIM][NV];
+  S g[DIM][NV];
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
 #pragma unroll
-    for (int i = 0; i < NV; ++i) g[d][i] = d == 0 ? v[i] : 0.0;
-  euler_flux_divergence<DIM>(gamma, W, g, out);
+    for (int i = 0; i < NV; ++i) g[d][i] = d == 0 ? v[i] : S(0.0);
+  euler_flux_divergence<DIM, S>(gamma, W, g, out);
+}
+
+// Out-of-line variants for the double-word flux.  Its code, fully inlined, is
+// several times larger than the FP64 code and overflows the instruction cache,
+// so the helpers called several times per Gauss point become shared calls
+// there; the FP64 instantiation keeps them inline.
+template <typename S>
+struct OutOfLine { static constexpr bool value = false; };
+template <>
+struct OutOfLine<dword> { static constexpr bool value = true; };
+
+template <int DIM, typename S>
+__device__ __noinline__ void slope_solve_ool(const Prim<DIM, S>& p, const PhysT<S>& P, const S* b, S* a) {
+  slope_solve<DIM, S>(p, P, b, a);
+}
+template <int DIM, typename S>
+__device__ __forceinline__ void slope_solve_c(const Prim<DIM, S>& p, const PhysT<S>& P, const S* b, S* a) {
+  if constexpr (OutOfLine<S>::value) slope_solve_ool<DIM, S>(p, P, b, a);
+  else slope_solve<DIM, S>(p, P, b, a);
+}
+template <int DIM, typename S>
+__device__ __noinline__ void euler_flux_divergence_ool(S gamma, const S* W, const S (*dW)[DIM + 2], S* out) {
+  euler_flux_divergence<DIM, S>(gamma, W, dW, out);
+}
+template <int DIM, typename S>
+__device__ __forceinline__ void euler_flux_divergence_c(S gamma, const S* W, const S (*dW)[DIM + 2], S* out) {
+  if constexpr (OutOfLine<S>::value) euler_flux_divergence_ool<DIM, S>(gamma, W, dW, out);
+  else euler_flux_divergence<DIM, S>(gamma, W, dW, out);
+}
+template <int DIM, typename S>
+__device__ __noinline__ void moments_ool(const Prim<DIM, S>& p, S K, int half, Mom<DIM, S>& m) {
+  tang_moments<DIM, S>(p, K, m);
+  normal_moments<DIM, S>(p, half, m);
+}
+template <int DIM, typename S>
+__device__ __forceinline__ void moments_c(const Prim<DIM, S>& p, S K, int half, Mom<DIM, S>& m) {
+  if constexpr (OutOfLine<S>::value) {
+    moments_ool<DIM, S>(p, K, half, m);
+  } else {
+    tang_moments<DIM, S>(p, K, m);
+    normal_moments<DIM, S>(p, half, m);
+  }
+}
+// <u^A0 psi (c0 + cA (a . u) + cT (A . psi))>
+template <int DIM, int A0, typename S>
+__device__ __forceinline__ void kin_moments(const Mom<DIM, S>& m, S c0, S cA, S cT, const S (*a)[DIM + 2],
+                                            const S* A, S* out) {
+  poly_psi_mom<DIM, A0, S>(m, make_poly<DIM, S>(c0, cA, cT, a, A), out);
+}
+template <int DIM, int A0, typename S>
+__device__ __noinline__ void kin_moments_ool(const Mom<DIM, S>& m, S c0, S cA, S cT, const S (*a)[DIM + 2],
+                                             const S* A, S* out) {
+  kin_moments<DIM, A0, S>(m, c0, cA, cT, a, A, out);
+}
+template <int DIM, int A0, typename S>
+__device__ __forceinline__ void kin_moments_c(const Mom<DIM, S>& m, S c0, S cA, S cT, const S (*a)[DIM + 2],
+                                              const S* A, S* out) {
+  if constexpr (OutOfLine<S>::value) kin_moments_ool<DIM, A0, S>(m, c0, cA, cT, a, A, out);
+  else kin_moments<DIM, A0, S>(m, c0, cA, cT, a, A, out);
 }
 
 // Gas-kinetic flux (time average over [0, dt]) and point value at t = dt in
 // the local frame (u normal).  G?[d][v] = derivative along local direction d.
-template <int DIM, bool POINT = true>
-__device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*Gl)[DIM + 2], const double* Wr,
-                         const double (*Gr)[DIM + 2], double dt, double* F, double* Wt) {
+template <int DIM, bool POINT = true, typename S = double>
+__device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2], const S* Wr, const S (*Gr)[DIM + 2],
+                         S dt, S* F, S* Wt) {
   constexpr int NV = DIM + 2;
-  const double K = P.K;
-  const Prim<DIM> pl = to_prim<DIM>(Wl, P), pr = to_prim<DIM>(Wr, P);
+  const S K = P.K;
+  const Prim<DIM, S> pl = to_prim<DIM, S>(Wl, P), pr = to_prim<DIM, S>(Wr, P);
   // half-space moments for the kinetic part
-  Mom<DIM> ml, mr;
-  tang_moments<DIM>(pl, K, ml);
-  tang_moments<DIM>(pr, K, mr);
-  normal_moments<DIM>(pl, +1, ml);
-  normal_moments<DIM>(pr, -1, mr);
+  Mom<DIM, S> ml, mr;
+  moments_c<DIM, S>(pl, K, +1, ml);
+  moments_c<DIM, S>(pr, K, -1, mr);
   // interface equilibrium from half-space moments (Eq. compatibility2)
-  double Wc[NV], t[NV];
+  S Wc[NV], t[NV];
   psi_mom<DIM, 0, 0, 0>(ml, Wc);
   psi_mom<DIM, 0, 0, 0>(mr, t);
 #pragma unroll
@@ -308,13 +386,13 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
   {
     // vacuum (both sides moving apart): no admissible interface equilibrium;
     // take the collisionless limit, i.e. the KFVS flux, point value W^c
-    double kc = 0.0;
+    S kc = S(0.0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) kc += Wc[1 + d] * Wc[1 + d];
-    const double pwc = (P.gamma - 1.0) * (Wc[DIM + 1] - 0.5 * kc / Wc[0]);
-    const double pwl = pl.rho * pl.h, pwr = pr.rho * pr.h;  // p = rho / (2 lambda)
-    if (!(Wc[0] > 1e-10 * (pl.rho + pr.rho)) || !(pwc > 1e-10 * (pwl + pwr))) {
-      double a[NV], b[NV];
+    const S pwc = (P.gamma - S(1.0)) * (Wc[DIM + 1] - S(0.5) * kc / Wc[0]);
+    const S pwl = pl.rho * pl.h, pwr = pr.rho * pr.h;  // p = rho / (2 lambda)
+    if (!(Wc[0] > S(1e-10) * (pl.rho + pr.rho)) || !(pwc > S(1e-10) * (pwl + pwr))) {
+      S a[NV], b[NV];
       psi_mom<DIM, 1, 0, 0>(ml, a);
       psi_mom<DIM, 1, 0, 0>(mr, b);
 #pragma unroll
@@ -325,73 +403,72 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
       return;
     }
   }
-  const Prim<DIM> pc = to_prim<DIM>(Wc, P);
-  Mom<DIM> mc;
-  tang_moments<DIM>(pc, K, mc);
-  normal_moments<DIM>(pc, 0, mc);
+  const Prim<DIM, S> pc = to_prim<DIM, S>(Wc, P);
+  Mom<DIM, S> mc;
+  moments_c<DIM, S>(pc, K, 0, mc);
   // spatial slopes of the three Maxwellians (Eq. co)
-  double al[DIM][NV], ar[DIM][NV], ac[DIM][NV], b[NV];
+  S al[DIM][NV], ar[DIM][NV], ac[DIM][NV], b[NV];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const double il = pl.irho, irr = pr.irho, ic = pc.irho;
+    const S il = pl.irho, irr = pr.irho, ic = pc.irho;
 #pragma unroll
     for (int i = 0; i < NV; ++i) b[i] = Gl[d][i] * il;
-    slope_solve<DIM>(pl, P, b, al[d]);
+    slope_solve_c<DIM, S>(pl, P, b, al[d]);
 #pragma unroll
     for (int i = 0; i < NV; ++i) b[i] = Gr[d][i] * irr;
-    slope_solve<DIM>(pr, P, b, ar[d]);
+    slope_solve_c<DIM, S>(pr, P, b, ar[d]);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) b[i] = 0.5 * (Gl[d][i] + Gr[d][i]) * ic;
-    slope_solve<DIM>(pc, P, b, ac[d]);
+    for (int i = 0; i < NV; ++i) b[i] = S(0.5) * (Gl[d][i] + Gr[d][i]) * ic;
+    slope_solve_c<DIM, S>(pc, P, b, ac[d]);
   }
   // time slopes from <A + a.u> = 0, with <psi (a.u)> of a full-space
   // Maxwellian given by the Euler-flux divergence of its slopes
-  double Al[NV], Ar[NV], Ac[NV];
+  S Al[NV], Ar[NV], Ac[NV];
   {
-    double s[NV];
-    euler_flux_divergence<DIM>(P.gamma, Wl, Gl, s);
+    S s[NV];
+    euler_flux_divergence_c<DIM, S>(P.gamma, Wl, Gl, s);
 #pragma unroll
     for (int i = 0; i < NV; ++i) s[i] *= -pl.irho;
-    slope_solve<DIM>(pl, P, s, Al);
-    euler_flux_divergence<DIM>(P.gamma, Wr, Gr, s);
+    slope_solve_c<DIM, S>(pl, P, s, Al);
+    euler_flux_divergence_c<DIM, S>(P.gamma, Wr, Gr, s);
 #pragma unroll
     for (int i = 0; i < NV; ++i) s[i] *= -pr.irho;
-    slope_solve<DIM>(pr, P, s, Ar);
+    slope_solve_c<DIM, S>(pr, P, s, Ar);
   }
   // interface Maxwellian: <psi (a_c.u)> = Euler-flux divergence; its time slope
   // gives <psi (A_c.psi)> = W_t = -<psi (a_c.u)> and <u psi (A_c.psi)> = J_n W_t
-  double PAc[NV], UAc[NV];
+  S PAc[NV], UAc[NV];
   {
-    double gc[DIM][NV];
+    S gc[DIM][NV];
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
-      for (int i = 0; i < NV; ++i) gc[d][i] = 0.5 * (Gl[d][i] + Gr[d][i]);
-    euler_flux_divergence<DIM>(P.gamma, Wc, gc, PAc);
-    double wt[NV];
+      for (int i = 0; i < NV; ++i) gc[d][i] = S(0.5) * (Gl[d][i] + Gr[d][i]);
+    euler_flux_divergence_c<DIM, S>(P.gamma, Wc, gc, PAc);
+    S wt[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       PAc[i] *= pc.irho;
       wt[i] = -PAc[i];
     }
-    euler_flux_jvp_normal<DIM>(P.gamma, Wc, wt, UAc);
+    euler_flux_jvp_normal<DIM, S>(P.gamma, Wc, wt, UAc);
   }
   (void)Ac;
   // collision time and time integrals
-  const double pL = pl.rho * pl.h, pR = pr.rho * pr.h;
-  const double tau = P.c1 * dt + P.c2 * fabs(pL - pR) / (pL + pR) * dt;
-  const double e = exp(-dt / tau);
-  const double T1 = dt - tau * (1.0 - e);
-  const double T2 = -tau * dt + 2.0 * tau * tau - tau * (dt + 2.0 * tau) * e;
-  const double T3 = 0.5 * dt * dt - tau * dt + tau * tau * (1.0 - e);
-  const double T4 = tau * (1.0 - e);
-  const double T5 = tau * tau - tau * (dt + tau) * e;
-  const double C1 = 1.0 - e, C2 = (dt + tau) * e - tau, C3 = dt - tau + tau * e;
+  const S pL = pl.rho * pl.h, pR = pr.rho * pr.h;
+  const S tau = P.c1 * dt + P.c2 * fabs(pL - pR) / (pL + pR) * dt;
+  const S e = exp(-dt / tau);
+  const S T1 = dt - tau * (S(1.0) - e);
+  const S T2 = -tau * dt + S(2.0) * tau * tau - tau * (dt + S(2.0) * tau) * e;
+  const S T3 = S(0.5) * dt * dt - tau * dt + tau * tau * (S(1.0) - e);
+  const S T4 = tau * (S(1.0) - e);
+  const S T5 = tau * tau - tau * (dt + tau) * e;
+  const S C1 = S(1.0) - e, C2 = (dt + tau) * e - tau, C3 = dt - tau + tau * e;
   // --- equilibrium part (g^c, full space): T1 + T2 (a_c . u) moments
-  double fx[NV], wx[NV];
+  S fx[NV], wx[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) wx[i] = 0.0;
-  poly_psi_mom<DIM, 1>(mc, make_poly<DIM>(T1, T2, 0.0, ac, nullptr), fx);
+  for (int i = 0; i < NV; ++i) wx[i] = S(0.0);
+  kin_moments_c<DIM, 1, S>(mc, T1, T2, S(0.0), ac, nullptr, fx);
 #pragma unroll
   for (int i = 0; i < NV; ++i) fx[i] += T3 * UAc[i];
   if (POINT) {
@@ -404,18 +481,18 @@ __device__ void gks_flux(const PhysParams& P, const double* Wl, const double (*G
   // --- kinetic part (g^l on u > 0, g^r on u < 0)
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
-    const Mom<DIM>& m = side == 0 ? ml : mr;
-    const double(*a)[NV] = side == 0 ? al : ar;
-    const double* Ak = side == 0 ? Al : Ar;
-    const double rho = side == 0 ? pl.rho : pr.rho;
+    const Mom<DIM, S>& m = side == 0 ? ml : mr;
+    const S(*a)[NV] = side == 0 ? al : ar;
+    const S* Ak = side == 0 ? Al : Ar;
+    const S rho = side == 0 ? pl.rho : pr.rho;
     // flux: T4 - (tau T4 + T5) (a . u) - tau T4 (A . psi); point value at dt:
     // e - e (tau + dt) (a . u) - e tau (A . psi)
-    poly_psi_mom<DIM, 1>(m, make_poly<DIM>(T4, -(tau * T4 + T5), -tau * T4, a, Ak), fx);
-    if (POINT) poly_psi_mom<DIM, 0>(m, make_poly<DIM>(e, -e * (tau + dt), -e * tau, a, Ak), wx);
+    kin_moments_c<DIM, 1, S>(m, T4, -(tau * T4 + T5), -tau * T4, a, Ak, fx);
+    if (POINT) kin_moments_c<DIM, 0, S>(m, e, -e * (tau + dt), -e * tau, a, Ak, wx);
 #pragma unroll
     for (int i = 0; i < NV; ++i) { F[i] += rho * fx[i]; Wt[i] += rho * wx[i]; }
   }
-  const double idt = 1.0 / dt;
+  const S idt = S(1.0) / dt;
 #pragma unroll
   for (int i = 0; i < NV; ++i) F[i] *= idt;
 }
@@ -439,34 +516,34 @@ __device__ __forceinline__ void kfvs_flux(const PhysParams& P, const double* Wl,
 }
 
 // DF point factor 1 / (1 + D^2) from local-frame states (Sec 3.3)
-template <int DIM>
-__device__ __forceinline__ double df_factor(double gamma, const double* Wl, const double* Wr) {
-  double kl = 0.0, kr = 0.0;
+template <int DIM, typename S = double>
+__device__ __forceinline__ S df_factor(S gamma, const S* Wl, const S* Wr) {
+  S kl = S(0.0), kr = S(0.0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) { kl += Wl[1 + d] * Wl[1 + d]; kr += Wr[1 + d] * Wr[1 + d]; }
-  const double pl = (gamma - 1.0) * (Wl[DIM + 1] - 0.5 * kl / Wl[0]);
-  const double pr = (gamma - 1.0) * (Wr[DIM + 1] - 0.5 * kr / Wr[0]);
-  const double il = 1.0 / (Wl[0] * sqrt(gamma * pl / Wl[0]));  // 1 / (rho c)
-  const double ir = 1.0 / (Wr[0] * sqrt(gamma * pr / Wr[0]));
-  const double dp = fabs(pl - pr);
-  double D = dp / pl + dp / pr;
+  const S pl = (gamma - S(1.0)) * (Wl[DIM + 1] - S(0.5) * kl / Wl[0]);
+  const S pr = (gamma - S(1.0)) * (Wr[DIM + 1] - S(0.5) * kr / Wr[0]);
+  const S il = S(1.0) / (Wl[0] * sqrt(gamma * pl / Wl[0]));  // 1 / (rho c)
+  const S ir = S(1.0) / (Wr[0] * sqrt(gamma * pr / Wr[0]));
+  const S dp = fabs(pl - pr);
+  S D = dp / pl + dp / pr;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const double dm = Wl[1 + d] * il - Wr[1 + d] * ir;
+    const S dm = Wl[1 + d] * il - Wr[1 + d] * ir;
     D += dm * dm;
   }
-  return 1.0 / (1.0 + D * D);
+  return S(1.0) / (S(1.0) + D * D);
 }
 
 // ---------------------------------------------------------------------------
 // frames: rows n, t1, t2
-template <int DIM>
+template <int DIM, typename S = double>
 struct Frame {
-  double r[DIM][DIM];
+  S r[DIM][DIM];
 };
-template <int DIM>
-__device__ __forceinline__ Frame<DIM> make_frame(const double* n) {
-  Frame<DIM> f;
+template <int DIM, typename S>
+__device__ __forceinline__ Frame<DIM, S> make_frame(const S* n) {
+  Frame<DIM, S> f;
   if constexpr (DIM == 2) {
     f.r[0][0] = n[0]; f.r[0][1] = n[1];
     f.r[1][0] = -n[1]; f.r[1][1] = n[0];
@@ -474,34 +551,34 @@ __device__ __forceinline__ Frame<DIM> make_frame(const double* n) {
     int a = 0;
     if (fabs(n[1]) < fabs(n[a])) a = 1;
     if (fabs(n[DIM - 1]) < fabs(n[a])) a = 2;
-    double e[3] = {0.0, 0.0, 0.0};
-    e[a] = 1.0;
-    double t1[3] = {n[1] * e[2] - n[2] * e[1], n[2] * e[0] - n[0] * e[2], n[0] * e[1] - n[1] * e[0]};
-    const double il = 1.0 / sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+    S e[3] = {S(0.0), S(0.0), S(0.0)};
+    e[a] = S(1.0);
+    S t1[3] = {n[1] * e[2] - n[2] * e[1], n[2] * e[0] - n[0] * e[2], n[0] * e[1] - n[1] * e[0]};
+    const S il = S(1.0) / sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
     for (int i = 0; i < 3; ++i) t1[i] *= il;
-    const double t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
+    const S t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
     for (int i = 0; i < DIM; ++i) { f.r[0][i] = n[i]; f.r[1][i] = t1[i]; f.r[DIM - 1][i] = t2[i]; }
   }
   return f;
 }
-template <int DIM>
-__device__ __forceinline__ void to_local(const Frame<DIM>& f, const double* W, double* Wl) {
+template <int DIM, typename S>
+__device__ __forceinline__ void to_local(const Frame<DIM, S>& f, const S* W, S* Wl) {
   Wl[0] = W[0];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    double s = 0.0;
+    S s = S(0.0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) s += f.r[a][d] * W[1 + d];
     Wl[1 + a] = s;
   }
   Wl[DIM + 1] = W[DIM + 1];
 }
-template <int DIM>
-__device__ __forceinline__ void to_global(const Frame<DIM>& f, const double* Wl, double* W) {
+template <int DIM, typename S>
+__device__ __forceinline__ void to_global(const Frame<DIM, S>& f, const S* Wl, S* W) {
   W[0] = Wl[0];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    double s = 0.0;
+    S s = S(0.0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) s += f.r[a][d] * Wl[1 + a];
     W[1 + d] = s;
@@ -509,20 +586,20 @@ __device__ __forceinline__ void to_global(const Frame<DIM>& f, const double* Wl,
   W[DIM + 1] = Wl[DIM + 1];
 }
 // global gradient g[v][d] -> local derivatives Gl[a][v'] (direction a, rotated variable v')
-template <int DIM>
-__device__ __forceinline__ void grad_to_local(const Frame<DIM>& f, const double (*g)[DIM], double (*Gl)[DIM + 2]) {
+template <int DIM, typename S>
+__device__ __forceinline__ void grad_to_local(const Frame<DIM, S>& f, const S (*g)[DIM], S (*Gl)[DIM + 2]) {
   constexpr int NV = DIM + 2;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    double dir[NV];
+    S dir[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double s = 0.0;
+      S s = S(0.0);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) s += f.r[a][d] * g[v][d];
       dir[v] = s;
     }
-    to_local<DIM>(f, dir, Gl[a]);
+    to_local<DIM, S>(f, dir, Gl[a]);
   }
 }
 
@@ -595,25 +672,25 @@ __device__ __forceinline__ T spectral_radius(T gamma, const T* Wa, const T* Wb, 
 // boundary ghosts, global frame
 enum : int { kTagWall = 1, kTagFarfield = 2 };
 
-template <int DIM>
-__device__ __forceinline__ bool inflow(const double* winf, const double* n) {
-  double un = 0.0;
+template <int DIM, typename S = double>
+__device__ __forceinline__ bool inflow(const S* winf, const S* n) {
+  S un = S(0.0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) un += winf[1 + d] * n[d];
-  return un < 0.0;
+  return un < S(0.0);
 }
-template <int DIM>
-__device__ __forceinline__ void ghost_state(int tag, const double* winf, const double* n, const double* W, double* Wg) {
+template <int DIM, typename S = double>
+__device__ __forceinline__ void ghost_state(int tag, const S* winf, const S* n, const S* W, S* Wg) {
   constexpr int NV = DIM + 2;
   if (tag == kTagWall) {
-    double mn = 0.0;
+    S mn = S(0.0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) mn += W[1 + d] * n[d];
 #pragma unroll
     for (int i = 0; i < NV; ++i) Wg[i] = W[i];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) Wg[1 + d] = W[1 + d] - 2.0 * mn * n[d];
-  } else if (inflow<DIM>(winf, n)) {
+    for (int d = 0; d < DIM; ++d) Wg[1 + d] = W[1 + d] - S(2.0) * mn * n[d];
+  } else if (inflow<DIM, S>(winf, n)) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) Wg[i] = winf[i];
   } else {
@@ -622,38 +699,38 @@ __device__ __forceinline__ void ghost_state(int tag, const double* winf, const d
   }
 }
 // gradient g[v][d] of the ghost field
-template <int DIM>
-__device__ __forceinline__ void ghost_grad(int tag, const double* winf, const double* n, const double (*g)[DIM],
-                                           double (*gg)[DIM]) {
+template <int DIM, typename S = double>
+__device__ __forceinline__ void ghost_grad(int tag, const S* winf, const S* n, const S (*g)[DIM],
+                                           S (*gg)[DIM]) {
   constexpr int NV = DIM + 2;
   if (tag == kTagWall) {
     // scalars: (I - 2nn^T) grad;  momentum: (I - 2nn^T) (dm/dx) (I - 2nn^T)
-    double t[NV][DIM];
+    S t[NV][DIM];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double s = 0.0;
+      S s = S(0.0);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) s += g[v][d] * n[d];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) t[v][d] = g[v][d] - 2.0 * s * n[d];
+      for (int d = 0; d < DIM; ++d) t[v][d] = g[v][d] - S(2.0) * s * n[d];
     }
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      double s = 0.0;
+      S s = S(0.0);
 #pragma unroll
       for (int e = 0; e < DIM; ++e) s += n[e] * t[1 + e][d];
 #pragma unroll
-      for (int e = 0; e < DIM; ++e) t[1 + e][d] -= 2.0 * n[e] * s;
+      for (int e = 0; e < DIM; ++e) t[1 + e][d] -= S(2.0) * n[e] * s;
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int d = 0; d < DIM; ++d) gg[v][d] = t[v][d];
-  } else if (inflow<DIM>(winf, n)) {
+  } else if (inflow<DIM, S>(winf, n)) {
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) gg[v][d] = 0.0;
+      for (int d = 0; d < DIM; ++d) gg[v][d] = S(0.0);
   } else {
 #pragma unroll
     for (int v = 0; v < NV; ++v)
