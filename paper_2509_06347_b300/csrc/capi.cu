@@ -183,6 +183,7 @@ struct cgks_ctx {
   std::map<int, std::unique_ptr<cgks::MeshDev>> meshes;
   std::string err;
   std::vector<std::unique_ptr<cgks::DBuf>> scratch;  // point-evaluation helpers
+  int sms = 148;                                      // SM count of the device (set at creation)
 };
 
 namespace cgks {
@@ -195,6 +196,14 @@ MeshDev& get_mesh(cgks_t* h, int id) {
 }
 
 PhysParams phys(const cgks_config& c, int dim) { return make_phys(c.gamma, dim, c.tau_c1, c.tau_c2); }
+
+// Block size for a launch over n items: the (tuned) size b, halved down to one
+// warp while the grid would give fewer than two blocks per SM, so that the
+// small coarse-level and per-colour launches spread over every SM.
+int fit_block(const cgks_t* h, int64_t n, int b) {
+  while (b > 32 && (n + b - 1) / b < 2 * (int64_t)h->sms) b >>= 1;
+  return b;
+}
 
 // ---- device structures from the host hierarchy ----------------------------
 void build_fine_device(MeshDev& M) {
@@ -425,33 +434,44 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
   for (int c = 0; c < nc - 1; ++c) {
     const int lo = L.color_off[c], hi = L.color_off[c + 1];
     if (hi > lo)
-      k_sweep<DIM, T, 0><<<blocks_for(hi - lo, M.blk[B_SWEEP]), M.blk[B_SWEEP], 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
-                                                                         L.rface, h->cfg.gamma, dWs, dW);
+    {
+      const int b = fit_block(h, hi - lo, M.blk[B_SWEEP]);
+      k_sweep<DIM, T, 0><<<blocks_for(hi - lo, b), b, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
+                                                                     L.rface, h->cfg.gamma, dWs, dW);
+    }
   }
   {
     const int lo = L.color_off[nc - 1], hi = L.color_off[nc];
     if (hi > lo)
-      k_sweep<DIM, T, 2><<<blocks_for(hi - lo, M.blk[B_SWEEP]), M.blk[B_SWEEP], 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
-                                                                         L.rface, h->cfg.gamma, dWs, dW);
+    {
+      const int b = fit_block(h, hi - lo, M.blk[B_SWEEP]);
+      k_sweep<DIM, T, 2><<<blocks_for(hi - lo, b), b, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
+                                                                     L.rface, h->cfg.gamma, dWs, dW);
+    }
   }
   for (int c = nc - 2; c >= 0; --c) {
     const int lo = L.color_off[c], hi = L.color_off[c + 1];
     if (hi > lo)
-      k_sweep<DIM, T, 1><<<blocks_for(hi - lo, M.blk[B_SWEEP]), M.blk[B_SWEEP], 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
-                                                                         L.rface, h->cfg.gamma, dWs, dW);
+    {
+      const int b = fit_block(h, hi - lo, M.blk[B_SWEEP]);
+      k_sweep<DIM, T, 1><<<blocks_for(hi - lo, b), b, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
+                                                                     L.rface, h->cfg.gamma, dWs, dW);
+    }
   }
   const bool fine = &L == &M.lev[0];
   const bool masked = fine && !M.lgrp.empty();
-  k_update<DIM, T><<<blocks_for(L.n, M.blk[B_UPDATE]), M.blk[B_UPDATE], 0, h->stream>>>(
+  const int bu = fit_block(h, L.n, M.blk[B_UPDATE]);
+  k_update<DIM, T><<<blocks_for(L.n, bu), bu, 0, h->stream>>>(
       L.n, h->cfg.gamma, L.W, dW, M.cnt, masked ? M.lgrp[0] : nullptr, masked ? M.active : nullptr);
 }
 
 template <int DIM>
 void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag) {
   const PhysParams p = phys(h->cfg, DIM);
-  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, M.blk[B_FACE]), M.blk[B_FACE], 0, h->stream>>>(
+  const int bf = fit_block(h, L.faces.nf, M.blk[B_FACE]), bc = fit_block(h, L.n, M.blk[B_CELL]);
+  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(
       L.faces, L.W, M.winf, p, L.Fc, want_diag ? L.rface : nullptr);
-  k_coarse_cell<DIM><<<blocks_for(L.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(
+  k_coarse_cell<DIM><<<blocks_for(L.n, bc), bc, 0, h->stream>>>(
       L.topo, L.W, L.Fc, L.rface, Pf, nullptr, h->cfg.df_relax ? L.alpha : L.ones, h->cfg.gamma, h->cfg.cfl_exp,
       h->cfg.cfl_imp, L.R, want_diag ? L.D : nullptr);
 }
@@ -460,9 +480,9 @@ void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want
 template <int DIM>
 void coarse_forcing(cgks_t* h, MeshDev& M, LevelDev& L) {
   const PhysParams p = phys(h->cfg, DIM);
-  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, M.blk[B_FACE]), M.blk[B_FACE], 0, h->stream>>>(L.faces, L.W0, M.winf,
-                                                                                              p, L.Fc, nullptr);
-  k_coarse_cell<DIM><<<blocks_for(L.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr,
+  const int bf = fit_block(h, L.faces.nf, M.blk[B_FACE]), bc = fit_block(h, L.n, M.blk[B_CELL]);
+  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, nullptr);
+  k_coarse_cell<DIM><<<blocks_for(L.n, bc), bc, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr,
                                                                                         nullptr, L.Rstar,
                                                                     L.alpha, h->cfg.gamma, 0.0, 0.0, L.P, nullptr);
 }
@@ -492,7 +512,8 @@ void vcycle_coarse(cgks_t* h, MeshDev& M) {
   for (int l = 1; l < M.nlev; ++l) {
     LevelDev& F = M.lev[l - 1];
     LevelDev& C = M.lev[l];
-    k_restrict<DIM><<<blocks_for(C.n), kBlock, 0, h->stream>>>(C.n, C.ch_off, C.ch_idx, F.vol, C.vol, F.W, F.alpha,
+    const int br = fit_block(h, C.n, kBlock);
+    k_restrict<DIM><<<blocks_for(C.n, br), br, 0, h->stream>>>(C.n, C.ch_off, C.ch_idx, F.vol, C.vol, F.W, F.alpha,
                                                                 F.R, C.W0, C.W, C.alpha, C.Rstar);
     coarse_forcing<DIM>(h, M, C);
     for (int s = 0; s < h->cfg.n_sweep_coarse; ++s) {
@@ -505,7 +526,8 @@ void vcycle_coarse(cgks_t* h, MeshDev& M) {
     LevelDev& F = M.lev[l - 1];
     LevelDev& C = M.lev[l];
     const bool masked = l == 1 && !M.lgrp.empty();
-    k_prolong<DIM><<<blocks_for(F.n), kBlock, 0, h->stream>>>(F.n, F.parent, h->cfg.df_prolong ? F.alpha : F.ones,
+    const int bp = fit_block(h, F.n, kBlock);
+    k_prolong<DIM><<<blocks_for(F.n, bp), bp, 0, h->stream>>>(F.n, F.parent, h->cfg.df_prolong ? F.alpha : F.ones,
                                                                C.W, C.W0, h->cfg.gamma, F.W, M.cnt,
                                                                masked ? M.lgrp[0] : nullptr,
                                                                masked ? M.active : nullptr);
@@ -730,6 +752,12 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
       (h->cfg.df_relax != 0 && h->cfg.df_relax != 1) || (h->cfg.df_prolong != 0 && h->cfg.df_prolong != 1)) {
     delete h;
     return CGKS_ERR_ARG;
+  }
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      h->sms = sms;
   }
   if (stream) {
     h->stream = (cudaStream_t)stream;
