@@ -234,6 +234,13 @@ int cgks_launch_count(cgks_t* h, int mesh_id, int mode, int* count);
  * recorded on the device as in cgks_vcycle. */
 int cgks_vcycle_launch(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int mode);
 
+/* Check of the double-word arithmetic used by flux_precision 1 (no paper
+ * counterpart): a, b (host, [n]) are split into double-words on the GPU and
+ * out (host, [n][7]) receives, converted back to FP64, a + b, a - b, a * b,
+ * a / b, sqrt(a), exp(-a), erfc(b).  Requires a > 0, b != 0, values within the
+ * float exponent range.  Synchronises the stream. */
+int cgks_dword_selftest(cgks_t* h, int64_t n, const double* a, const double* b, double* out);
+
 /* Arithmetic-throughput probe: independent FMA chains on every SM (precision
  * 0 = FP64, 1 = FP32); *tflops receives the rate measured with CUDA events.
  * Synchronises the stream.  Used as the ALU roofline denominator. */

@@ -27,7 +27,7 @@ EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_erro
            "cgks_init_state", "cgks_get_state", "cgks_set_state", "cgks_residual", "cgks_reconstruct",
            "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
            "cgks_gks_points", "cgks_kfvs_points", "cgks_run_stage", "cgks_launch_count",
-           "cgks_vcycle_launch", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
+           "cgks_vcycle_launch", "cgks_dword_selftest", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
            "cgks_autotune", "cgks_residual_coarse_noalloc", "cgks_mlp_set_params", "cgks_mlp_get_params",
            "cgks_mlp_forward", "cgks_mlp_grad", "cgks_mlp_dataset_append", "cgks_mlp_dataset_size",
            "cgks_mlp_dataset_clear", "cgks_mlp_train", "cgks_mlp_collect", "cgks_learned_stats",
@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
         "cgks_upload_mesh": [P, I, I, I64, P, P, I64, P, P],
         "cgks_upload_hierarchy": [P, I, I, P],
         "cgks_mesh_info": [P, I, P, P],
+        "cgks_dword_selftest": [P, I64, P, P, P],
         "cgks_get_coloring": [P, I, I, P],
         "cgks_set_freestream": [P, I, P],
         "cgks_init_state": [P, I, P, P, I],
@@ -269,6 +270,13 @@ class Context:
     def cgks_vcycle_launch(self, mesh_ids, n_cycles: int, mode: int = PLAIN_FP64):
         ids = np.ascontiguousarray(mesh_ids, np.int32)
         self._check(self._L.cgks_vcycle_launch(self.h, _ptr(ids), ids.size, n_cycles, mode))
+
+    def cgks_dword_selftest(self, a, b):
+        a = np.ascontiguousarray(a, np.float64)
+        b = np.ascontiguousarray(b, np.float64)
+        out = np.zeros((a.size, 7))
+        self._check(self._L.cgks_dword_selftest(self.h, a.size, _ptr(a), _ptr(b), _ptr(out)))
+        return out
 
     def cgks_fma_probe(self, precision: int = 0) -> float:
         out = C.c_double()

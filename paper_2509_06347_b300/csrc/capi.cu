@@ -1190,6 +1190,25 @@ int cgks_vcycle_launch(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycle
   });
 }
 
+int cgks_dword_selftest(cgks_t* h, int64_t n, const double* a, const double* b, double* out) {
+  return guarded(h, [&]() -> int {
+    if (n < 0 || (n > 0 && (!a || !b || !out))) throw ArgError("invalid self-test arguments");
+    if (n == 0) return CGKS_OK;
+    DBuf da, db, dout;
+    da.alloc((size_t)n * 8);
+    db.alloc((size_t)n * 8);
+    dout.alloc((size_t)n * 7 * 8);
+    CK(cudaMemcpyAsync(da.p, a, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(db.p, b, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream));
+    k_dword_selftest<<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, da.as<double>(), db.as<double>(),
+                                                              dout.as<double>());
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, dout.p, (size_t)n * 7 * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return CGKS_OK;
+  });
+}
+
 int cgks_fma_probe(cgks_t* h, int precision, double* tflops) {
   return guarded(h, [&]() -> int {
     if (!tflops || (precision != 0 && precision != 1)) throw ArgError("invalid probe arguments");

@@ -329,6 +329,23 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
   }
 }
 
+// double-word arithmetic check: a, b split into double-words, then
+// out[i] = (a + b, a - b, a * b, a / b, sqrt(a), exp(-a), erfc(b)) returned in FP64
+__global__ void k_dword_selftest(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                 double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const dword x(a[i]), y(b[i]);
+  double* o = out + (size_t)i * 7;
+  o[0] = static_cast<double>(x + y);
+  o[1] = static_cast<double>(x - y);
+  o[2] = static_cast<double>(x * y);
+  o[3] = static_cast<double>(x / y);
+  o[4] = static_cast<double>(sqrt(x));
+  o[5] = static_cast<double>(exp(-x));
+  o[6] = static_cast<double>(erfc(y));
+}
+
 // ---------------------------------------------------------------------------
 // K2: gas-kinetic flux, one lane per (face, Gauss point)
 // ---------------------------------------------------------------------------

@@ -103,3 +103,42 @@ def test_fullsize_sphere_residual_sampled_dword(ctx):
     Smax = float(np.max(om.faces(0)["S"]))
     np.testing.assert_allclose(R[seeds], ro["R"][sp], rtol=0, atol=TOL * Fs * Smax)
     np.testing.assert_allclose(al[seeds], ro["alpha"][sp], rtol=TOL, atol=32e-14)
+
+
+def test_dword_arithmetic_error_bounds(ctx):
+    """The double-word operations against extended-precision references on the
+    same split inputs (x = hi + lo, the float32 split of each double), within
+    small multiples of u^2 = 2^-48: sum and difference normwise, product,
+    quotient and root relative; exp and erfc relative with the FP64 function's
+    own error added, and an absolute 2^-149 where the result leaves the float
+    range."""
+    rng = np.random.default_rng(17)
+    n = 20000
+    a = 10.0 ** rng.uniform(-6, 6, n)
+    b = 10.0 ** rng.uniform(-6, 6, n) * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    # include cancellation and exact cases
+    b[:500] = -a[:500] * (1 + 1e-9 * rng.standard_normal(500))
+    b[500:600] = 1.0
+    out = ctx.cgks_dword_selftest(a, b)
+
+    def split(v):
+        hi = v.astype(np.float32)
+        lo = (v - hi.astype(np.float64)).astype(np.float32)
+        return hi.astype(np.longdouble) + lo.astype(np.longdouble)
+
+    x, y = split(a), split(b)
+    u2 = np.longdouble(2.0) ** -48
+    got = out.astype(np.longdouble)
+    np.testing.assert_array_less(np.abs(got[:, 0] - (x + y)), 4 * u2 * (np.abs(x) + np.abs(y)))
+    np.testing.assert_array_less(np.abs(got[:, 1] - (x - y)), 4 * u2 * (np.abs(x) + np.abs(y)))
+    np.testing.assert_array_less(np.abs(got[:, 2] - x * y), 8 * u2 * np.abs(x * y))
+    np.testing.assert_array_less(np.abs(got[:, 3] - x / y), 16 * u2 * np.abs(x / y))
+    np.testing.assert_array_less(np.abs(got[:, 4] - np.sqrt(x)), 8 * u2 * np.sqrt(x))
+    # results below the float range keep an absolute error under the smallest
+    # float subnormal, 2^-149
+    tiny = np.longdouble(2.0) ** -149
+    ex = np.exp(-x)
+    np.testing.assert_array_less(np.abs(got[:, 5] - ex), 8 * u2 * ex + tiny)
+    import math
+    ec = np.array([math.erfc(float(t)) for t in y], dtype=np.longdouble)
+    np.testing.assert_array_less(np.abs(got[:, 6] - ec), 8 * u2 * ec + 4e-16 * ec + tiny)
