@@ -326,6 +326,17 @@ int cgks_mlp_train(cgks_t* h, int n_steps, int batch, double lr, uint64_t seed, 
  * (scaled by the free stream) to the training set. */
 int cgks_mlp_collect(cgks_t* h, int mesh_id, int n_cycles, int mode);
 
+/* The network input of every fine cell at the current state of a 2-D mesh:
+ * X_out (host, [n][68] bfloat16 bit patterns, original cell order).  Per cell
+ * 17 values scaled by the free stream's rho, rho c, rho c, rho c^2: W (4),
+ * slopes times |Omega|^(1/2) (8), R dt_imp / |Omega| (4) and the DF factor,
+ * for the cell and then its 3 face neighbours in stored face order (face k
+ * opposite vertex k); across a boundary face the ghost state and slopes, zero
+ * residual and the cell's own DF factor and size.  R, dt_imp and DF come from
+ * a residual evaluation at the current state (as cgks_residual; the state is
+ * not changed).  Needs cgks_mlp_set_params. */
+int cgks_mlp_features(cgks_t* h, int mesh_id, uint16_t* X_out);
+
 /* Learned-cycle statistics of the last cgks_vcycle(..., CGKS_LEARNED, ...):
  * out[6] = learned cycles, plain cycles, judge cycles, stall fallbacks,
  * network disabled (0/1), last judge relative RMS error (-1 if none).

@@ -30,7 +30,7 @@ EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_erro
            "cgks_vcycle_launch", "cgks_dword_selftest", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
            "cgks_autotune", "cgks_residual_coarse_noalloc", "cgks_mlp_set_params", "cgks_mlp_get_params",
            "cgks_mlp_forward", "cgks_mlp_grad", "cgks_mlp_dataset_append", "cgks_mlp_dataset_size",
-           "cgks_mlp_dataset_clear", "cgks_mlp_train", "cgks_mlp_collect", "cgks_learned_stats",
+           "cgks_mlp_dataset_clear", "cgks_mlp_train", "cgks_mlp_collect", "cgks_mlp_features", "cgks_learned_stats",
            "cgks_synchronize"]
 
 
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
         "cgks_upload_hierarchy": [P, I, I, P],
         "cgks_mesh_info": [P, I, P, P],
         "cgks_dword_selftest": [P, I64, P, P, P],
+        "cgks_mlp_features": [P, I, P],
         "cgks_get_coloring": [P, I, I, P],
         "cgks_set_freestream": [P, I, P],
         "cgks_init_state": [P, I, P, P, I],
@@ -347,6 +348,13 @@ class Context:
 
     def cgks_mlp_collect(self, mesh_id: int, n_cycles: int, mode: int = PLAIN_FP64):
         self._check(self._L.cgks_mlp_collect(self.h, mesh_id, n_cycles, mode))
+
+    def cgks_mlp_features(self, mesh_id: int):
+        """Network inputs [n, 68] of the current state, as float32."""
+        n = self.meshes[mesh_id]["n"]
+        bits = np.zeros((n, 68), np.uint16)
+        self._check(self._L.cgks_mlp_features(self.h, mesh_id, _ptr(bits)))
+        return (bits.astype(np.uint32) << 16).view(np.float32)
 
     def cgks_learned_stats(self, mesh_id: int):
         out = np.zeros(6)

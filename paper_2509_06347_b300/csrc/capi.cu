@@ -1647,6 +1647,26 @@ void enqueue_kind(cgks_t* h, MeshDev& M, int kind, int prec) {
 
 extern "C" {
 
+int cgks_mlp_features(cgks_t* h, int mesh_id, uint16_t* X_out) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    require_ready(M, true);
+    if (!X_out) throw ArgError("null output");
+    ensure_learned(h, M);
+    LevelDev& L = M.lev[0];
+    // residual, time steps and DF at the current state (slopes unchanged)
+    fine_residual<2>(h, M, false, false, false, false, nullptr, nullptr);
+    features(h, M);
+    std::vector<uint16_t> tmp((size_t)L.n * kIn);
+    CK(cudaMemcpyAsync(tmp.data(), M.X, tmp.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const auto& iperm = M.H.fine.iperm;
+    for (int64_t i = 0; i < L.n; ++i)
+      std::memcpy(X_out + (size_t)iperm[i] * kIn, tmp.data() + (size_t)i * kIn, kIn * sizeof(uint16_t));
+    return CGKS_OK;
+  });
+}
+
 int cgks_mlp_collect(cgks_t* h, int mesh_id, int n_cycles, int mode) {
   return guarded(h, [&]() -> int {
     MeshDev& M = get_mesh(h, mesh_id);

@@ -53,8 +53,10 @@ def test_forward_matches_oracle(ctx, n):
     assert np.max(err) <= 2e-2 * (np.max(np.abs(Po)) + 1e-3), np.max(err)
 
 
-def test_gradient_matches_oracle(ctx):
-    theta, X, Y = case(2, 4096)
+@pytest.mark.parametrize("n", [4096, 16384])
+def test_gradient_matches_oracle(ctx, n):
+    """Weight gradients with the split-K reduction, up to the training batch size."""
+    theta, X, Y = case(2, n)
     ctx.cgks_mlp_set_params(theta)
     g = torch.zeros(mlp.N_PARAMS, dtype=torch.float32, device="cuda")
     loss = ctx.cgks_mlp_grad(bf16_dev(X), torch.tensor(Y, dtype=torch.float32, device="cuda"), g)
