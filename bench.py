@@ -585,7 +585,8 @@ def run_batch(args):
     t_gen = time.time() - t0
     n = len(W0)
     stream = torch.cuda.Stream(device=dev)
-    ctx = cgks.Context(stream=stream.cuda_stream)
+    fprec = 1 if args.flux_precision == "dword" else 0
+    ctx = cgks.Context(stream=stream.cuda_stream, flux_precision=fprec)
     t0 = time.time()
     ctx.setup(1, union, winf[0], W0)
     ctx.cgks_set_groups(1, grp, winf)
