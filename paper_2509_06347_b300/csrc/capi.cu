@@ -1094,7 +1094,6 @@ int cgks_vcycle(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int 
       CK(cudaStreamSynchronize(h->stream));
       std::vector<double> hist;
       int done = 0;
-      double ref = -1.0;
       bool stop = false;
       while (done < n_cycles && !stop) {
         const int chunk = std::min(h->cfg.check_every, n_cycles - done);
@@ -1107,7 +1106,6 @@ int cgks_vcycle(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int 
         if (upto > 0) {
           const double first = hist[0];
           const double last = hist[(size_t)(upto - 1) * 2 * nv];
-          ref = first;
           if (!std::isfinite(last) || (first > 0 && last > h->cfg.diverge_factor * first)) {
             status = CGKS_ERR_DIVERGED;
             stop = true;
