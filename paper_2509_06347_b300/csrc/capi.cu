@@ -1114,7 +1114,6 @@ int cgks_vcycle(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int 
           }
         }
       }
-      (void)ref;
       Counters c{};
       CK(cudaMemcpy(&c, M.cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
       if (c.nonfinite > 0) status = CGKS_ERR_DIVERGED;
