@@ -11,7 +11,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "capi.cu"), os.path.join(HERE, "csrc", "host_mesh.cpp")]
-DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("kernels.cuh", "physics.cuh", "host_mesh.hpp")] + \
+CSRC = os.path.join(HERE, "csrc")
+# every source and header of the library (a change to any of them rebuilds it)
+DEPS = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cu", ".cuh", ".cpp", ".hpp"))] + \
     [os.path.join(ROOT, "include", "cgks.h")]
 LIB = os.path.join(HERE, "_lib", "libcgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -30,9 +32,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in DEPS):
             return LIB
+    # per-process object and library names: concurrent builds (several ranks)
+    # never write the same file, and the final rename is atomic
     objs = []
     for src in SRC:
-        obj = os.path.join(os.path.dirname(LIB), os.path.basename(src) + ".o")
+        obj = os.path.join(os.path.dirname(LIB), f"{os.path.basename(src)}.{os.getpid()}.o")
         cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I",
                os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         if verbose:
@@ -42,6 +46,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
     os.replace(tmp, LIB)
+    for obj in objs:
+        os.remove(obj)
     return LIB
 
 
