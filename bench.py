@@ -41,7 +41,6 @@ L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 # ((2 x DFMA + DADD + DMUL) / Gauss points).  The current kernel expands the
 # distribution polynomial once per side and executes fewer (second figures,
 # same ncu counters); achieved = unit x Gauss points / event time.
-# (profiles/k_flux_cylinder65k.md, profiles/k_flux_sphere.md)
 FLUX_FLOP_PER_GP_2D = 2947.1
 FLUX_EXEC_FLOP_PER_GP_2D = 2631.1
 FLUX_FLOP_PER_GP_3D = 5301.1
