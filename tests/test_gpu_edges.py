@@ -166,3 +166,47 @@ def test_lusgs_df_limits(cg, a):
             np.testing.assert_allclose(dWg, rhs * (dte / V)[:, None], rtol=1e-12, atol=1e-15 * sc)
     finally:
         ctx.close()
+
+
+def test_checkpoint_resume_is_exact(cg):
+    """get_state / set_state of (W, slopes, DF): 3 cycles, checkpoint, 3 more
+    cycles equal 6 cycles in one go, bit for bit (deterministic kernels)."""
+    m = tp.MESHES["cylinder"]
+    W0, G0, w = tp.state_for("cylinder", m, np.random.default_rng(5))
+    n = len(W0)
+    ctx = cg.Context()
+    try:
+        ctx.setup(1, m, w, W0, G0)
+        ctx.cgks_vcycle([1], 6, cg.MIXED, check=False)
+        Wa = np.zeros_like(W0)
+        ctx.cgks_get_state(1, Wa)
+        ctx.setup(2, m, w, W0, G0)
+        ctx.cgks_vcycle([2], 3, cg.MIXED, check=False)
+        Wc, Gc, ac = np.zeros_like(W0), np.zeros((n, 4, 2)), np.zeros(n)
+        ctx.cgks_get_state(2, Wc, Gc, ac)
+        ctx.setup(3, m, w, W0, G0)  # a fresh mesh slot, then resume from the checkpoint
+        ctx.cgks_set_state(3, Wc, Gc, ac)
+        ctx.cgks_vcycle([3], 3, cg.MIXED, check=False)
+        Wb = np.zeros_like(W0)
+        ctx.cgks_get_state(3, Wb)
+        np.testing.assert_array_equal(Wb, Wa)
+    finally:
+        ctx.close()
+
+
+def test_divergence_is_reported(cg):
+    """A run that blows up (Mach 5 from the free stream, no DF relaxation, CFL
+    1000) ends with CGKS_ERR_DIVERGED, found on the host from the residual
+    history and the non-finite counter, and the context stays usable."""
+    m = synth.cylinder_mesh(16, 8, n_refine=2)
+    w = synth.freestream(5.0)
+    W = synth.uniform_state(m, w)
+    ctx = cg.Context(df_relax=0, cfl_imp=1000.0)
+    try:
+        ctx.setup(1, m, w, W)
+        rc = ctx.cgks_vcycle([1], 200, cg.MIXED, check=False)
+        assert rc == -4
+        ctx.cgks_init_state(1, W)  # reset and run a sane single cycle
+        ctx.cgks_vcycle([1], 1, cg.PLAIN_FP64, check=False)
+    finally:
+        ctx.close()
