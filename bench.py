@@ -74,6 +74,8 @@ def parse():
                     help="skip the learned-correction leg (train on batch cylinders, held-out Mach runs)")
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the multigrid-versus-explicit leg and its DF ablations")
+    ap.add_argument("--no-agglomeration", action="store_true",
+                    help="skip the leg that solves on an agglomerated hierarchy against the nested one")
     ap.add_argument("--profile-steps", action="store_true",
                     help="only warm-up + steps, for ncu launch lists")
     return ap.parse_args()
@@ -381,6 +383,9 @@ def run_ours(args):
     ablation = None
     if not args.no_ablation and not sphere:
         ablation = ablation_leg(cgks, stream)
+    agglo = None
+    if not args.no_agglomeration and not sphere:
+        agglo = agglomeration_leg(cgks, stream)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         if sphere:
@@ -418,6 +423,7 @@ def run_ours(args):
         "convergence": conv,
         "learned": learned,
         "ablation": ablation,
+        "agglomeration": agglo,
         "residual_rms_rho_last": float(rn[0, 0]),
         "counters": {"recon_fallback": int(counters[0]), "update_halved": int(counters[1]),
                      "update_zeroed": int(counters[2]), "nonfinite": int(counters[3])},
@@ -544,6 +550,43 @@ def ablation_leg(cgks, stream):
             else:  # the variant never reached it: its whole run against GMG's time
                 entry["speedup_of_gmg"][k] = {"at": f"1e-{d}", "value": r["wall_s"] / g[key], "bound": "lower",
                                               "variant_cycles": r["cycles"]}
+        out[name] = entry
+    return out
+
+
+def agglomeration_leg(cgks, stream, passes=3, min_skew=0.1):
+    """Multigrid on a hierarchy built by the agglomeration coarsening of
+    Sec 5.1 (hash-selected face removal, skewness guard) against the nested
+    hierarchy of the same fine mesh: host time of the coarsening, level sizes,
+    time per V-cycle and wall time to each decade of residual drop (MIXED),
+    on the stationary vortex and the Mach-5 cylinder."""
+    mv = synth.vortex_mesh(n_coarse=8, n_refine=2)
+    Wv, Gv = synth.vortex_state(mv)
+    wv = np.array([1.0, 0.0, 0.0, 1.0 / 0.4])
+    mc, wc, Wc = workload()
+    cases = [("vortex_2048tri_3level", mv, wv, Wv, Gv, {"tau_c1": 1.0}, 1000),
+             (WORKLOAD, mc, wc, Wc, None, {}, 2000)]
+    out = {}
+    for name, mesh, w, W0, G0, cfg, cap in cases:
+        ctx = cgks.Context(stream=stream.cuda_stream, **cfg)
+        t0 = time.perf_counter()
+        parents = ctx.cgks_agglomerate(mesh, 3, passes, min_skew)
+        t_host = time.perf_counter() - t0
+        ctx.close()
+        entry = {"config": cfg or {"tau_c1": 0.01}, "mode": "mixed", "passes_per_level": passes,
+                 "min_skew": min_skew, "agglomerate_host_s": t_host}
+        for k, m in (("nested", mesh), ("agglomerated", dict(mesh, parents=parents))):
+            r, _ = _solve_to_drop(cgks, m, w, W0, G0, cgks.MIXED, cap, stream, **cfg)
+            r["levels"] = [len(W0)] + [int(p.max()) + 1 for p in m["parents"][:2]]
+            r["ms_per_cycle"] = 1e3 * r["wall_s"] / max(1, r["cycles"])
+            entry[k] = {kk: v for kk, v in r.items() if kk in ("rc", "cycles", "wall_s", "final_drop", "min_drop",
+                                                               "levels", "ms_per_cycle")
+                        or kk.startswith("wall_s_to") or kk.startswith("cycles_to")}
+        a, b = entry["nested"], entry["agglomerated"]
+        deep = max([d for d in range(1, 11) if f"cycles_to_1e-{d}" in a and f"cycles_to_1e-{d}" in b], default=0)
+        if deep:
+            entry["common_drop"] = f"1e-{deep}"
+            entry["wall_ratio_agglomerated_over_nested"] = b[f"wall_s_to_1e-{deep}"] / a[f"wall_s_to_1e-{deep}"]
         out[name] = entry
     return out
 

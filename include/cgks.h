@@ -127,6 +127,35 @@ int cgks_upload_mesh(cgks_t* h, int mesh_id, int dim, int64_t n_cells, const int
  */
 int cgks_upload_hierarchy(cgks_t* h, int mesh_id, int n_levels, const int32_t* const* parent);
 
+/*
+ * Agglomeration coarsening (Sec 5.1, Eqs. hash value, virtual center and
+ * skewness factor; Algorithm cell-merge) for meshes that are not nested by
+ * construction.  Host-only; needs no mesh slot and touches no device memory.
+ * Mesh arrays as in cgks_upload_mesh (host, read only; here a boundary tag
+ * only groups a cell's boundary faces, so any value is taken).  The faces of
+ * a level are its neighbour pairs and its (cell, tag) boundary groups, with
+ * summed area vectors and centres weighted by fine face area.  One pass visits the
+ * interior faces in (lower, higher) cell-id order, keeps each face whose hash
+ * h = [23 (N_l + N_r) + N_l N_r] mod N_f is new (N_f = interior faces of the
+ * level), and then merges the two cells of each kept face when neither was
+ * merged in this pass, the face is not on a periodic seam, and every other
+ * face of the merged cell has sin(alpha) = d.n / |d| > min_skew, d pointing
+ * from the volume-weighted virtual centre to the face centre, n the outward
+ * unit normal.  Boundary faces are never removed.  Coarse ids follow the
+ * lowest member id.  One level is `passes` passes (1..8), each on the
+ * agglomerates of the previous pass.  Outputs (host, caller-owned):
+ *   parents     [(n_levels-1) * n_cells]  the array of level l (1..n_levels-1)
+ *               starts at (l-1)*n_cells and holds level_cells[l-1] entries:
+ *               the level-l agglomerate of each level-(l-1) cell, ready for
+ *               cgks_upload_hierarchy; may be NULL when n_levels == 1
+ *   level_cells [n_levels]  cells of each level (level_cells[0] = n_cells)
+ * n_levels 1..8; min_skew in [-1, 1).  Returns CGKS_ERR_ARG for invalid
+ * arguments and CGKS_ERR_MESH for a mesh that cgks_upload_mesh rejects.
+ */
+int cgks_agglomerate(cgks_t* h, int dim, int64_t n_cells, const int32_t* cell_nodes, const double* cell_xyz,
+                     int64_t n_bfaces, const int32_t* bface_nodes, const int32_t* bface_tag, int n_levels,
+                     int passes, double min_skew, int32_t* parents, int64_t* level_cells);
+
 /* Sizes: out[4*l + 0..3] = cells, colours, faces, boundary faces of level l
  * (out must hold 4 * n_levels values); *n_levels receives the level count. */
 int cgks_mesh_info(cgks_t* h, int mesh_id, int* n_levels, int64_t* out);

@@ -15,6 +15,9 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   LU-SGS ........................................... pinned (dense block factorisation,
                                                      alpha = 0 explicit limit)
   FAS forcing / prolongation ....................... pinned (zero-forcing, alpha = 0)
+  agglomeration coarsening (agglomerate.py) ......... pinned (hand-worked hashes, closed-form
+                                                     skewness in 2D and 3D, a hash-decided
+                                                     strip, partition invariants)
   V-cycle histories ................................ parity unpinned beyond the above
 """
 from __future__ import annotations

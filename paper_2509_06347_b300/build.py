@@ -10,7 +10,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", "capi.cu"), os.path.join(HERE, "csrc", "host_mesh.cpp")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("capi.cu", "host_mesh.cpp", "agglomerate.cpp")]
 CSRC = os.path.join(HERE, "csrc")
 # every source and header of the library (a change to any of them rebuilds it)
 DEPS = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cu", ".cuh", ".cpp", ".hpp"))] + \

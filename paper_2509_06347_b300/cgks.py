@@ -23,7 +23,7 @@ TAG_WALL, TAG_FARFIELD = 1, 2
 
 # every entry point declared in include/cgks.h
 EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_error", "cgks_upload_mesh",
-           "cgks_upload_hierarchy", "cgks_mesh_info", "cgks_get_coloring", "cgks_set_freestream",
+           "cgks_upload_hierarchy", "cgks_agglomerate", "cgks_mesh_info", "cgks_get_coloring", "cgks_set_freestream",
            "cgks_init_state", "cgks_get_state", "cgks_set_state", "cgks_residual", "cgks_reconstruct",
            "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
            "cgks_gks_points", "cgks_kfvs_points", "cgks_run_stage", "cgks_launch_count",
@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
         "cgks_upload_mesh": [P, I, I, I64, P, P, I64, P, P],
         "cgks_upload_hierarchy": [P, I, I, P],
         "cgks_mesh_info": [P, I, P, P],
+        "cgks_agglomerate": [P, I, I64, P, P, I64, P, P, I, I, D, P, P],
         "cgks_dword_selftest": [P, I64, P, P, P],
         "cgks_mlp_features": [P, I, P],
         "cgks_get_coloring": [P, I, I, P],
@@ -182,6 +183,23 @@ class Context:
         arrs = [np.ascontiguousarray(p, np.int32) for p in parents]
         ptrs = (C.c_void_p * max(1, len(arrs)))(*[a.ctypes.data for a in arrs])
         self._check(self._L.cgks_upload_hierarchy(self.h, mesh_id, len(arrs) + 1, ptrs))
+
+    def cgks_agglomerate(self, mesh: dict, n_levels: int = 3, passes: int = 3, min_skew: float = 0.1):
+        """Parent arrays of an agglomerated hierarchy (list of n_levels - 1 int32
+        arrays, original numbering), for cgks_upload_hierarchy.  Three pairwise
+        passes per level give about 3.5:1 in 2D and 3:1 in 3D on the first level."""
+        dim = int(mesh["dim"])
+        cn = np.ascontiguousarray(mesh["cell_nodes"], np.int32)
+        cx = np.ascontiguousarray(mesh["cell_xyz"], np.float64)
+        bn = np.ascontiguousarray(mesh["bface_nodes"], np.int32)
+        bt = np.ascontiguousarray(mesh["bface_tag"], np.int32)
+        n = cn.shape[0]
+        par = np.zeros(max(1, (n_levels - 1) * n), np.int32)
+        sizes = np.zeros(n_levels, np.int64)
+        self._check(self._L.cgks_agglomerate(self.h, dim, n, _ptr(cn), _ptr(cx), bt.size,
+                                             _ptr(bn) if bt.size else None, _ptr(bt) if bt.size else None,
+                                             n_levels, passes, float(min_skew), _ptr(par), _ptr(sizes)))
+        return [par[(l - 1) * n:(l - 1) * n + sizes[l - 1]].copy() for l in range(1, n_levels)]
 
     def cgks_mesh_info(self, mesh_id: int):
         nl = C.c_int()

@@ -849,6 +849,32 @@ int cgks_upload_hierarchy(cgks_t* h, int mesh_id, int n_levels, const int32_t* c
   });
 }
 
+int cgks_agglomerate(cgks_t* h, int dim, int64_t n_cells, const int32_t* cell_nodes, const double* cell_xyz,
+                     int64_t n_bfaces, const int32_t* bface_nodes, const int32_t* bface_tag, int n_levels,
+                     int passes, double min_skew, int32_t* parents, int64_t* level_cells) {
+  return guarded(h, [&]() -> int {
+    if ((dim != 2 && dim != 3) || n_cells <= 0 || !cell_nodes || !cell_xyz || n_bfaces < 0 ||
+        (n_bfaces > 0 && (!bface_nodes || !bface_tag)) || n_cells >= (1ll << 30) || n_levels < 1 ||
+        n_levels > 8 || passes < 1 || passes > 8 || !(min_skew >= -1.0 && min_skew < 1.0) || !level_cells ||
+        (n_levels > 1 && !parents))
+      throw ArgError("invalid agglomeration arguments");
+    std::vector<std::vector<int32_t>> P;
+    try {
+      agglomerate(dim, n_cells, cell_nodes, cell_xyz, n_bfaces, bface_nodes, bface_tag, n_levels, passes,
+                  min_skew, P);
+    } catch (const std::runtime_error& e) {
+      return fail(h, CGKS_ERR_MESH, e.what());
+    }
+    level_cells[0] = n_cells;
+    for (int l = 1; l < n_levels; ++l) {
+      const std::vector<int32_t>& p = P[l - 1];
+      std::memcpy(parents + (size_t)(l - 1) * n_cells, p.data(), p.size() * sizeof(int32_t));
+      level_cells[l] = 1 + *std::max_element(p.begin(), p.end());
+    }
+    return CGKS_OK;
+  });
+}
+
 int cgks_mesh_info(cgks_t* h, int mesh_id, int* n_levels, int64_t* out) {
   return guarded(h, [&]() -> int {
     MeshDev& M = get_mesh(h, mesh_id);

@@ -84,6 +84,16 @@ void build_fine_level(int dim, int64_t n, const int32_t* cell_nodes, const doubl
 void build_coarse_level(const Hierarchy& H, int level_index, const int32_t* parent_orig,
                         CoarseLevel& out);
 
+// Agglomeration coarsening by hash-selected face removal with a skewness
+// guard (Sec 5.1).  Same mesh arrays as build_fine_level, original order.
+// parents[l-1][i] = level-l agglomerate of level-(l-1) cell i, for
+// l = 1..n_levels-1; each level is `passes` pairwise merge passes; a merge
+// needs every remaining face of the merged cell to have sin(alpha) > min_skew.
+// Throws std::runtime_error for a mesh that build_fine_level would reject.
+void agglomerate(int dim, int64_t n, const int32_t* cell_nodes, const double* cell_xyz, int64_t nb,
+                 const int32_t* bface_nodes, const int32_t* bface_tag, int n_levels, int passes,
+                 double min_skew, std::vector<std::vector<int32_t>>& parents);
+
 // Breadth-first greedy colouring from cell 0 (Sec 4.1).  nbr lists per cell
 // in stored order (-1 = no neighbour).  Returns number of colours.
 int greedy_colouring(int64_t n, const std::vector<int64_t>& off, const std::vector<int64_t>& nbr,
