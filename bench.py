@@ -506,7 +506,8 @@ def ablation_leg(cgks, stream):
     gas-kinetic scheme on the GPU, and its relaxation ablations: wall time to
     each decade of residual drop for
       GMG (3 levels, DF-relaxed LU-SGS, DF prolongation; the method),
-      GMG without DF relaxation, GMG without DF prolongation,
+      GMG without DF relaxation (fully implicit), GMG with the fixed relaxation
+      factor 0.5 in place of DF, GMG without DF prolongation,
       one level of DF-relaxed LU-SGS (no coarse levels),
       the explicit scheme (one level, explicit update at CFL 0.5),
     on the stationary vortex (converges) and the Mach-5 cylinder (plateaus);
@@ -522,6 +523,7 @@ def ablation_leg(cgks, stream):
         runs = {
             "gmg": (None, dict(base), n_gmg),
             "gmg_no_df_relaxation": (None, dict(base, df_relax=0), n_gmg),
+            "gmg_fixed_relaxation_0.5": (None, dict(base, df_relax=2, relax_beta=0.5), n_gmg),
             "gmg_no_df_prolongation": (None, dict(base, df_prolong=0), n_gmg),
             "one_level_lusgs": (1, dict(base), n_one),
             "explicit": (1, dict(base, fine_smoother=1), n_one),
@@ -554,39 +556,49 @@ def ablation_leg(cgks, stream):
     return out
 
 
-def agglomeration_leg(cgks, stream, passes=3, min_skew=0.1):
-    """Multigrid on a hierarchy built by the agglomeration coarsening of
-    Sec 5.1 (hash-selected face removal, skewness guard) against the nested
-    hierarchy of the same fine mesh: host time of the coarsening, level sizes,
-    time per V-cycle and wall time to each decade of residual drop (MIXED),
-    on the stationary vortex and the Mach-5 cylinder."""
+def agglomeration_leg(cgks, stream, settings=((3, 0.1), (3, 0.3))):
+    """Multigrid on hierarchies built by the agglomeration coarsening of
+    Sec 5.1 (hash-selected face removal, skewness guard; `settings` lists
+    (passes per level, skewness limit)) against the nested hierarchy of the
+    same fine mesh: host time of the coarsening, level sizes, time per V-cycle
+    and wall time to each decade of residual drop (MIXED), on the stationary
+    vortex and the Mach-5 cylinder."""
     mv = synth.vortex_mesh(n_coarse=8, n_refine=2)
     Wv, Gv = synth.vortex_state(mv)
     wv = np.array([1.0, 0.0, 0.0, 1.0 / 0.4])
     mc, wc, Wc = workload()
     cases = [("vortex_2048tri_3level", mv, wv, Wv, Gv, {"tau_c1": 1.0}, 1000),
              (WORKLOAD, mc, wc, Wc, None, {}, 2000)]
+    keys = ("rc", "cycles", "wall_s", "final_drop", "min_drop", "levels", "ms_per_cycle", "agglomerate_host_s")
     out = {}
     for name, mesh, w, W0, G0, cfg, cap in cases:
-        ctx = cgks.Context(stream=stream.cuda_stream, **cfg)
-        t0 = time.perf_counter()
-        parents = ctx.cgks_agglomerate(mesh, 3, passes, min_skew)
-        t_host = time.perf_counter() - t0
-        ctx.close()
-        entry = {"config": cfg or {"tau_c1": 0.01}, "mode": "mixed", "passes_per_level": passes,
-                 "min_skew": min_skew, "agglomerate_host_s": t_host}
-        for k, m in (("nested", mesh), ("agglomerated", dict(mesh, parents=parents))):
+        entry = {"config": cfg or {"tau_c1": 0.01}, "mode": "mixed"}
+        variants = [("nested", mesh, None)]
+        for passes, lim in settings:
+            ctx = cgks.Context(stream=stream.cuda_stream, **cfg)
+            t0 = time.perf_counter()
+            parents = ctx.cgks_agglomerate(mesh, 3, passes, lim)
+            t_host = time.perf_counter() - t0
+            ctx.close()
+            variants.append((f"agglomerated_passes{passes}_skew{lim}", dict(mesh, parents=parents), t_host))
+        for k, m, t_host in variants:
             r, _ = _solve_to_drop(cgks, m, w, W0, G0, cgks.MIXED, cap, stream, **cfg)
             r["levels"] = [len(W0)] + [int(p.max()) + 1 for p in m["parents"][:2]]
             r["ms_per_cycle"] = 1e3 * r["wall_s"] / max(1, r["cycles"])
-            entry[k] = {kk: v for kk, v in r.items() if kk in ("rc", "cycles", "wall_s", "final_drop", "min_drop",
-                                                               "levels", "ms_per_cycle")
-                        or kk.startswith("wall_s_to") or kk.startswith("cycles_to")}
-        a, b = entry["nested"], entry["agglomerated"]
-        deep = max([d for d in range(1, 11) if f"cycles_to_1e-{d}" in a and f"cycles_to_1e-{d}" in b], default=0)
-        if deep:
-            entry["common_drop"] = f"1e-{deep}"
-            entry["wall_ratio_agglomerated_over_nested"] = b[f"wall_s_to_1e-{deep}"] / a[f"wall_s_to_1e-{deep}"]
+            if t_host is not None:
+                r["agglomerate_host_s"] = t_host
+            entry[k] = {kk: v for kk, v in r.items() if kk in keys or kk.startswith("wall_s_to")
+                        or kk.startswith("cycles_to")}
+        a = entry["nested"]
+        for k, _, _ in variants[1:]:
+            b = entry[k]
+            deep = max([d for d in range(1, 11) if f"cycles_to_1e-{d}" in a and f"cycles_to_1e-{d}" in b],
+                       default=0)
+            if b["rc"] != 0:
+                b["diverged"] = True
+            elif deep:
+                b["wall_ratio_over_nested"] = {"at": f"1e-{deep}",
+                                               "value": b[f"wall_s_to_1e-{deep}"] / a[f"wall_s_to_1e-{deep}"]}
         out[name] = entry
     return out
 

@@ -75,7 +75,8 @@ typedef struct cgks_config {
                              third-order residual; 1: explicit local-time-step update
                              W -= dt_exp R / V (Eq. smo) (0) */
   int df_relax;           /* 1: DF-weighted implicit/explicit LU-SGS (Sec 4.3); 0: fully
-                             implicit LU-SGS, DF ignored (ablation) (1) */
+                             implicit LU-SGS, DF ignored (ablation); 2: the fixed-factor
+                             relaxation of Sec 4.3's remark, relax_beta in place of DF (1) */
   int df_prolong;         /* 1: prolongation scaled by DF (Eq. prolongation); 0: plain
                              injection (ablation) (1) */
   double df_gate;         /* learned correction applied only where DF >= df_gate (0.9) */
@@ -83,6 +84,7 @@ typedef struct cgks_config {
   double learned_max_error;  /* judge relative RMS error above which the network is disabled (0.5) */
   int flux_precision;        /* fine gas-kinetic flux: 0 FP64; 1 double-word (two floats, ~48-bit
                                 significand, about 3.6e-15 unit roundoff) on the FP32 pipes (0) */
+  double relax_beta;         /* constant relaxation factor of df_relax 2, in [0, 1] (0.5) */
 } cgks_config;
 
 typedef struct cgks_ctx cgks_t;

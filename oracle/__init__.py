@@ -33,7 +33,8 @@ _SRC = os.path.join(_HERE, "cgks_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libcgks_oracle.so")
 
 DEFAULTS = dict(gamma=1.4, cfl_imp=10.0, cfl_exp=0.5, tau_c1=0.01, tau_c2=1.0,
-                weno_gamma_high=0.95, weno_eps=1e-15, r_safety=1.0, n_sweep=6)
+                weno_gamma_high=0.95, weno_eps=1e-15, r_safety=1.0, n_sweep=6,
+                relax=-1.0, df_prolong=1, fine_smoother=0)
 
 
 def build(force: bool = False) -> str:
@@ -97,7 +98,10 @@ def lib():
 
 def cfg_vector(dim: int, winf=None, **over) -> np.ndarray:
     """Flat configuration: gamma, cfl_imp, cfl_exp, tau_c1, tau_c2, weno_gamma_high,
-    weno_eps, r_safety, n_sweep, then the free-stream state (nv values)."""
+    weno_eps, r_safety, n_sweep, then the free-stream state (nv values), then the
+    V-cycle switches: relax (negative: DF relaxes LU-SGS; else this constant
+    stands for DF), df_prolong (1: DF-scaled prolongation; 0: plain injection)
+    and fine_smoother (0: LU-SGS step; 1: explicit update)."""
     c = dict(DEFAULTS)
     c.update(over)
     nv = dim + 2
@@ -107,7 +111,8 @@ def cfg_vector(dim: int, winf=None, **over) -> np.ndarray:
         w[-1] = 1.0 / (c["gamma"] * (c["gamma"] - 1.0))
     return np.ascontiguousarray(np.concatenate([[c["gamma"], c["cfl_imp"], c["cfl_exp"], c["tau_c1"],
                                                  c["tau_c2"], c["weno_gamma_high"], c["weno_eps"],
-                                                 c["r_safety"], float(c["n_sweep"])], w]))
+                                                 c["r_safety"], float(c["n_sweep"])], w,
+                                                [c["relax"], float(c["df_prolong"]), float(c["fine_smoother"])]]))
 
 
 def _c(a, dt=np.float64):

@@ -44,6 +44,11 @@ typedef struct {
   double gamma, cfl_imp, cfl_exp, tau_c1, tau_c2, weno_gh, weno_eps, r_safety;
   int n_sweep;            /* LU-SGS sweeps per coarse level */
   double winf[MAXV];      /* free stream (conservative) for far-field ghosts */
+  double relax;           /* V-cycle LU-SGS relaxation factor: < 0 the DF of each cell
+                             (Sec 4.3); otherwise this constant in place of DF (1: fully
+                             implicit; in (0,1): the fixed-factor scheme of the remark) */
+  int df_prolong;         /* 1: prolongation scaled by DF; 0: plain injection */
+  int fine_smoother;      /* 0: DF-relaxed LU-SGS step; 1: explicit update (Eq. smo) */
 } OCfg;
 
 static void cfg_from(const double* c, int nv, OCfg* o) {
@@ -51,6 +56,9 @@ static void cfg_from(const double* c, int nv, OCfg* o) {
   o->tau_c2 = c[4]; o->weno_gh = c[5]; o->weno_eps = c[6]; o->r_safety = c[7];
   o->n_sweep = (int)c[8];
   for (int v = 0; v < nv; ++v) o->winf[v] = c[9 + v];
+  o->relax = c[9 + nv];
+  o->df_prolong = (int)c[10 + nv];
+  o->fine_smoother = (int)c[11 + nv];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1479,13 +1487,18 @@ int om_vcycle(void* h, const double* cfgv, double* W, double* G, double* alpha, 
   double* dte = malloc(n0 * sizeof(double));
   double* dti = malloc(n0 * sizeof(double));
   double* rhs = malloc((size_t)n0 * nv * sizeof(double));
-  double *Wl[8], *Wl0[8], *al[8], *Rs[8], *Pl[8];
-  for (int l = 1; l < nl; ++l) {
+  double *Wl[8], *Wl0[8], *al[8], *Rs[8], *Pl[8], *kl[8], *one[8];
+  /* kl: the constant relaxation factor of each level; one: plain injection */
+  for (int l = 0; l < nl; ++l) {
     int n = M->lev[l].n_cells;
+    kl[l] = malloc(n * sizeof(double)); one[l] = malloc(n * sizeof(double));
+    for (int c = 0; c < n; ++c) { kl[l][c] = cfg.relax; one[l][c] = 1.0; }
+    if (l == 0) continue;
     Wl[l] = malloc((size_t)n * nv * sizeof(double)); Wl0[l] = malloc((size_t)n * nv * sizeof(double));
     al[l] = malloc(n * sizeof(double)); Rs[l] = malloc((size_t)n * nv * sizeof(double));
     Pl[l] = malloc((size_t)n * nv * sizeof(double));
   }
+  const int use_df = cfg.relax < 0.0;
   for (int cyc = 0; cyc < n_cycles; ++cyc) {
     /* 1. residual, DF and slopes; slope update with DF */
     fine_residual(M, &cfg, W, G, alpha, R, Gn, an, dte, dti, &st);
@@ -1494,9 +1507,18 @@ int om_vcycle(void* h, const double* cfgv, double* W, double* G, double* alpha, 
       for (int i = 0; i < nv * dim; ++i) G[(size_t)c * nv * dim + i] = an[c] * Gn[(size_t)c * nv * dim + i];
       alpha[c] = an[c];
     }
-    /* 2. fine pre-smoothing: one DF-relaxed LU-SGS step driven by -R */
-    for (int i = 0; i < n0 * nv; ++i) rhs[i] = -R[i];
-    lusgs(M, 0, &cfg, W, rhs, alpha, dte, dti, NULL, &st);
+    /* 2. fine pre-smoothing: one DF-relaxed LU-SGS step driven by -R, or the
+       explicit local-time-step update W -= dt R / V (Eq. smo) */
+    if (cfg.fine_smoother == 1) {
+      for (int c = 0; c < n0; ++c) {
+        double d[MAXV];
+        for (int v = 0; v < nv; ++v) d[v] = -dte[c] * R[(size_t)c * nv + v] / M->lev[0].vol[c];
+        apply_update(dim, cfg.gamma, W + (size_t)c * nv, d, &st);
+      }
+    } else {
+      for (int i = 0; i < n0 * nv; ++i) rhs[i] = -R[i];
+      lusgs(M, 0, &cfg, W, rhs, use_df ? alpha : kl[0], dte, dti, NULL, &st);
+    }
     if (nl == 1) continue;
     /* 3. residual at the smoothed state (slopes not updated); its DF is kept */
     fine_residual(M, &cfg, W, G, alpha, R, Gn, an, NULL, NULL, &st);
@@ -1511,7 +1533,7 @@ int om_vcycle(void* h, const double* cfgv, double* W, double* G, double* alpha, 
       kfvs_residual(M, l, &cfg, Wl0[l], Pl[l]);
       for (int i = 0; i < n * nv; ++i) Pl[l][i] = Rs[l][i] - Pl[l][i];
       memcpy(Wl[l], Wl0[l], (size_t)n * nv * sizeof(double));
-      coarse_smooth(M, l, &cfg, Wl[l], Pl[l], al[l], cfg.n_sweep, &st);
+      coarse_smooth(M, l, &cfg, Wl[l], Pl[l], use_df ? al[l] : kl[l], cfg.n_sweep, &st);
       if (l + 1 < nl) {
         /* residual to restrict: R^l(W) + P at the smoothed state */
         kfvs_residual(M, l, &cfg, Wl[l], Rs[l]);
@@ -1521,13 +1543,16 @@ int om_vcycle(void* h, const double* cfgv, double* W, double* G, double* alpha, 
     }
     /* 8. DF-limited prolongation, coarse to fine */
     for (int l = nl - 1; l >= 1; --l) {
-      if (l - 1 >= 1) prolong(M, l - 1, &cfg, Wl[l - 1], al[l - 1], Wl[l], Wl0[l], &st);
-      else prolong(M, 0, &cfg, W, alpha, Wl[l], Wl0[l], &st);
+      if (l - 1 >= 1) prolong(M, l - 1, &cfg, Wl[l - 1], cfg.df_prolong ? al[l - 1] : one[l - 1], Wl[l], Wl0[l], &st);
+      else prolong(M, 0, &cfg, W, cfg.df_prolong ? alpha : one[0], Wl[l], Wl0[l], &st);
     }
   }
   if (stats) { stats[0] = st.recon_fallback; stats[1] = st.rank_fallback; stats[2] = st.update_halved; stats[3] = st.update_zeroed; }
   free(R); free(Gn); free(an); free(dte); free(dti); free(rhs);
-  for (int l = 1; l < nl; ++l) { free(Wl[l]); free(Wl0[l]); free(al[l]); free(Rs[l]); free(Pl[l]); }
+  for (int l = 0; l < nl; ++l) {
+    free(kl[l]); free(one[l]);
+    if (l > 0) { free(Wl[l]); free(Wl0[l]); free(al[l]); free(Rs[l]); free(Pl[l]); }
+  }
   return 0;
 }
 /* DF-limited injection prolongation from level lev+1 into level lev */

@@ -47,7 +47,8 @@ class Config(C.Structure):
                 ("n_pre", C.c_int), ("n_post", C.c_int), ("check_every", C.c_int), ("tol", C.c_double),
                 ("diverge_factor", C.c_double), ("fine_smoother", C.c_int), ("df_relax", C.c_int),
                 ("df_prolong", C.c_int), ("df_gate", C.c_double), ("learned_judge_every", C.c_int),
-                ("learned_max_error", C.c_double), ("flux_precision", C.c_int)]
+                ("learned_max_error", C.c_double), ("flux_precision", C.c_int),
+                ("relax_beta", C.c_double)]
 
 
 _lib = None

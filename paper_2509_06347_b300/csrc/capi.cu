@@ -86,7 +86,8 @@ struct LevelDev {
   int* iperm = nullptr;  // new -> original
   double* vol = nullptr;
   double *W = nullptr, *W0 = nullptr, *alpha = nullptr, *R = nullptr, *P = nullptr, *Rstar = nullptr;
-  double* ones = nullptr;  // DF = 1 everywhere (ablation switches)
+  double* ones = nullptr;   // DF = 1 everywhere (prolongation ablation)
+  double* relax = nullptr;  // the constant that stands for DF in LU-SGS when df_relax != 1
   FaceSet faces{};
   double* Fc = nullptr;     // coarse face fluxes [nf][nv]
   double* rface = nullptr;  // spectral radius per face [nf]
@@ -263,13 +264,18 @@ Topo make_topo(MeshDev& M, int64_t n, const std::vector<int64_t>& off, const std
   return t;
 }
 
-void alloc_level_state(MeshDev& M, LevelDev& L) {
+// The factor that replaces DF in the LU-SGS relaxation when df_relax != 1:
+// 1 for the fully implicit scheme, relax_beta for the fixed-factor scheme.
+double relax_constant(const cgks_config& cfg) { return cfg.df_relax == 2 ? cfg.relax_beta : 1.0; }
+
+void alloc_level_state(MeshDev& M, LevelDev& L, const cgks_config& cfg) {
   auto& P = M.pool;
   const int nv = M.nv;
   L.W = dalloc<double>(P, (size_t)L.n * nv);
   L.W0 = dalloc<double>(P, (size_t)L.n * nv);
   L.alpha = dalloc<double>(P, L.n);
   L.ones = upload(P, std::vector<double>(L.n, 1.0));
+  L.relax = upload(P, std::vector<double>(L.n, relax_constant(cfg)));
   L.R = dalloc<double>(P, (size_t)L.n * nv);
   L.P = dalloc<double>(P, (size_t)L.n * nv);
   L.Rstar = dalloc<double>(P, (size_t)L.n * nv);
@@ -311,7 +317,7 @@ void build_levels_device(MeshDev& M, const cgks_config& cfg) {
         for (int d = 0; d < dim; ++d) nrm[e * dim + d] = F.cside[e] * F.fn[f * dim + d];
       }
     L.topo = make_topo(M, F.n, off, nbr, tag, side, S, nrm, L.vol, face);
-    alloc_level_state(M, L);
+    alloc_level_state(M, L, cfg);
     L.faces = FaceSet{M.fine.nf, M.fine.fL, M.fine.fR, M.fine.ftag, M.fine.fn, M.fine.fS};
     L.rface = dalloc<double>(M.pool, F.nf);
   }
@@ -338,7 +344,7 @@ void build_levels_device(MeshDev& M, const cgks_config& cfg) {
         for (int d = 0; d < dim; ++d) nrm[e * dim + d] = sd * C.fn[f * dim + d];
       }
     L.topo = make_topo(M, C.n, C.cf_off, nbr, tag, C.cf_side, S, nrm, L.vol, C.cf_face);
-    alloc_level_state(M, L);
+    alloc_level_state(M, L, cfg);
     L.faces = FaceSet{(int)C.nf, upload(M.pool, to_i32(C.fL)), upload(M.pool, to_i32(C.fR)), upload(M.pool, C.ftag),
                       upload(M.pool, C.fn), upload(M.pool, C.fS)};
     L.Fc = dalloc<double>(M.pool, (size_t)C.nf * M.nv);
@@ -413,7 +419,8 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
   k_gather<DIM><<<blocks_for(L.n, gb), gb, 0, h->stream>>>(
       M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R,
       slopes_update ? M.G : nullptr, alpha_out_dev ? alpha_out_dev : L.alpha, want_diag ? L.D : nullptr,
-      gradnew_dev, (want_norm && !grouped) ? M.norm_part : nullptr, h->cfg.df_relax, L.rface,
+      gradnew_dev, (want_norm && !grouped) ? M.norm_part : nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg),
+      L.rface,
       (want_norm && grouped) ? M.qcell : nullptr, (grouped && !alpha_out_dev) ? M.active : nullptr);
   if (want_norm && !grouped)
     k_norm_final<DIM + 2><<<1, kBlock, 0, h->stream>>>(M.norm_part, M.norm_blocks, L.n, record ? M.hist : nullptr,
@@ -427,7 +434,7 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
 
 template <int DIM, typename T>
 void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
-  const double* alpha = h->cfg.df_relax ? L.alpha : L.ones;
+  const double* alpha = h->cfg.df_relax == 1 ? L.alpha : L.relax;
   T* dWs = sizeof(T) == 8 ? (T*)L.dWs64 : (T*)L.dWs32;
   T* dW = sizeof(T) == 8 ? (T*)L.dW64 : (T*)L.dW32;
   const int nc = L.n_colors;
@@ -472,7 +479,7 @@ void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want
   k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(
       L.faces, L.W, M.winf, p, L.Fc, want_diag ? L.rface : nullptr);
   k_coarse_cell<DIM><<<blocks_for(L.n, bc), bc, 0, h->stream>>>(
-      L.topo, L.W, L.Fc, L.rface, Pf, nullptr, h->cfg.df_relax ? L.alpha : L.ones, h->cfg.gamma, h->cfg.cfl_exp,
+      L.topo, L.W, L.Fc, L.rface, Pf, nullptr, h->cfg.df_relax == 1 ? L.alpha : L.relax, h->cfg.gamma, h->cfg.cfl_exp,
       h->cfg.cfl_imp, L.R, want_diag ? L.D : nullptr);
 }
 
@@ -734,6 +741,7 @@ int cgks_default_config(cgks_config* c) {
   c->learned_judge_every = 20;
   c->learned_max_error = 0.5;
   c->flux_precision = 0;
+  c->relax_beta = 0.5;
   return CGKS_OK;
 }
 
@@ -749,7 +757,8 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
       h->cfg.r_safety != 1.0 || !(h->cfg.weno_gamma_high > 0.0 && h->cfg.weno_gamma_high <= 1.0) ||
       h->cfg.check_every < 1 || (h->cfg.fine_smoother != 0 && h->cfg.fine_smoother != 1) ||
       (h->cfg.flux_precision != 0 && h->cfg.flux_precision != 1) ||
-      (h->cfg.df_relax != 0 && h->cfg.df_relax != 1) || (h->cfg.df_prolong != 0 && h->cfg.df_prolong != 1)) {
+      (h->cfg.df_relax < 0 || h->cfg.df_relax > 2) || (h->cfg.df_prolong != 0 && h->cfg.df_prolong != 1) ||
+      !(h->cfg.relax_beta >= 0.0 && h->cfg.relax_beta <= 1.0)) {
     delete h;
     return CGKS_ERR_ARG;
   }
@@ -1277,9 +1286,13 @@ int cgks_run_stage(cgks_t* h, int mesh_id, int stage) {
       else launch_flux<3>(h, M);
     } else {
       if (M.dim == 2)
-        k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax, L.rface, nullptr, nullptr);
+        k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
+            M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.alpha,
+            L.D, nullptr, nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg), L.rface, nullptr, nullptr);
       else
-        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.D, nullptr, nullptr, nullptr, h->cfg.df_relax, L.rface, nullptr, nullptr);
+        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
+            M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.alpha,
+            L.D, nullptr, nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg), L.rface, nullptr, nullptr);
     }
     CK(cudaGetLastError());
     return CGKS_OK;

@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
                                                    const double* __restrict__ dti, double* __restrict__ R,
                                                    double* __restrict__ Gout, double* __restrict__ alpha,
                                                    double* __restrict__ Dg, double* __restrict__ gradnew_out,
-                                                   double* __restrict__ norm_part, int df_relax,
+                                                   double* __restrict__ norm_part, double relax_fixed,
                                                    const double* __restrict__ rface, double* __restrict__ qcell,
                                                    const int* __restrict__ active) {
   using Dm = Dims<DIM>;
@@ -560,7 +560,8 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
       }
     }
     if (live) alpha[c] = a;
-    if (Dg) Dg[c] = lusgs_diag<DIM>(T, c, rface, df_relax ? a : 1.0, dte[c], dti[c]);
+    // LU-SGS diagonal with DF, or with the constant of the fixed-factor schemes (relax_fixed >= 0)
+    if (Dg) Dg[c] = lusgs_diag<DIM>(T, c, rface, relax_fixed < 0.0 ? a : relax_fixed, dte[c], dti[c]);
   }
   if (norm_part) {
     // block reduction in a fixed order: warp shuffles then warp 0

@@ -79,6 +79,10 @@ def test_errors_are_status_codes(cg):
         ctx.close()
     with pytest.raises(cg.CgksError):
         cg.Context(n_pre=2)  # only one pre-smoothing step is supported
+    with pytest.raises(cg.CgksError):
+        cg.Context(df_relax=3)  # no such relaxation scheme
+    with pytest.raises(cg.CgksError):
+        cg.Context(df_relax=2, relax_beta=1.5)  # the fixed factor lies in [0, 1]
 
 
 def test_open_mesh_is_rejected(cg):

@@ -308,3 +308,41 @@ def test_mixed_vcycle_error_against_oracle(ctx, name):
     print(f"\n{name}: MIXED state error {err:.2e} (state moved {moved:.2e})")
     assert err <= 1e-5
     np.testing.assert_allclose(norms, out["norms"], rtol=1e-3)
+
+
+SWITCHES = {
+    "fully_implicit": (dict(df_relax=0), dict(relax=1.0)),
+    "fixed_factor_0.5": (dict(df_relax=2, relax_beta=0.5), dict(relax=0.5)),
+    "plain_injection": (dict(df_prolong=0), dict(df_prolong=0)),
+    "explicit_fine_smoother": (dict(fine_smoother=1), dict(fine_smoother=1)),
+}
+
+
+@pytest.mark.parametrize("switch", list(SWITCHES))
+@pytest.mark.parametrize("name", ["vortex", "cylinder"])
+def test_vcycle_switches_match_oracle(name, switch):
+    """V-cycles (plain FP64) with the relaxation and prolongation switches of
+    the ablations: LU-SGS relaxed by 1 or by a fixed factor instead of DF,
+    plain injection instead of the DF-scaled prolongation, and the explicit
+    fine smoother; state and norms against the oracle with the same switch."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_06347_b300 import build, cgks
+    build.build()
+    lib_kw, ora_kw = SWITCHES[switch]
+    c = cgks.Context(**lib_kw)
+    try:
+        m = MESHES[name]
+        W, G, w = state_for(name, m, np.random.default_rng(13))
+        c.setup(1, m, w, W, G)
+        dim, nv, n = m["dim"], m["dim"] + 2, len(W)
+        ncyc = 3
+        norms = np.zeros((ncyc, nv, 2))
+        c.cgks_vcycle([1], ncyc, cgks.PLAIN_FP64, norms)
+        Wd = np.zeros_like(W)
+        c.cgks_get_state(1, Wd)
+    finally:
+        c.close()
+    out = oracle.OracleMesh(m).vcycle(oracle.cfg_vector(dim, winf=w, **ora_kw), W, G, np.ones(n), ncyc)
+    np.testing.assert_allclose(norms, out["norms"], rtol=1e-8)
+    np.testing.assert_allclose(Wd, out["W"], rtol=0, atol=1e-9 * np.max(np.abs(W)))

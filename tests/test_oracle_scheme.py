@@ -360,3 +360,46 @@ def test_vcycle_preserves_freestream():
     out = om.vcycle(oracle.cfg_vector(2), W, np.zeros((n, 4, 2)), np.ones(n), 2)
     np.testing.assert_allclose(out["W"], W, rtol=1e-14, atol=1e-14)
     assert np.all(out["stats"] == 0)
+
+
+@pytest.mark.parametrize("switch", [dict(), dict(relax=1.0), dict(relax=0.5), dict(df_prolong=0),
+                                    dict(fine_smoother=1)])
+def test_vcycle_is_its_steps(switch):
+    """A two-level V-cycle equals its steps run one by one (Sec 5.2): the
+    third-order residual with the DF slope update, the fine smoothing (an
+    LU-SGS step relaxed by DF, by a constant for the fully implicit (1) and
+    fixed-factor (0.5) schemes, or the explicit update of Eq. smo), the
+    residual at the smoothed state, restriction, the coarse FAS solve relaxed
+    the same way, and prolongation scaled by DF or plain injection."""
+    m = MESHES["cylinder"]
+    om = oracle.OracleMesh(m, levels=2)
+    rng = np.random.default_rng(31)
+    w = synth.freestream(2.0, angle_deg=10.0)
+    Wq, Gq, _, _ = physical_quadratic_state(rng, 2, m["cell_xyz"], scale=0.05)
+    W0 = synth.uniform_state(m, w) + Wq - Wq.mean(0)
+    n = len(W0)
+    a0 = rng.uniform(0.3, 1.0, n)
+    cfg = oracle.cfg_vector(2, winf=w, **switch)
+    out = om.vcycle(cfg, W0, Gq, a0, 1)
+
+    relax = switch.get("relax", -1.0)
+    r = om.residual(cfg, W0, Gq, a0)
+    al = r["alpha"]
+    G = al[:, None, None] * r["grad"]
+    if switch.get("fine_smoother", 0) == 1:
+        vol = om.cells(0)[0]
+        W = W0 - (r["dt_exp"] / vol)[:, None] * r["R"]
+    else:
+        W, _ = om.lusgs(cfg, W0, -r["R"], al if relax < 0 else np.full(n, relax), r["dt_exp"], r["dt_imp"])
+    r2 = om.residual(cfg, W, G, al)
+    al = r2["alpha"]
+    Wc0, ac, Rc = om.restrict(0, W, al, r2["R"])
+    Wc = om.coarse_solve(cfg, 1, Wc0, Rc, ac if relax < 0 else np.full(len(ac), relax))
+    W = om.prolong(cfg, 0, W, al if switch.get("df_prolong", 1) else np.ones(n), Wc, Wc0)
+    np.testing.assert_allclose(out["W"], W, rtol=0, atol=1e-14 * np.max(np.abs(W0)))
+    np.testing.assert_allclose(out["grad"], G, rtol=0, atol=1e-14 * np.max(np.abs(G)))
+    np.testing.assert_allclose(out["alpha"], al, rtol=0, atol=1e-13)
+    # the switches change the result
+    if switch:
+        base = om.vcycle(oracle.cfg_vector(2, winf=w), W0, Gq, a0, 1)
+        assert np.max(np.abs(base["W"] - out["W"])) > 1e-10
