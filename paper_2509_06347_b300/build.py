@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", f) for f in ("capi.cu", "host_mesh.cpp", "agglomerate.cpp")]
 CSRC = os.path.join(HERE, "csrc")
 # every source and header of the library (a change to any of them rebuilds it)
-DEPS = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cu", ".cuh", ".cpp", ".hpp"))] + \
+DEPS = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cu", ".cuh", ".cpp", ".hpp", ".inc"))] + \
     [os.path.join(ROOT, "include", "cgks.h")]
 LIB = os.path.join(HERE, "_lib", "libcgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -27,7 +27,7 @@ EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_erro
            "cgks_init_state", "cgks_get_state", "cgks_set_state", "cgks_residual", "cgks_reconstruct",
            "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
            "cgks_gks_points", "cgks_kfvs_points", "cgks_run_stage", "cgks_launch_count",
-           "cgks_vcycle_launch", "cgks_dword_selftest", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
+           "cgks_vcycle_launch", "cgks_dword_selftest", "cgks_special_selftest", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
            "cgks_autotune", "cgks_residual_coarse_noalloc", "cgks_mlp_set_params", "cgks_mlp_get_params",
            "cgks_mlp_forward", "cgks_mlp_grad", "cgks_mlp_dataset_append", "cgks_mlp_dataset_size",
            "cgks_mlp_dataset_clear", "cgks_mlp_train", "cgks_mlp_collect", "cgks_mlp_features", "cgks_learned_stats",
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH):
         "cgks_mesh_info": [P, I, P, P],
         "cgks_agglomerate": [P, I, I64, P, P, I64, P, P, I, I, D, P, P],
         "cgks_dword_selftest": [P, I64, P, P, P],
+        "cgks_special_selftest": [P, I64, P, P],
         "cgks_mlp_features": [P, I, P],
         "cgks_get_coloring": [P, I, I, P],
         "cgks_set_freestream": [P, I, P],
@@ -296,6 +297,13 @@ class Context:
         b = np.ascontiguousarray(b, np.float64)
         out = np.zeros((a.size, 7))
         self._check(self._L.cgks_dword_selftest(self.h, a.size, _ptr(a), _ptr(b), _ptr(out)))
+        return out
+
+    def cgks_special_selftest(self, x):
+        x = np.ascontiguousarray(x, np.float64)
+        out = np.zeros((x.size, 3))
+        self._check(self._L.cgks_special_selftest(self.h, x.size, _ptr(x) if x.size else None,
+                                                  _ptr(out) if x.size else None))
         return out
 
     def cgks_fma_probe(self, precision: int = 0) -> float:

@@ -1241,6 +1241,22 @@ int cgks_dword_selftest(cgks_t* h, int64_t n, const double* a, const double* b, 
   });
 }
 
+int cgks_special_selftest(cgks_t* h, int64_t n, const double* x, double* out) {
+  return guarded(h, [&]() -> int {
+    if (n < 0 || n >= (1ll << 31) || (n > 0 && (!x || !out))) throw ArgError("invalid self-test arguments");
+    if (n == 0) return CGKS_OK;
+    DBuf dx, dout;
+    dx.alloc((size_t)n * 8);
+    dout.alloc((size_t)n * 3 * 8);
+    CK(cudaMemcpyAsync(dx.p, x, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream));
+    k_special_selftest<<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, dx.as<double>(), dout.as<double>());
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, dout.p, (size_t)n * 3 * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return CGKS_OK;
+  });
+}
+
 int cgks_fma_probe(cgks_t* h, int precision, double* tflops) {
   return guarded(h, [&]() -> int {
     if (!tflops || (precision != 0 && precision != 1)) throw ArgError("invalid probe arguments");

@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include "dword.cuh"
+#include "special.cuh"
 
 namespace cgks {
 
@@ -127,8 +128,9 @@ __device__ __forceinline__ void normal_moments(const Prim<DIM, S>& p, int half, 
     m.mu[1] = U;
   } else {
     const S sl = sqrt(p.lam);
-    const S te = exp(-p.lam * U * U) * S(0.5 * M_2_SQRTPI) * (sl * h);  // e^{-lam U^2} / (2 sqrt(pi lam))
-    const S hs = S(0.5) * erfc(S(-half) * sl * U);
+    const S E = exp(-p.lam * U * U);
+    const S te = E * S(0.5 * M_2_SQRTPI) * (sl * h);  // e^{-lam U^2} / (2 sqrt(pi lam))
+    const S hs = S(0.5) * erfc_with_exp(S(-half) * sl * U, E);  // erfc(x) from E = e^{-x^2}
     m.mu[0] = hs;
     m.mu[1] = U * hs + half * te;
   }
