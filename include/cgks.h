@@ -272,11 +272,12 @@ int cgks_vcycle_launch(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycle
  * float exponent range.  Synchronises the stream. */
 int cgks_dword_selftest(cgks_t* h, int64_t n, const double* a, const double* b, double* out);
 
-/* Check of the complementary error function of the half-space moments (no
- * paper counterpart; Sec 2.3 uses erfc): for x (host, [n]) out (host,
- * [n][3]) receives erfc(x) as the flux computes it (exp(-x^2) times the
- * piecewise-polynomial erfcx), erfcx(|x|), and the CUDA library's erfc(x) for
- * comparison.  n < 2^31.  Synchronises the stream. */
+/* Check of the exponential and complementary error function of the
+ * half-space moments and time integrals (no paper counterpart; Sec 2.3 uses
+ * exp and erfc): for x (host, [n]) out (host, [n][5]) receives erfc(x) as the
+ * flux computes it (exp(-x^2) times the piecewise-polynomial erfcx),
+ * erfcx(|x|), exp(-|x|) as the flux computes it, and the CUDA library's
+ * erfc(x) and exp(-|x|) for comparison.  n < 2^31.  Synchronises the stream. */
 int cgks_special_selftest(cgks_t* h, int64_t n, const double* x, double* out);
 
 /* Arithmetic-throughput probe: independent FMA chains on every SM (precision

@@ -301,7 +301,7 @@ class Context:
 
     def cgks_special_selftest(self, x):
         x = np.ascontiguousarray(x, np.float64)
-        out = np.zeros((x.size, 3))
+        out = np.zeros((x.size, 5))
         self._check(self._L.cgks_special_selftest(self.h, x.size, _ptr(x) if x.size else None,
                                                   _ptr(out) if x.size else None))
         return out

@@ -1247,11 +1247,11 @@ int cgks_special_selftest(cgks_t* h, int64_t n, const double* x, double* out) {
     if (n == 0) return CGKS_OK;
     DBuf dx, dout;
     dx.alloc((size_t)n * 8);
-    dout.alloc((size_t)n * 3 * 8);
+    dout.alloc((size_t)n * 5 * 8);
     CK(cudaMemcpyAsync(dx.p, x, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream));
     k_special_selftest<<<blocks_for(n), kBlock, 0, h->stream>>>((int)n, dx.as<double>(), dout.as<double>());
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(out, dout.p, (size_t)n * 3 * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(out, dout.p, (size_t)n * 5 * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return CGKS_OK;
   });

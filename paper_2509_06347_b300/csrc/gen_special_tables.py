@@ -1,7 +1,8 @@
-"""Writes erfcx_table.inc: the coefficients of the scaled complementary error
-function erfcx(x) = exp(x^2) erfc(x) used by special.cuh.
+"""Writes special_tables.inc, the tables of special.cuh: the coefficients of the
+scaled complementary error function erfcx(x) = exp(x^2) erfc(x), and 2^(j/64)
+for j = 0..63 (the table of the exponential), each rounded to the nearest double.
 
-    python paper_2509_06347_b300/csrc/gen_erfcx_table.py
+    python paper_2509_06347_b300/csrc/gen_special_tables.py
 
 On [0, 8): 128 intervals of width 1/16; on each, the degree-7 polynomial in
 s = x - centre that interpolates erfcx at the 8 Chebyshev points of the
@@ -67,9 +68,9 @@ def main():
     for z in np.linspace(1e-9, 1.0, 257):
         ref = g(mp.mpf(float(z)))
         worst_tail = max(worst_tail, float(abs((horner(tail, float(z)) - ref) / ref)))
-    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "erfcx_table.inc")
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "special_tables.inc")
     with open(out, "w") as f:
-        f.write("// Generated by gen_erfcx_table.py: erfcx on [0, 8) in 128 intervals of width 1/16,\n")
+        f.write("// Generated by gen_special_tables.py.  erfcx on [0, 8) in 128 intervals of width 1/16,\n")
         f.write("// rows {centre, a0..a7, 0} of the degree-7 polynomial in x - centre; then the\n")
         f.write(f"// degree-{DEG_TAIL} polynomial in z = 64 / x^2 of x sqrt(pi) erfcx(x) for x >= 8.\n")
         f.write(f"// Largest relative error (double Horner vs mpmath): {worst:.2e} on [0, 8), "
@@ -80,6 +81,9 @@ def main():
         f.write("};\n")
         f.write(f"__device__ const double kErfcxTail[{DEG_TAIL + 1}] = {{"
                 + ", ".join(repr(v) for v in tail) + "};\n")
+        f.write("// 2^(j/64), j = 0..63\n")
+        f.write("__device__ const double kExp2Table[64] = {"
+                + ", ".join(repr(float(mp.mpf(2) ** (mp.mpf(j) / 64))) for j in range(64)) + "};\n")
     print(out, f"worst relative error {worst:.3e} (table), {worst_tail:.3e} (tail)")
 
 

@@ -346,16 +346,18 @@ __global__ void k_dword_selftest(int n, const double* __restrict__ a, const doub
   o[6] = static_cast<double>(erfc(y));
 }
 
-// out[i] = (erfc(x) from exp(-x^2) and the erfcx polynomials, erfcx(|x|), the
-// CUDA library erfc(x)) for the check of special.cuh
+// out[i] = (erfc(x) as the flux computes it, erfcx(|x|), exp(-|x|), and the
+// CUDA library's erfc(x) and exp(-|x|)) for the check of special.cuh
 __global__ void k_special_selftest(int n, const double* __restrict__ x, double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = x[i];
-  double* o = out + (size_t)i * 3;
-  o[0] = erfc_with_exp(v, exp(-v * v));
+  double* o = out + (size_t)i * 5;
+  o[0] = erfc_with_exp(v, exp_neg(-v * v));
   o[1] = erfcx_pos(fabs(v));
-  o[2] = erfc(v);
+  o[2] = exp_neg(-fabs(v));
+  o[3] = erfc(v);
+  o[4] = exp(-fabs(v));
 }
 
 // ---------------------------------------------------------------------------

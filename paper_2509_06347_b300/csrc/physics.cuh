@@ -128,7 +128,7 @@ __device__ __forceinline__ void normal_moments(const Prim<DIM, S>& p, int half, 
     m.mu[1] = U;
   } else {
     const S sl = sqrt(p.lam);
-    const S E = exp(-p.lam * U * U);
+    const S E = exp_neg(-p.lam * U * U);
     const S te = E * S(0.5 * M_2_SQRTPI) * (sl * h);  // e^{-lam U^2} / (2 sqrt(pi lam))
     const S hs = S(0.5) * erfc_with_exp(S(-half) * sl * U, E);  // erfc(x) from E = e^{-x^2}
     m.mu[0] = hs;
@@ -459,7 +459,7 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
   // collision time and time integrals
   const S pL = pl.rho * pl.h, pR = pr.rho * pr.h;
   const S tau = P.c1 * dt + P.c2 * fabs(pL - pR) / (pL + pR) * dt;
-  const S e = exp(-dt / tau);
+  const S e = exp_neg(-dt / tau);
   const S T1 = dt - tau * (S(1.0) - e);
   const S T2 = -tau * dt + S(2.0) * tau * tau - tau * (dt + S(2.0) * tau) * e;
   const S T3 = S(0.5) * dt * dt - tau * dt + tau * tau * (S(1.0) - e);
