@@ -243,9 +243,48 @@ __device__ __forceinline__ S poly_mom(const Mom<DIM, S>& m, const Poly<DIM, S>& 
   return s + m.xi2 * t;
 }
 
+// 2-D form of <u^A0 psi P>.  Grouped by powers of v, P reads
+//   sum_j v^j (sum_i c_ij u^i) + xi^2 (e_00 + e_10 u + e_01 v),
+// with c_i0 = (p0, pl0, pq00, qc0), c_i1 = (pl1, pq01, qc1), c_i2 = (pq11, qc0),
+// c_03 = qc1 and e = (h, qc0, qc1).  With D_j(a) = sum_i c_ij mu[a+i],
+// E_0(a) = h mu[a] + qc0 mu[a+1] and E_1(a) = qc1 mu[a] = D_3(a):
+//   <u^a v^b P>      = sum_j mv[b+j] D_j(a) + xi2 (mv[b] E_0(a) + mv[b+1] E_1(a))
+//   <u^a xi^2 P>     = xi2 sum_j mv[j] D_j(a) + xi4 (mv[0] E_0(a) + mv[1] E_1(a)).
+// Each 1-D moment product is formed once instead of once per output.
+template <int A0, typename S>
+__device__ __forceinline__ void poly_psi_mom_2d(const Mom<2, S>& m, const Poly<2, S>& P, S* out) {
+  const S* mu = m.mu;
+  const S* mv = m.mv;
+  S F0[3], F1[3], D2[3], D3[3], D0a = S(0.0), D1a = S(0.0), E0a = S(0.0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int a = A0 + k;
+    const S d0 = P.p0 * mu[a] + P.pl[0] * mu[a + 1] + P.pq[0][0] * mu[a + 2] + P.qc[0] * mu[a + 3];
+    const S d1 = P.pl[1] * mu[a] + P.pq[0][1] * mu[a + 1] + P.qc[1] * mu[a + 2];
+    const S e0 = P.h * mu[a] + P.qc[0] * mu[a + 1];
+    D2[k] = P.pq[1][1] * mu[a] + P.qc[0] * mu[a + 1];
+    D3[k] = P.qc[1] * mu[a];
+    F0[k] = d0 + m.xi2 * e0;
+    F1[k] = d1 + m.xi2 * D3[k];
+    if (k == 0) { D0a = d0; D1a = d1; E0a = e0; }
+  }
+  // <u^(A0+k) v^b P>; mv[0] = 1
+  auto M = [&](int k, int b) { return mv[b] * F0[k] + mv[b + 1] * F1[k] + mv[b + 2] * D2[k] + mv[b + 3] * D3[k]; };
+  out[0] = M(0, 0);
+  out[1] = M(1, 0);
+  out[2] = M(0, 1);
+  const S mxi = m.xi2 * (D0a * mv[0] + D1a * mv[1] + D2[0] * mv[2] + D3[0] * mv[3]) +
+                m.xi4 * (E0a * mv[0] + D3[0] * mv[1]);
+  out[3] = S(0.5) * (M(2, 0) + M(0, 2) + mxi);
+}
+
 // out = <u^A0 psi P>
 template <int DIM, int A0, typename S>
 __device__ __forceinline__ void poly_psi_mom(const Mom<DIM, S>& m, const Poly<DIM, S>& P, S* out) {
+  if constexpr (DIM == 2) {
+    poly_psi_mom_2d<A0, S>(m, P, out);
+    return;
+  }
   out[0] = poly_mom<DIM, A0, 0, 0, false>(m, P);
   out[1] = poly_mom<DIM, A0 + 1, 0, 0, false>(m, P);
   out[2] = poly_mom<DIM, A0, 1, 0, false>(m, P);
