@@ -216,33 +216,6 @@ __device__ __forceinline__ Poly<DIM, S> make_poly(S c0, S cA, S cT, const S (*a)
   return P;
 }
 
-// <x^(a,b,c) P>  (XI = false)  or  <x^(a,b,c) xi^2 P>  (XI = true)
-template <int DIM, int A, int B, int C, bool XI, typename S>
-__device__ __forceinline__ S poly_mom(const Mom<DIM, S>& m, const Poly<DIM, S>& P) {
-  // velocity part without the xi^2 terms of P
-  S s = P.p0 * G<DIM, A, B, C>(m);
-  s += P.pl[0] * G<DIM, A + 1, B, C>(m) + P.pl[1] * G<DIM, A, B + 1, C>(m);
-  s += P.pq[0][0] * G<DIM, A + 2, B, C>(m) + P.pq[0][1] * G<DIM, A + 1, B + 1, C>(m) +
-       P.pq[1][1] * G<DIM, A, B + 2, C>(m);
-  S q0 = G<DIM, A + 3, B, C>(m) + G<DIM, A + 1, B + 2, C>(m);
-  S q1 = G<DIM, A + 2, B + 1, C>(m) + G<DIM, A, B + 3, C>(m);
-  if constexpr (DIM == 3) {
-    s += P.pl[2] * G<DIM, A, B, C + 1>(m);
-    s += P.pq[0][2] * G<DIM, A + 1, B, C + 1>(m) + P.pq[1][2] * G<DIM, A, B + 1, C + 1>(m) +
-         P.pq[2][2] * G<DIM, A, B, C + 2>(m);
-    q0 += G<DIM, A + 1, B, C + 2>(m);
-    q1 += G<DIM, A, B + 1, C + 2>(m);
-    const S q2 = G<DIM, A + 2, B, C + 1>(m) + G<DIM, A, B + 2, C + 1>(m) + G<DIM, A, B, C + 3>(m);
-    s += P.qc[2] * q2;
-  }
-  s += P.qc[0] * q0 + P.qc[1] * q1;
-  // terms of P carrying xi^2: h xi^2 + sum_d qc_d x_d xi^2
-  S t = P.h * G<DIM, A, B, C>(m) + P.qc[0] * G<DIM, A + 1, B, C>(m) + P.qc[1] * G<DIM, A, B + 1, C>(m);
-  if constexpr (DIM == 3) t += P.qc[2] * G<DIM, A, B, C + 1>(m);
-  if constexpr (XI) return m.xi2 * s + m.xi4 * t;
-  return s + m.xi2 * t;
-}
-
 // 2-D form of <u^A0 psi P>.  Grouped by powers of v, P reads
 //   sum_j v^j (sum_i c_ij u^i) + xi^2 (e_00 + e_10 u + e_01 v),
 // with c_i0 = (p0, pl0, pq00, qc0), c_i1 = (pl1, pq01, qc1), c_i2 = (pq11, qc0),
@@ -278,23 +251,66 @@ __device__ __forceinline__ void poly_psi_mom_2d(const Mom<2, S>& m, const Poly<2
   out[3] = S(0.5) * (M(2, 0) + M(0, 2) + mxi);
 }
 
+// 3-D form of <u^A0 psi P>, grouped by the powers (j, k) of v and w:
+//   D_00(a) = p0 mu[a] + pl0 mu[a+1] + pq00 mu[a+2] + qc0 mu[a+3]
+//   D_10(a) = pl1 mu[a] + pq01 mu[a+1] + qc1 mu[a+2]
+//   D_01(a) = pl2 mu[a] + pq02 mu[a+1] + qc2 mu[a+2]
+//   D_20(a) = pq11 mu[a] + qc0 mu[a+1],  D_02(a) = pq22 mu[a] + qc0 mu[a+1]
+//   D_11(a) = pq12 mu[a],  D_30 = D_12 = Q1(a) = qc1 mu[a],  D_21 = D_03 = Q2(a) = qc2 mu[a]
+// and the xi^2 part E_00(a) = h mu[a] + qc0 mu[a+1], E_10 = Q1, E_01 = Q2, so
+//   <u^a v^b w^c P> = sum_jk mv[b+j] mw[c+k] (D_jk(a) + xi2 E_jk(a))
+//   <u^a xi^2 P>    = xi2 sum_jk mv[j] mw[k] D_jk(a) + xi4 sum_jk mv[j] mw[k] E_jk(a).
+template <int A0, typename S>
+__device__ __forceinline__ void poly_psi_mom_3d(const Mom<3, S>& m, const Poly<3, S>& P, S* out) {
+  const S* mu = m.mu;
+  const S* mv = m.mv;
+  const S* mw = m.mw;
+  struct Grp { S F00, F10, F01, D20, D02, D11, Q1, Q2; };
+  Grp g[3];
+  S D00a = S(0.0), D10a = S(0.0), D01a = S(0.0), E00a = S(0.0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int a = A0 + k;
+    const S d00 = P.p0 * mu[a] + P.pl[0] * mu[a + 1] + P.pq[0][0] * mu[a + 2] + P.qc[0] * mu[a + 3];
+    const S d10 = P.pl[1] * mu[a] + P.pq[0][1] * mu[a + 1] + P.qc[1] * mu[a + 2];
+    const S d01 = P.pl[2] * mu[a] + P.pq[0][2] * mu[a + 1] + P.qc[2] * mu[a + 2];
+    const S e00 = P.h * mu[a] + P.qc[0] * mu[a + 1];
+    g[k].D20 = P.pq[1][1] * mu[a] + P.qc[0] * mu[a + 1];
+    g[k].D02 = P.pq[2][2] * mu[a] + P.qc[0] * mu[a + 1];
+    g[k].D11 = P.pq[1][2] * mu[a];
+    g[k].Q1 = P.qc[1] * mu[a];
+    g[k].Q2 = P.qc[2] * mu[a];
+    g[k].F00 = d00 + m.xi2 * e00;
+    g[k].F10 = d10 + m.xi2 * g[k].Q1;
+    g[k].F01 = d01 + m.xi2 * g[k].Q2;
+    if (k == 0) { D00a = d00; D10a = d10; D01a = d01; E00a = e00; }
+  }
+  // <u^(A0+k) v^b w^c P>, summed by powers of w; mv[0] = mw[0] = 1
+  auto M = [&](int k, int b, int c) {
+    const Grp& q = g[k];
+    return mw[c] * (mv[b] * q.F00 + mv[b + 1] * q.F10 + mv[b + 2] * q.D20 + mv[b + 3] * q.Q1) +
+           mw[c + 1] * (mv[b] * q.F01 + mv[b + 1] * q.D11 + mv[b + 2] * q.Q2) +
+           mw[c + 2] * (mv[b] * q.D02 + mv[b + 1] * q.Q1) + mw[c + 3] * (mv[b] * q.Q2);
+  };
+  out[0] = M(0, 0, 0);
+  out[1] = M(1, 0, 0);
+  out[2] = M(0, 1, 0);
+  out[3] = M(0, 0, 1);
+  const Grp& q = g[0];
+  const S sv = (D00a + mv[1] * D10a + mv[2] * q.D20 + mv[3] * q.Q1) +
+               mw[1] * (D01a + mv[1] * q.D11 + mv[2] * q.Q2) + mw[2] * (q.D02 + mv[1] * q.Q1) + mw[3] * q.Q2;
+  const S mxi = m.xi2 * sv + m.xi4 * (E00a + mv[1] * q.Q1 + mw[1] * q.Q2);
+  out[4] = S(0.5) * (M(2, 0, 0) + M(0, 2, 0) + M(0, 0, 2) + mxi);
+}
+
 // out = <u^A0 psi P>
 template <int DIM, int A0, typename S>
 __device__ __forceinline__ void poly_psi_mom(const Mom<DIM, S>& m, const Poly<DIM, S>& P, S* out) {
   if constexpr (DIM == 2) {
     poly_psi_mom_2d<A0, S>(m, P, out);
-    return;
+  } else {
+    poly_psi_mom_3d<A0, S>(m, P, out);
   }
-  out[0] = poly_mom<DIM, A0, 0, 0, false>(m, P);
-  out[1] = poly_mom<DIM, A0 + 1, 0, 0, false>(m, P);
-  out[2] = poly_mom<DIM, A0, 1, 0, false>(m, P);
-  S e = poly_mom<DIM, A0 + 2, 0, 0, false>(m, P) + poly_mom<DIM, A0, 2, 0, false>(m, P) +
-        poly_mom<DIM, A0, 0, 0, true>(m, P);
-  if constexpr (DIM == 3) {
-    out[3] = poly_mom<DIM, A0, 0, 1, false>(m, P);
-    e += poly_mom<DIM, A0, 0, 2, false>(m, P);
-  }
-  out[DIM + 1] = S(0.5) * e;
 }
 
 // Sum over directions d of (dF_d/dW) . dW_d for the Euler fluxes F_d along the
