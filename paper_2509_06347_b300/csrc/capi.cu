@@ -386,7 +386,7 @@ void launch_recon(cgks_t* h, MeshDev& M) {
 }
 
 template <int DIM>
-void launch_flux(cgks_t* h, MeshDev& M, bool point = true) {
+void launch_flux(cgks_t* h, MeshDev& M, bool point = true, bool radius = true) {
   LevelDev& L = M.lev[0];
   constexpr int NGP = Dims<DIM>::NGP, FPW = 32 / NGP;
   const int64_t warps = (M.fine.nf + FPW - 1) / FPW;
@@ -396,11 +396,11 @@ void launch_flux(cgks_t* h, MeshDev& M, bool point = true) {
   if (h->cfg.flux_precision == 1) {
     auto kern = point ? k_flux<DIM, true, dword> : k_flux<DIM, false, dword>;
     kern<<<nb, M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef_dw, L.dte, M.winf, phys_dword(P), P.gamma, M.Fface,
-                                              M.Wface, M.aface, L.W, L.rface);
+                                              M.Wface, M.aface, L.W, radius ? L.rface : nullptr);
   } else {
     auto kern = point ? k_flux<DIM, true, double> : k_flux<DIM, false, double>;
     kern<<<nb, M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, P, P.gamma, M.Fface, M.Wface, M.aface,
-                                              L.W, L.rface);
+                                              L.W, radius ? L.rface : nullptr);
   }
 }
 
@@ -411,8 +411,8 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
                    double* alpha_out_dev, double* gradnew_dev) {
   LevelDev& L = M.lev[0];
   launch_recon<DIM>(h, M);
-  // the time-evolved point values only feed the slopes
-  launch_flux<DIM>(h, M, slopes_update || gradnew_dev != nullptr);
+  // the time-evolved point values only feed the slopes, the spectral radii only the LU-SGS diagonal
+  launch_flux<DIM>(h, M, slopes_update || gradnew_dev != nullptr, want_diag);
   const bool grouped = !M.lgrp.empty();
   // norm partials need whole blocks of kBlock threads
   const int gb = (want_norm && !grouped) ? kBlock : M.blk[B_GATHER];

@@ -191,9 +191,9 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
       for (int d = 0; d < DIM; ++d) un += W0[1 + d] * nrm[m][d];
       sum += Sf[m] * (fabs(un * ir) + cs);
     }
-    const double V = M.vol[c];
-    dte[c] = cfl_exp * V / sum;
-    dti[c] = cfl_imp * V / sum;
+    const double q = M.vol[c] / sum;
+    dte[c] = cfl_exp * q;
+    dti[c] = cfl_imp * q;
   }
   const bool ok = M.op_ok[c] != 0;
   const double ap = alpha_prev[c];
@@ -275,10 +275,13 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
       for (int x = d; x < DIM; ++x) b2q += H[d][x] * H[d][x];
     }
     b2 = b1s * b2 + b2s * b2q;
+    // w_H ~ gam_hi (1 + tz / (b2 + eps)), w_L ~ gl (1 + tz / (b1 + eps)), normalised;
+    // both multiplied by (b1 + eps)(b2 + eps) so that one reciprocal remains
     const double gl = 1.0 - gam_hi;
     const double tz = fabs(b2 - b1);
-    double wh = gam_hi * (1.0 + tz / (b2 + weps));
-    double wl = gl * (1.0 + tz / (b1 + weps));
+    const double e1 = b1 + weps, e2 = b2 + weps;
+    double wh = gam_hi * (e2 + tz) * e1;
+    double wl = gl * (e1 + tz) * e2;
     const double iw = 1.0 / (wh + wl);
     wh *= iw;
     wl *= iw;
@@ -302,8 +305,8 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
       double ke = 0.0;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) ke += Wp[1 + d] * Wp[1 + d];
-      const double pr = Wp[NV - 1] - 0.5 * ke / Wp[0];
-      if (!(Wp[0] > 0.0) || !(pr > 0.0)) bad = true;
+      // p > 0 as rho E - |rho u|^2 / 2 > 0 once rho > 0 (no division)
+      if (!(Wp[0] > 0.0) || !(Wp[NV - 1] * Wp[0] - 0.5 * ke > 0.0)) bad = true;
     }
   }
   if (bad) {
@@ -480,6 +483,8 @@ __global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(De
       if (POINT) Wface[(size_t)f * NV + v] = static_cast<double>(Ws[v]);
     }
     aface[f] = static_cast<double>(af);
+  }
+  if (rface && active && g == 0) {
     // spectral radius of the LU-SGS splitting at the mean of the cell means
     const int L = M.fL[f], R = M.fR[f];
     double n[DIM], WL[NV], WR[NV];
