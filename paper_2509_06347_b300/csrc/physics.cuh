@@ -351,6 +351,63 @@ __device__ __forceinline__ void euler_flux_divergence(S gamma, const S* W, const
   }
 }
 
+// Sum over directions d of (dQ_d/dW) . dW_d, with Q_d(W) = rho <u_0 u_d psi g_W>
+// the second velocity moments of the full-space Maxwellian of W (u_0 along the
+// local normal).  For the slopes a_d of that Maxwellian (<psi (a_d . psi)> = dW_d
+// / rho) this equals rho <u_0 psi (a . u)>, the part of the equilibrium flux
+// that the time integral T2 multiplies, in closed form.  With theta = p / rho,
+// D velocity components and K internal degrees of freedom,
+//   Q_d^rho = rho U_0 U_d + p delta_0d
+//   Q_d^i   = rho U_0 U_d U_i + p (U_0 delta_di + U_d delta_0i + U_i delta_0d)
+//   Q_d^E   = U_0 U_d (rho |U|^2 + (D + 4 + K) p) / 2
+//             + delta_0d (p |U|^2 + (D + 2 + K) p theta) / 2.
+template <int DIM, typename S>
+__device__ __forceinline__ void second_moment_divergence(S gamma, S K, const S* W, const S (*dW)[DIM + 2], S* out) {
+  constexpr int NV = DIM + 2;
+  const S ir = S(1.0) / W[0];
+  S U[DIM], q2 = S(0.0);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    U[i] = W[1 + i] * ir;
+    q2 += U[i] * U[i];
+  }
+  const S p = (gamma - S(1.0)) * (W[NV - 1] - S(0.5) * W[0] * q2);
+  const S th = p * ir;
+  const S cA = S(double(DIM + 4)) + K, cB = S(double(DIM + 2)) + K;
+  const S A = W[0] * q2 + cA * p;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = S(0.0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const S* g = dW[d];
+    S du[DIM], udu = S(0.0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      du[i] = (g[1 + i] - U[i] * g[0]) * ir;
+      udu += U[i] * du[i];
+    }
+    const S dp = (gamma - S(1.0)) * (g[NV - 1] - S(0.5) * g[0] * q2 - W[0] * udu);
+    const S u0d = U[0] * U[d];
+    const S du0d = du[0] * U[d] + U[0] * du[d];  // d(U_0 U_d)
+    out[0] += g[0] * u0d + W[0] * du0d;
+    if (d == 0) out[0] += dp;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      S t = g[0] * u0d * U[i] + W[0] * (du0d * U[i] + u0d * du[i]);
+      if (i == d) t += dp * U[0] + p * du[0];
+      if (i == 0) t += dp * U[d] + p * du[d];
+      if (d == 0) t += dp * U[i] + p * du[i];
+      out[1 + i] += t;
+    }
+    const S dA = g[0] * q2 + S(2.0) * W[0] * udu + cA * dp;
+    out[NV - 1] += S(0.5) * (du0d * A + u0d * dA);
+    if (d == 0) {
+      const S dth = (dp - th * g[0]) * ir;
+      out[NV - 1] += S(0.5) * (dp * q2 + S(2.0) * p * udu + cB * (dp * th + p * dth));
+    }
+  }
+}
+
 // (dF_n/dW) . v for the Euler flux through the local normal (first axis)
 template <int DIM, typename S>
 __device__ __forceinline__ void euler_flux_jvp_normal(S gamma, const S* W, const S* v, S* out) {
@@ -389,6 +446,16 @@ template <int DIM, typename S>
 __device__ __forceinline__ void euler_flux_divergence_c(S gamma, const S* W, const S (*dW)[DIM + 2], S* out) {
   if constexpr (OutOfLine<S>::value) euler_flux_divergence_ool<DIM, S>(gamma, W, dW, out);
   else euler_flux_divergence<DIM, S>(gamma, W, dW, out);
+}
+template <int DIM, typename S>
+__device__ __noinline__ void second_moment_divergence_ool(S gamma, S K, const S* W, const S (*dW)[DIM + 2], S* out) {
+  second_moment_divergence<DIM, S>(gamma, K, W, dW, out);
+}
+template <int DIM, typename S>
+__device__ __forceinline__ void second_moment_divergence_c(S gamma, S K, const S* W, const S (*dW)[DIM + 2],
+                                                           S* out) {
+  if constexpr (OutOfLine<S>::value) second_moment_divergence_ool<DIM, S>(gamma, K, W, dW, out);
+  else second_moment_divergence<DIM, S>(gamma, K, W, dW, out);
 }
 template <int DIM, typename S>
 __device__ __noinline__ void moments_ool(const Prim<DIM, S>& p, S K, int half, Mom<DIM, S>& m) {
@@ -460,23 +527,19 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
       return;
     }
   }
-  const Prim<DIM, S> pc = to_prim<DIM, S>(Wc, P);
-  Mom<DIM, S> mc;
-  moments_c<DIM, S>(pc, K, 0, mc);
-  // spatial slopes of the three Maxwellians (Eq. co)
-  S al[DIM][NV], ar[DIM][NV], ac[DIM][NV], b[NV];
+  const S irc = S(1.0) / Wc[0];
+  // spatial slopes of the two kinetic Maxwellians (Eq. co); the interface
+  // Maxwellian's slopes enter only through closed-form moments below
+  S al[DIM][NV], ar[DIM][NV], b[NV];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const S il = pl.irho, irr = pr.irho, ic = pc.irho;
+    const S il = pl.irho, irr = pr.irho;
 #pragma unroll
     for (int i = 0; i < NV; ++i) b[i] = Gl[d][i] * il;
     slope_solve_c<DIM, S>(pl, P, b, al[d]);
 #pragma unroll
     for (int i = 0; i < NV; ++i) b[i] = Gr[d][i] * irr;
     slope_solve_c<DIM, S>(pr, P, b, ar[d]);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) b[i] = S(0.5) * (Gl[d][i] + Gr[d][i]) * ic;
-    slope_solve_c<DIM, S>(pc, P, b, ac[d]);
   }
   // time slopes from <A + a.u> = 0, with <psi (a.u)> of a full-space
   // Maxwellian given by the Euler-flux divergence of its slopes
@@ -492,9 +555,11 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
     for (int i = 0; i < NV; ++i) s[i] *= -pr.irho;
     slope_solve_c<DIM, S>(pr, P, s, Ar);
   }
-  // interface Maxwellian: <psi (a_c.u)> = Euler-flux divergence; its time slope
-  // gives <psi (A_c.psi)> = W_t = -<psi (a_c.u)> and <u psi (A_c.psi)> = J_n W_t
-  S PAc[NV], UAc[NV];
+  // interface Maxwellian with the mean slopes: <psi (a_c.u)> = Euler-flux
+  // divergence; its time slope gives <psi (A_c.psi)> = W_t = -<psi (a_c.u)>
+  // and <u psi (A_c.psi)> = J_n W_t; <u psi (a_c.u)> is the divergence of the
+  // second moments; <u psi> is the Euler flux
+  S PAc[NV], UAc[NV], QAc[NV], Fc[NV];
   {
     S gc[DIM][NV];
 #pragma unroll
@@ -502,13 +567,24 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
 #pragma unroll
       for (int i = 0; i < NV; ++i) gc[d][i] = S(0.5) * (Gl[d][i] + Gr[d][i]);
     euler_flux_divergence_c<DIM, S>(P.gamma, Wc, gc, PAc);
+    second_moment_divergence_c<DIM, S>(P.gamma, K, Wc, gc, QAc);
     S wt[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      PAc[i] *= pc.irho;
+      PAc[i] *= irc;
       wt[i] = -PAc[i];
     }
     euler_flux_jvp_normal<DIM, S>(P.gamma, Wc, wt, UAc);
+    // Euler flux of W^c through the local normal
+    const S un = Wc[1] * irc;
+    S kc = S(0.0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) kc += Wc[1 + d] * Wc[1 + d];
+    const S pwc = (P.gamma - S(1.0)) * (Wc[NV - 1] - S(0.5) * kc * irc);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Fc[i] = un * Wc[i];
+    Fc[1] += pwc;
+    Fc[NV - 1] += un * pwc;
   }
   (void)Ac;
   // collision time and time integrals
@@ -521,20 +597,14 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
   const S T4 = tau * (S(1.0) - e);
   const S T5 = tau * tau - tau * (dt + tau) * e;
   const S C1 = S(1.0) - e, C2 = (dt + tau) * e - tau, C3 = dt - tau + tau * e;
-  // --- equilibrium part (g^c, full space): T1 + T2 (a_c . u) moments
+  // --- equilibrium part (g^c, full space): T1 <u psi> + T2 <u psi (a_c . u)>
+  // + T3 <u psi (A_c . psi)>; point value C1 <psi> + (C2 - C3) <psi (A_c . psi)>
   S fx[NV], wx[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) wx[i] = S(0.0);
-  kin_moments_c<DIM, 1, S>(mc, T1, T2, S(0.0), ac, nullptr, fx);
-#pragma unroll
-  for (int i = 0; i < NV; ++i) fx[i] += T3 * UAc[i];
-  if (POINT) {
-    psi_mom<DIM, 0, 0, 0>(mc, t);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) wx[i] += C1 * t[i] + (C2 - C3) * PAc[i];
+  for (int i = 0; i < NV; ++i) {
+    F[i] = T1 * Fc[i] + T2 * QAc[i] + T3 * Wc[0] * UAc[i];
+    Wt[i] = POINT ? C1 * Wc[i] + (C2 - C3) * Wc[0] * PAc[i] : S(0.0);
   }
-#pragma unroll
-  for (int i = 0; i < NV; ++i) { F[i] = pc.rho * fx[i]; Wt[i] = pc.rho * wx[i]; }
   // --- kinetic part (g^l on u > 0, g^r on u < 0)
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
