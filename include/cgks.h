@@ -56,7 +56,13 @@ enum {
 };
 
 /* boundary tags */
-enum { CGKS_TAG_WALL = 1, CGKS_TAG_FARFIELD = 2 };
+/* boundary tags: slip (inviscid) wall; far field (free stream on inflow faces,
+ * interior state on outflow faces); no-slip adiabatic wall (Navier-Stokes);
+ * far field from the Riemann invariants along the normal (subsonic faces take
+ * the outgoing invariant from the interior, the incoming one from the free
+ * stream, tangential velocity and entropy from upstream; supersonic faces the
+ * upwind state) */
+enum { CGKS_TAG_WALL = 1, CGKS_TAG_FARFIELD = 2, CGKS_TAG_NOSLIP_WALL = 3, CGKS_TAG_FARFIELD_RIEMANN = 4 };
 
 typedef struct cgks_config {
   double gamma;           /* ratio of specific heats (1.4) */
@@ -85,6 +91,10 @@ typedef struct cgks_config {
   int flux_precision;        /* fine gas-kinetic flux: 0 FP64; 1 double-word (two floats, ~48-bit
                                 significand, about 3.6e-15 unit roundoff) on the FP32 pipes (0) */
   double relax_beta;         /* constant relaxation factor of df_relax 2, in [0, 1] (0.5) */
+  double mu;                 /* dynamic viscosity: 0 solves the Euler equations (tau = C1 dt +
+                                C2 |dp|/(pl+pr) dt); mu > 0 the Navier-Stokes equations with
+                                Pr = 1 (Sec 2.1): tau = mu / p + C2 |dp|/(pl+pr) dt on the fine
+                                level, p that of the interface equilibrium (0) */
 } cgks_config;
 
 typedef struct cgks_ctx cgks_t;

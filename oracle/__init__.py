@@ -34,7 +34,7 @@ _LIB = os.path.join(_HERE, "_build", "libcgks_oracle.so")
 
 DEFAULTS = dict(gamma=1.4, cfl_imp=10.0, cfl_exp=0.5, tau_c1=0.01, tau_c2=1.0,
                 weno_gamma_high=0.95, weno_eps=1e-15, r_safety=1.0, n_sweep=6,
-                relax=-1.0, df_prolong=1, fine_smoother=0)
+                relax=-1.0, df_prolong=1, fine_smoother=0, mu=0.0)
 
 
 def build(force: bool = False) -> str:
@@ -88,6 +88,7 @@ def lib():
             "om_norms": (None, [P, I, dp, dp]),
             "om_vcycle": (I, [P, dp, dp, dp, dp, I, dp, lp]),
             "om_prolong": (None, [P, I, dp, dp, dp, dp, dp]),
+            "om_ghost_state": (None, [I, dp, I, dp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -101,7 +102,8 @@ def cfg_vector(dim: int, winf=None, **over) -> np.ndarray:
     weno_eps, r_safety, n_sweep, then the free-stream state (nv values), then the
     V-cycle switches: relax (negative: DF relaxes LU-SGS; else this constant
     stands for DF), df_prolong (1: DF-scaled prolongation; 0: plain injection)
-    and fine_smoother (0: LU-SGS step; 1: explicit update)."""
+    and fine_smoother (0: LU-SGS step; 1: explicit update), then mu (dynamic
+    viscosity; 0 for the Euler equations)."""
     c = dict(DEFAULTS)
     c.update(over)
     nv = dim + 2
@@ -112,7 +114,8 @@ def cfg_vector(dim: int, winf=None, **over) -> np.ndarray:
     return np.ascontiguousarray(np.concatenate([[c["gamma"], c["cfl_imp"], c["cfl_exp"], c["tau_c1"],
                                                  c["tau_c2"], c["weno_gamma_high"], c["weno_eps"],
                                                  c["r_safety"], float(c["n_sweep"])], w,
-                                                [c["relax"], float(c["df_prolong"]), float(c["fine_smoother"])]]))
+                                                [c["relax"], float(c["df_prolong"]), float(c["fine_smoother"]),
+                                                 c["mu"]]]))
 
 
 def _c(a, dt=np.float64):
@@ -261,6 +264,13 @@ class OracleMesh:
                         norms.reshape(-1), stats)
         return dict(W=Ws, grad=np.transpose(Gs, (0, 2, 1)).copy(), alpha=al, norms=norms,
                     stats=stats)
+
+
+def ghost_state(dim, cfg, tag, n, W):
+    """Ghost state across a boundary face with outward unit normal n."""
+    Wg = np.zeros(dim + 2)
+    lib().om_ghost_state(dim, _c(cfg), int(tag), _c(n), _c(W), Wg)
+    return Wg
 
 
 def gks_point(dim, cfg, Wl, dWl, Wr, dWr, dt):

@@ -49,6 +49,7 @@ typedef struct {
                              implicit; in (0,1): the fixed-factor scheme of the remark) */
   int df_prolong;         /* 1: prolongation scaled by DF; 0: plain injection */
   int fine_smoother;      /* 0: DF-relaxed LU-SGS step; 1: explicit update (Eq. smo) */
+  double mu;              /* dynamic viscosity: 0 Euler; > 0 Navier-Stokes, Pr = 1 */
 } OCfg;
 
 static void cfg_from(const double* c, int nv, OCfg* o) {
@@ -59,6 +60,7 @@ static void cfg_from(const double* c, int nv, OCfg* o) {
   o->relax = c[9 + nv];
   o->df_prolong = (int)c[10 + nv];
   o->fine_smoother = (int)c[11 + nv];
+  o->mu = c[12 + nv];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -268,7 +270,7 @@ typedef struct {
 /* Wl, Wr: conservative states (rho, rho u_n, rho u_t1, [rho u_t2], rho E);
  * dWl, dWr: derivatives [dim][nv] along (n, t1, t2);  dt: flux time step.
  * Outputs: Fbar (time-averaged flux over [0, dt]), Wt (point value at t = dt). */
-static void gks_point(int dim, double gamma, double c1, double c2, const double* Wl,
+static void gks_point(int dim, double gamma, double c1, double c2, double mu, const double* Wl,
                       const double* dWl, const double* Wr, const double* dWr, double dt,
                       double* Fbar, double* Wt, GksDebug* dbg) {
   int nv = dim + 2;
@@ -307,6 +309,7 @@ static void gks_point(int dim, double gamma, double c1, double c2, const double*
   /* equilibrium state at the interface from half-space moments (Eq. compatibility2) */
   double Wc[MAXV], pc[MAXV];
   for (int i = 0; i < nv; ++i) Wc[i] = poly_mom(&glp, &psi[i]) + poly_mom(&grm, &psi[i]);
+  const double p_eq = pressure(dim, gamma, Wc);
   {
     /* reading (vacuum, not treated by the paper): when both sides move apart so
      * fast that the half-space moments give no admissible equilibrium, the
@@ -335,9 +338,11 @@ static void gks_point(int dim, double gamma, double c1, double c2, const double*
   for (int i = 0; i < nv; ++i) bc[i] = -poly_mom2(&gc, &psi[i], &auc);
   solve_slope(&gc, dim, bc, Ac);
 
-  /* reading: numerical collision time for the Euler equations */
+  /* reading: numerical collision time C1 dt + C2 |dp| / (pl + pr) dt for the
+   * Euler equations; for the Navier-Stokes equations (Sec 2.1: tau = mu / p,
+   * Pr = 1) mu / p of the interface equilibrium replaces C1 dt */
   double pL = 1.0 / (2.0 * pl[1 + dim]) * pl[0], pR = 1.0 / (2.0 * pr[1 + dim]) * pr[0];
-  double tau = c1 * dt + c2 * fabs(pL - pR) / (pL + pR) * dt;
+  double tau = (mu > 0.0 ? mu / p_eq : c1 * dt) + c2 * fabs(pL - pR) / (pL + pR) * dt;
 
   Poly Alp, Arp, Acp;
   poly_lin(&Alp, dim, Al);
@@ -813,12 +818,57 @@ static int is_inflow(const OCfg* cfg, int dim, const double* n) {
   return un < 0.0;
 }
 /* ghost mean state across a boundary face with outward unit normal n */
+/* far field by the characteristic (Riemann-invariant) boundary state: with
+ * the outward normal n, J+ = u_n + 2c/(gamma-1) leaves the domain (interior
+ * values) and J- = u_n - 2c/(gamma-1) enters it (free-stream values); on the
+ * face u_n = (J+ + J-)/2 and c = (gamma-1)(J+ - J-)/4, while the entropy
+ * p/rho^gamma and the tangential velocity are those of the upstream side.  A
+ * supersonic normal free stream takes the free stream on inflow and the
+ * interior on outflow. */
+static void riemann_state(const OCfg* cfg, int dim, const double* n, const double* W, double* Wb) {
+  int nv = dim + 2;
+  double g = cfg->gamma;
+  double ui[MAXD], uf[MAXD], uin = 0, ufn = 0;
+  for (int d = 0; d < dim; ++d) {
+    ui[d] = W[1 + d] / W[0]; uf[d] = cfg->winf[1 + d] / cfg->winf[0];
+    uin += ui[d] * n[d]; ufn += uf[d] * n[d];
+  }
+  double p_i = pressure(dim, g, W), p_f = pressure(dim, g, cfg->winf);
+  double c_i = sqrt(g * p_i / W[0]), c_f = sqrt(g * p_f / cfg->winf[0]);
+  if (fabs(ufn) >= c_f) {
+    const double* src = ufn < 0.0 ? cfg->winf : W;
+    for (int v = 0; v < nv; ++v) Wb[v] = src[v];
+    return;
+  }
+  double jp = uin + 2.0 * c_i / (g - 1.0), jm = ufn - 2.0 * c_f / (g - 1.0);
+  double un = 0.5 * (jp + jm), c = 0.25 * (g - 1.0) * (jp - jm);
+  int inflow = un < 0.0;
+  double s = inflow ? p_f / pow(cfg->winf[0], g) : p_i / pow(W[0], g);
+  const double* ut = inflow ? uf : ui;
+  double utn = inflow ? ufn : uin;
+  double rho = pow(c * c / (g * s), 1.0 / (g - 1.0));
+  double p = rho * c * c / g, q2 = 0.0;
+  Wb[0] = rho;
+  for (int d = 0; d < dim; ++d) {
+    double u = ut[d] - utn * n[d] + un * n[d];
+    Wb[1 + d] = rho * u;
+    q2 += u * u;
+  }
+  Wb[nv - 1] = p / (g - 1.0) + 0.5 * rho * q2;
+}
+
 static void ghost_mean(const OCfg* cfg, int dim, int tag, const double* n, const double* W, double* Wg) {
   int nv = dim + 2;
-  if (tag == 1) {
+  if (tag == 4) {
+    riemann_state(cfg, dim, n, W, Wg);
+  } else if (tag == 1) {
     double mn = 0; for (int d = 0; d < dim; ++d) mn += W[1 + d] * n[d];
     for (int v = 0; v < nv; ++v) Wg[v] = W[v];
     for (int d = 0; d < dim; ++d) Wg[1 + d] = W[1 + d] - 2.0 * mn * n[d];
+  } else if (tag == 3) {
+    /* no-slip adiabatic wall: the velocity reversed, density and energy kept */
+    for (int v = 0; v < nv; ++v) Wg[v] = W[v];
+    for (int d = 0; d < dim; ++d) Wg[1 + d] = -W[1 + d];
   } else if (is_inflow(cfg, dim, n)) {
     for (int v = 0; v < nv; ++v) Wg[v] = cfg->winf[v];
   } else {
@@ -828,8 +878,10 @@ static void ghost_mean(const OCfg* cfg, int dim, int tag, const double* n, const
 /* ghost gradient G[d][v] (global) */
 static void ghost_grad(const OCfg* cfg, int dim, int tag, const double* n, const double* G, double* Gg) {
   int nv = dim + 2;
-  if (tag == 1) {
-    /* reflection H = I - 2 n n^T: scalar fields get H grad; momentum H (dm/dx) H */
+  if (tag == 1 || tag == 3) {
+    /* the ghost field is the mirror image q(H x), H = I - 2 n n^T: scalar fields
+     * get H grad; the momentum is reflected at a slip wall, H (dm/dx) H, and
+     * reversed at a no-slip wall, -(dm/dx) H */
     double tmp[MAXD * MAXV];
     for (int v = 0; v < nv; ++v) {
       double s = 0; for (int d = 0; d < dim; ++d) s += n[d] * G[d * nv + v];
@@ -838,9 +890,10 @@ static void ghost_grad(const OCfg* cfg, int dim, int tag, const double* n, const
     for (int d = 0; d < dim; ++d) {
       double s = 0; for (int e = 0; e < dim; ++e) s += n[e] * tmp[d * nv + 1 + e];
       for (int v = 0; v < nv; ++v) Gg[d * nv + v] = tmp[d * nv + v];
-      for (int e = 0; e < dim; ++e) Gg[d * nv + 1 + e] = tmp[d * nv + 1 + e] - 2.0 * n[e] * s;
+      for (int e = 0; e < dim; ++e)
+        Gg[d * nv + 1 + e] = tag == 1 ? tmp[d * nv + 1 + e] - 2.0 * n[e] * s : -tmp[d * nv + 1 + e];
     }
-  } else if (is_inflow(cfg, dim, n)) {
+  } else if (tag == 4 || is_inflow(cfg, dim, n)) {
     for (int i = 0; i < dim * nv; ++i) Gg[i] = 0.0;
   } else {
     for (int i = 0; i < dim * nv; ++i) Gg[i] = G[i];
@@ -1143,7 +1196,7 @@ static void fine_residual(const OMesh* M, const OCfg* cfg, const double* W, cons
       rot_to(dim, Rm, Wr, wr);
       rot_grad(dim, Rm, Gl, gl);
       rot_grad(dim, Rm, Gr, gr);
-      gks_point(dim, cfg->gamma, cfg->tau_c1, cfg->tau_c2, wl, gl, wr, gr, dt, Floc, Wtl, NULL);
+      gks_point(dim, cfg->gamma, cfg->tau_c1, cfg->tau_c2, cfg->mu, wl, gl, wr, gr, dt, Floc, Wtl, NULL);
       rot_from(dim, Rm, Floc, Fg);
       rot_from(dim, Rm, Wtl, Wg);
       for (int v = 0; v < nv; ++v) { Fs[v] += wq * Fg[v]; Ws[v] += wq * Wg[v]; }
@@ -1409,7 +1462,7 @@ void om_gks_point(int dim, const double* cfgv, const double* Wl, const double* d
                   const double* dWr, double dt, double* F, double* Wt, double* dbg /* 2*15+5+15+5+1+5 */) {
   OCfg cfg; cfg_from(cfgv, dim + 2, &cfg);
   GksDebug d;
-  gks_point(dim, cfg.gamma, cfg.tau_c1, cfg.tau_c2, Wl, dWl, Wr, dWr, dt, F, Wt, &d);
+  gks_point(dim, cfg.gamma, cfg.tau_c1, cfg.tau_c2, cfg.mu, Wl, dWl, Wr, dWr, dt, F, Wt, &d);
   if (dbg) {
     int o = 0;
     for (int a = 0; a < MAXD; ++a) for (int i = 0; i < MAXV; ++i) dbg[o++] = d.al[a][i];
@@ -1554,6 +1607,11 @@ int om_vcycle(void* h, const double* cfgv, double* W, double* G, double* alpha, 
     if (l > 0) { free(Wl[l]); free(Wl0[l]); free(al[l]); free(Rs[l]); free(Pl[l]); }
   }
   return 0;
+}
+/* ghost state of a boundary face (tag, outward unit normal n) for the interior W */
+void om_ghost_state(int dim, const double* cfgv, int tag, const double* n, const double* W, double* Wg) {
+  OCfg cfg; cfg_from(cfgv, dim + 2, &cfg);
+  ghost_mean(&cfg, dim, tag, n, W, Wg);
 }
 /* DF-limited injection prolongation from level lev+1 into level lev */
 void om_prolong(void* h, int lev, const double* cfgv, double* Wf, const double* af, const double* Wc, const double* Wc0) {

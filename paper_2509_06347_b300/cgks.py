@@ -19,7 +19,7 @@ CGKS_OK = 0
 ERRORS = {-1: "CGKS_ERR_ARG", -2: "CGKS_ERR_MESH", -3: "CGKS_ERR_CUDA", -4: "CGKS_ERR_DIVERGED",
           -5: "CGKS_ERR_NONPOSITIVE", -6: "CGKS_ERR_TIMEOUT", -7: "CGKS_ERR_STATE"}
 PLAIN_FP64, MIXED, LEARNED = 0, 1, 2
-TAG_WALL, TAG_FARFIELD = 1, 2
+TAG_WALL, TAG_FARFIELD, TAG_NOSLIP_WALL, TAG_FARFIELD_RIEMANN = 1, 2, 3, 4
 
 # every entry point declared in include/cgks.h
 EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_error", "cgks_upload_mesh",
@@ -48,7 +48,7 @@ class Config(C.Structure):
                 ("diverge_factor", C.c_double), ("fine_smoother", C.c_int), ("df_relax", C.c_int),
                 ("df_prolong", C.c_int), ("df_gate", C.c_double), ("learned_judge_every", C.c_int),
                 ("learned_max_error", C.c_double), ("flux_precision", C.c_int),
-                ("relax_beta", C.c_double)]
+                ("relax_beta", C.c_double), ("mu", C.c_double)]
 
 
 _lib = None

@@ -196,7 +196,7 @@ MeshDev& get_mesh(cgks_t* h, int id) {
   return *it->second;
 }
 
-PhysParams phys(const cgks_config& c, int dim) { return make_phys(c.gamma, dim, c.tau_c1, c.tau_c2); }
+PhysParams phys(const cgks_config& c, int dim) { return make_phys(c.gamma, dim, c.tau_c1, c.tau_c2, c.mu); }
 
 // Block size for a launch over n items: the (tuned) size b, halved down to one
 // warp while the grid would give fewer than two blocks per SM, so that the
@@ -742,6 +742,7 @@ int cgks_default_config(cgks_config* c) {
   c->learned_max_error = 0.5;
   c->flux_precision = 0;
   c->relax_beta = 0.5;
+  c->mu = 0.0;
   return CGKS_OK;
 }
 
@@ -758,7 +759,7 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
       h->cfg.check_every < 1 || (h->cfg.fine_smoother != 0 && h->cfg.fine_smoother != 1) ||
       (h->cfg.flux_precision != 0 && h->cfg.flux_precision != 1) ||
       (h->cfg.df_relax < 0 || h->cfg.df_relax > 2) || (h->cfg.df_prolong != 0 && h->cfg.df_prolong != 1) ||
-      !(h->cfg.relax_beta >= 0.0 && h->cfg.relax_beta <= 1.0)) {
+      !(h->cfg.relax_beta >= 0.0 && h->cfg.relax_beta <= 1.0) || !(h->cfg.mu >= 0.0 && h->cfg.mu < 1e300)) {
     delete h;
     return CGKS_ERR_ARG;
   }
@@ -808,7 +809,7 @@ int cgks_upload_mesh(cgks_t* h, int mesh_id, int dim, int64_t n_cells, const int
         (n_bfaces > 0 && (!bface_nodes || !bface_tag)) || n_cells >= (1ll << 30))
       throw ArgError("invalid mesh arguments");
     for (int64_t b = 0; b < n_bfaces; ++b)
-      if (bface_tag[b] != CGKS_TAG_WALL && bface_tag[b] != CGKS_TAG_FARFIELD) throw ArgError("unknown boundary tag");
+      if (bface_tag[b] < CGKS_TAG_WALL || bface_tag[b] > CGKS_TAG_FARFIELD_RIEMANN) throw ArgError("unknown boundary tag");
     auto M = std::make_unique<MeshDev>();
     M->dim = dim;
     M->nv = dim + 2;
@@ -1937,7 +1938,7 @@ __global__ void __launch_bounds__(kBlock) k_noalloc_face(FaceSet Fs, const int* 
 #pragma unroll
     for (int v = 0; v < NV; ++v) WR[v] = W_orig[(size_t)iperm[R] * NV + v];
   } else {
-    ghost_state<DIM>(Fs.ftag[f], winf + NV * (Fs.grp ? Fs.grp[L] : 0), n, WL, WR);
+    ghost_state<DIM>(Fs.ftag[f], winf + NV * (Fs.grp ? Fs.grp[L] : 0), n, WL, WR, P.gamma);
   }
   const Frame<DIM> fr = make_frame<DIM>(n);
   double wl[NV], wr[NV], Fl[NV], Fg[NV];

@@ -26,6 +26,7 @@ using ::erfc;
 using ::exp;
 using ::fabs;
 using ::sqrt;
+using ::pow;
 
 struct dword {
   float hi, lo;
@@ -129,6 +130,9 @@ __device__ __forceinline__ dword fabs(dword x) { return (x.hi < 0.0f || (x.hi ==
 __device__ __forceinline__ dword sqrt(dword x) { return dw::sqrt(x); }
 __device__ __forceinline__ dword to_dword(double x) { return dword(x); }
 __device__ __forceinline__ dword exp(dword x) { return dword(::exp(static_cast<double>(x))); }
+__device__ __forceinline__ dword pow(dword x, dword y) {
+  return dword(::pow(static_cast<double>(x), static_cast<double>(y)));
+}
 __device__ __forceinline__ dword erfc(dword x) { return dword(::erfc(static_cast<double>(x))); }
 
 // scalar-generic helpers used by the templated flux code

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
 #pragma unroll
         for (int d = 0; d < DIM; ++d) g0[v][d] = Gr[((size_t)c * NV + v) * DIM + d];
       const double* wi = winf + NV * (M.grp ? M.grp[c] : 0);
-      ghost_state<DIM>(tag, wi, nrm[m], W0, Qm[m]);
+      ghost_state<DIM>(tag, wi, nrm[m], W0, Qm[m], gamma);
       ghost_grad<DIM>(tag, wi, nrm[m], g0, Dm[m]);
     }
   }
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(De
       S wi[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) wi[v] = S(wd[v]);
-      ghost_state<DIM, S>(tag, wi, n, Wl, Wr);
+      ghost_state<DIM, S>(tag, wi, n, Wl, Wr, P.gamma);
       ghost_grad<DIM, S>(tag, wi, n, gl, gr);
     }
     S wl[NV], wr[NV], Gl[DIM][NV], Gr[DIM][NV], Fl[NV], Wt[NV];
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(De
 #pragma unroll
       for (int v = 0; v < NV; ++v) WR[v] = Wc[(size_t)R * NV + v];
     } else {
-      ghost_state<DIM>(M.ftag[f], winf + NV * (M.grp ? M.grp[L] : 0), n, WL, WR);
+      ghost_state<DIM>(M.ftag[f], winf + NV * (M.grp ? M.grp[L] : 0), n, WL, WR, gamma);
     }
     rface[f] = spectral_radius<DIM, double>(gamma, WL, WR, n);
   }
@@ -853,7 +853,7 @@ __global__ void __launch_bounds__(kBlock) k_face_kfvs(FaceSet Fs, const double* 
 #pragma unroll
     for (int v = 0; v < NV; ++v) WR[v] = W[(size_t)R * NV + v];
   } else {
-    ghost_state<DIM>(Fs.ftag[f], winf + NV * (Fs.grp ? Fs.grp[L] : 0), n, WL, WR);
+    ghost_state<DIM>(Fs.ftag[f], winf + NV * (Fs.grp ? Fs.grp[L] : 0), n, WL, WR, P.gamma);
   }
   if (Fout) {
     const Frame<DIM> fr = make_frame<DIM>(n);
@@ -1096,7 +1096,7 @@ __global__ void __launch_bounds__(kBlock) k_features2(DevFine M, const double* _
       const double sd = M.cside[(size_t)c * 3 + m];
       double n[2] = {sd * M.fn[(size_t)f * 2], sd * M.fn[(size_t)f * 2 + 1]};
       double Wg[4], gg[4][2];
-      ghost_state<2>(M.ftag[f], wi, n, Wc, Wg);
+      ghost_state<2>(M.ftag[f], wi, n, Wc, Wg, gamma);
       ghost_grad<2>(M.ftag[f], wi, n, gc, gg);
       cell_features(Wg, gg, 0.0, nullptr, alpha[c], hc, sc, o);
     }

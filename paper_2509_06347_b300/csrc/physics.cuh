@@ -31,14 +31,16 @@ struct PhysT {
   S gamma;   // ratio of specific heats
   S K;       // internal degrees of freedom
   S c1, c2;  // collision-time coefficients
+  S mu;      // dynamic viscosity (Navier-Stokes, tau = mu / p); 0 for the Euler equations
   // derived on the host: N = K + dim, 2/N, 4/N
   S N, twoOverN, fourOverN;
 };
 using PhysParams = PhysT<double>;
 
-inline PhysParams make_phys(double gamma, int dim, double c1, double c2) {
+inline PhysParams make_phys(double gamma, int dim, double c1, double c2, double mu = 0.0) {
   PhysParams p;
   p.gamma = gamma;
+  p.mu = mu;
   p.K = dim == 2 ? (4.0 - 2.0 * gamma) / (gamma - 1.0) : (5.0 - 3.0 * gamma) / (gamma - 1.0);
   p.c1 = c1;
   p.c2 = c2;
@@ -52,6 +54,7 @@ inline PhysT<dword> phys_dword(const PhysParams& p) {
   PhysT<dword> q;
   q.gamma = dword(p.gamma);
   q.K = dword(p.K);
+  q.mu = dword(p.mu);
   q.c1 = dword(p.c1);
   q.c2 = dword(p.c2);
   q.N = dword(p.N);
@@ -507,13 +510,17 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
   psi_mom<DIM, 0, 0, 0>(mr, t);
 #pragma unroll
   for (int i = 0; i < NV; ++i) Wc[i] = pl.rho * Wc[i] + pr.rho * t[i];
+  // pressure of the interface equilibrium
+  S pwc;
   {
-    // vacuum (both sides moving apart): no admissible interface equilibrium;
-    // take the collisionless limit, i.e. the KFVS flux, point value W^c
     S kc = S(0.0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) kc += Wc[1 + d] * Wc[1 + d];
-    const S pwc = (P.gamma - S(1.0)) * (Wc[DIM + 1] - S(0.5) * kc / Wc[0]);
+    pwc = (P.gamma - S(1.0)) * (Wc[DIM + 1] - S(0.5) * kc / Wc[0]);
+  }
+  {
+    // vacuum (both sides moving apart): no admissible interface equilibrium;
+    // take the collisionless limit, i.e. the KFVS flux, point value W^c
     const S pwl = pl.rho * pl.h, pwr = pr.rho * pr.h;  // p = rho / (2 lambda)
     if (!(Wc[0] > S(1e-10) * (pl.rho + pr.rho)) || !(pwc > S(1e-10) * (pwl + pwr))) {
       S a[NV], b[NV];
@@ -589,7 +596,9 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
   (void)Ac;
   // collision time and time integrals
   const S pL = pl.rho * pl.h, pR = pr.rho * pr.h;
-  const S tau = P.c1 * dt + P.c2 * fabs(pL - pR) / (pL + pR) * dt;
+  // Euler: tau = C1 dt + C2 |dp| / (pl + pr) dt; Navier-Stokes (Sec 2.1): the
+  // physical mu / p of the interface equilibrium in place of C1 dt
+  const S tau = (P.mu > S(0.0) ? P.mu / pwc : P.c1 * dt) + P.c2 * fabs(pL - pR) / (pL + pR) * dt;
   const S e = exp_neg(-dt / tau);
   const S T1 = dt - tau * (S(1.0) - e);
   const S T2 = -tau * dt + S(2.0) * tau * tau - tau * (dt + S(2.0) * tau) * e;
@@ -797,7 +806,7 @@ __device__ __forceinline__ T spectral_radius(T gamma, const T* Wa, const T* Wb, 
 
 // ---------------------------------------------------------------------------
 // boundary ghosts, global frame
-enum : int { kTagWall = 1, kTagFarfield = 2 };
+enum : int { kTagWall = 1, kTagFarfield = 2, kTagNoSlipWall = 3, kTagFarfieldRiemann = 4 };
 
 template <int DIM, typename S = double>
 __device__ __forceinline__ bool inflow(const S* winf, const S* n) {
@@ -806,10 +815,64 @@ __device__ __forceinline__ bool inflow(const S* winf, const S* n) {
   for (int d = 0; d < DIM; ++d) un += winf[1 + d] * n[d];
   return un < S(0.0);
 }
+// Far-field state from the Riemann invariants along the outward normal n:
+// R+ = u_n + 2c/(gamma-1) from the interior, R- = u_n - 2c/(gamma-1) from the
+// free stream (each the invariant carried into the face by its characteristic);
+// their sum and difference give u_n and c on the face, and the tangential
+// velocity and the entropy p/rho^gamma come from upstream (the free stream on
+// inflow, the interior on outflow).  Supersonic faces take the upwind state.
 template <int DIM, typename S = double>
-__device__ __forceinline__ void ghost_state(int tag, const S* winf, const S* n, const S* W, S* Wg) {
+__device__ __forceinline__ void riemann_farfield(S gamma, const S* winf, const S* n, const S* W, S* Wb) {
   constexpr int NV = DIM + 2;
-  if (tag == kTagWall) {
+  const S gm1 = gamma - S(1.0);
+  const S ri = S(1.0) / W[0], rf = S(1.0) / winf[0];
+  S uni = S(0.0), unf = S(0.0), qi = S(0.0), qf = S(0.0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    uni += W[1 + d] * n[d];
+    unf += winf[1 + d] * n[d];
+    qi += W[1 + d] * W[1 + d];
+    qf += winf[1 + d] * winf[1 + d];
+  }
+  uni *= ri;
+  unf *= rf;
+  const S pi = gm1 * (W[NV - 1] - S(0.5) * qi * ri), pf = gm1 * (winf[NV - 1] - S(0.5) * qf * rf);
+  const S ci = sqrt(gamma * pi * ri), cf = sqrt(gamma * pf * rf);
+  if (!(fabs(unf) < cf)) {  // supersonic normal flow
+    const S* src = unf < S(0.0) ? winf : W;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Wb[i] = src[i];
+    return;
+  }
+  const S rp = uni + S(2.0) * ci / gm1, rm = unf - S(2.0) * cf / gm1;
+  const S un = S(0.5) * (rp + rm), cb = S(0.25) * gm1 * (rp - rm);
+  const bool in = un < S(0.0);
+  const S* up = in ? winf : W;
+  const S ir = in ? rf : ri;
+  const S ent = (in ? pf : pi) / pow(up[0], gamma);  // p / rho^gamma upstream
+  const S rho = pow(cb * cb / (gamma * ent), S(1.0) / gm1);
+  const S p = rho * cb * cb / gamma;
+  S upn = S(0.0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) upn += up[1 + d] * n[d];
+  upn *= ir;
+  S q = S(0.0);
+  Wb[0] = rho;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const S u = up[1 + d] * ir + (un - upn) * n[d];  // upstream tangential part, face normal part
+    Wb[1 + d] = rho * u;
+    q += u * u;
+  }
+  Wb[NV - 1] = p / gm1 + S(0.5) * rho * q;
+}
+
+template <int DIM, typename S = double>
+__device__ __forceinline__ void ghost_state(int tag, const S* winf, const S* n, const S* W, S* Wg, S gamma) {
+  constexpr int NV = DIM + 2;
+  if (tag == kTagFarfieldRiemann) {
+    riemann_farfield<DIM, S>(gamma, winf, n, W, Wg);
+  } else if (tag == kTagWall) {
     S mn = S(0.0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) mn += W[1 + d] * n[d];
@@ -817,6 +880,12 @@ __device__ __forceinline__ void ghost_state(int tag, const S* winf, const S* n, 
     for (int i = 0; i < NV; ++i) Wg[i] = W[i];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) Wg[1 + d] = W[1 + d] - S(2.0) * mn * n[d];
+  } else if (tag == kTagNoSlipWall) {
+    // no-slip adiabatic wall: every velocity component reversed, density and energy kept
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Wg[i] = W[i];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) Wg[1 + d] = -W[1 + d];
   } else if (inflow<DIM, S>(winf, n)) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) Wg[i] = winf[i];
@@ -830,8 +899,9 @@ template <int DIM, typename S = double>
 __device__ __forceinline__ void ghost_grad(int tag, const S* winf, const S* n, const S (*g)[DIM],
                                            S (*gg)[DIM]) {
   constexpr int NV = DIM + 2;
-  if (tag == kTagWall) {
-    // scalars: (I - 2nn^T) grad;  momentum: (I - 2nn^T) (dm/dx) (I - 2nn^T)
+  if (tag == kTagWall || tag == kTagNoSlipWall) {
+    // mirror image q(H x), H = I - 2nn^T: scalars H grad;  momentum: slip
+    // H (dm/dx) H (reflected), no-slip -(dm/dx) H (reversed)
     S t[NV][DIM];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -841,19 +911,26 @@ __device__ __forceinline__ void ghost_grad(int tag, const S* winf, const S* n, c
 #pragma unroll
       for (int d = 0; d < DIM; ++d) t[v][d] = g[v][d] - S(2.0) * s * n[d];
     }
+    if (tag == kTagWall) {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      S s = S(0.0);
+      for (int d = 0; d < DIM; ++d) {
+        S s = S(0.0);
 #pragma unroll
-      for (int e = 0; e < DIM; ++e) s += n[e] * t[1 + e][d];
+        for (int e = 0; e < DIM; ++e) s += n[e] * t[1 + e][d];
 #pragma unroll
-      for (int e = 0; e < DIM; ++e) t[1 + e][d] -= S(2.0) * n[e] * s;
+        for (int e = 0; e < DIM; ++e) t[1 + e][d] -= S(2.0) * n[e] * s;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < DIM; ++e)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) t[1 + e][d] = -t[1 + e][d];
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int d = 0; d < DIM; ++d) gg[v][d] = t[v][d];
-  } else if (inflow<DIM, S>(winf, n)) {
+  } else if (tag == kTagFarfieldRiemann || inflow<DIM, S>(winf, n)) {
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll

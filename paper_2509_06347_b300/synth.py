@@ -28,6 +28,8 @@ import numpy as np
 
 TAG_WALL = 1
 TAG_FARFIELD = 2
+TAG_NOSLIP_WALL = 3
+TAG_FARFIELD_RIEMANN = 4
 DEFAULT_SEED = 2509063470
 
 _M64 = (1 << 64) - 1
