@@ -37,19 +37,21 @@ WORKLOAD = "cylinder_mach5_65536tri_3level"
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 # Roofline work unit of the gas-kinetic flux kernel k_flux<dim,1> (flux and
 # point values): FP64 flops per Gauss point of its direct formulation, one
-# moment product per slope vector, as ncu counted them on this workload
-# ((2 x DFMA + DADD + DMUL) / Gauss points).  The current kernel expands the
-# distribution polynomial once per side and executes fewer (second figures,
-# same ncu counters); achieved = unit x Gauss points / event time.
+# moment product per slope vector and library exp/erfc, as ncu counted them on
+# this workload ((2 x DFMA + DADD + DMUL) / Gauss points).  The unit is kept
+# fixed so that frac follows the time per Gauss point; the current kernel
+# (grouped moments, closed-form equilibrium terms, table-driven exp and erfc)
+# executes fewer (second figures, same ncu counters); achieved = unit x Gauss
+# points / event time.
 FLUX_FLOP_PER_GP_2D = 2947.1
-FLUX_EXEC_FLOP_PER_GP_2D = 2631.1
+FLUX_EXEC_FLOP_PER_GP_2D = 2139.4
 FLUX_FLOP_PER_GP_3D = 5301.1
-FLUX_EXEC_FLOP_PER_GP_3D = 4670.4
+FLUX_EXEC_FLOP_PER_GP_3D = 3769.7
 # DRAM bytes (read + write) of one k_flux<2,1> launch on this workload, and per
 # face of k_flux<3,1> on the 16 x 16 x 16 sphere shell (297,984 faces), scaled
 # to the full shell by its number of faces; ncu, cold-cache replay.
-FLUX_DRAM_BYTES_PER_LAUNCH = 24812800
-FLUX_DRAM_BYTES_PER_FACE_3D = 510.1
+FLUX_DRAM_BYTES_PER_LAUNCH = 24812032
+FLUX_DRAM_BYTES_PER_FACE_3D = 470.7
 
 
 def parse():
