@@ -68,7 +68,8 @@ typedef struct cgks_config {
   double gamma;           /* ratio of specific heats (1.4) */
   double cfl_imp;         /* CFL of the implicit (DF-weighted) part, Sec 4.3 (10) */
   double cfl_exp;         /* CFL of the explicit part and of the flux time step (0.5) */
-  double tau_c1, tau_c2;  /* numerical collision time tau = c1 dt + c2 |dp|/(pl+pr) dt (0.01, 1) */
+  double tau_c1, tau_c2;  /* numerical collision time tau = c1 dt + c2 |dp|/(pl+pr) dt (0.01, 1);
+                             with mu > 0 the c1 dt term gives way to mu / p */
   double weno_gamma_high; /* linear weight of the large HWENO stencil (0.95) */
   double weno_eps;        /* WENO epsilon (1e-15) */
   double r_safety;        /* spectral-radius factor of the LU-SGS splitting (1) */
@@ -254,7 +255,8 @@ int cgks_counters(cgks_t* h, int mesh_id, uint64_t* out);
 /* Point evaluations for parity checks, device pointers, local frame (normal
  * = first velocity component): Wl, Wr [n][nv]; Gl, Gr [n][dim][nv] derivatives
  * along (n, t1, t2); dt [n].  Outputs F (time-averaged flux), Wt (point value
- * at t = dt) [n][nv] and the DF point factor alpha [n]. */
+ * at t = dt) [n][nv] and the DF point factor alpha [n].  The collision time
+ * follows the context's configuration (tau_c1, tau_c2, mu). */
 int cgks_gks_points(cgks_t* h, int dim, int64_t n, const double* Wl, const double* Gl, const double* Wr,
                     const double* Gr, const double* dt, double* F, double* Wt, double* alpha);
 /* First-order KFVS flux of constant states, device pointers [n][nv]. */
