@@ -185,6 +185,10 @@ struct cgks_ctx {
   std::string err;
   std::vector<std::unique_ptr<cgks::DBuf>> scratch;  // point-evaluation helpers
   int sms = 148;                                      // SM count of the device (set at creation)
+  // pinned host buffer for the small per-chunk reads of cgks_vcycle
+  double* pin = nullptr;
+  size_t pin_cap = 0;
+  cgks::DBuf pack;  // its device counterpart
 };
 
 namespace cgks {
@@ -787,6 +791,7 @@ int cgks_destroy(cgks_t* h) {
   cudaStreamSynchronize(h->stream);
   h->meshes.clear();
   h->scratch.clear();
+  if (h->pin) cudaFreeHost(h->pin);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
   return CGKS_OK;
@@ -1123,25 +1128,40 @@ int cgks_vcycle(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int 
     for (int k = 0; k < n_meshes; ++k) {
       MeshDev& M = get_mesh(h, mesh_ids[k]);
       require_ready(M, true);
-      const int nv = M.nv;
+      const int nv2 = 2 * M.nv;
       cudaGraphExec_t g = get_graph(h, M, mode);
-      int start = 0;
-      CK(cudaMemcpyAsync(&start, M.cycle, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaStreamSynchronize(h->stream));
-      std::vector<double> hist;
+      // one pinned read per chunk: the packed history (k_pack_hist) and the counters
+      const int cmax = std::max(1, std::min(h->cfg.check_every, n_cycles));
+      const size_t pack_n = 3 + (size_t)cmax * nv2;
+      const size_t pin_bytes = pack_n * sizeof(double) + sizeof(Counters);
+      if (h->pin_cap < pin_bytes) {
+        if (h->pin) CK(cudaFreeHost(h->pin));
+        h->pin = nullptr;
+        h->pin_cap = 0;
+        CK(cudaMallocHost(&h->pin, pin_bytes));
+        h->pin_cap = pin_bytes;
+      }
+      if (h->pack.bytes < pack_n * sizeof(double)) h->pack.alloc(pack_n * sizeof(double));
+      double* pk = h->pin;
+      Counters* pc = reinterpret_cast<Counters*>(h->pin + pack_n);
       int done = 0;
       bool stop = false;
       while (done < n_cycles && !stop) {
-        const int chunk = std::min(h->cfg.check_every, n_cycles - done);
+        const int chunk = std::min(cmax, n_cycles - done);
         for (int i = 0; i < chunk; ++i) CK(cudaGraphLaunch(g, h->stream));
-        done += chunk;
-        const int upto = std::min(start + done, M.max_hist);
-        hist.resize((size_t)upto * 2 * nv);
-        CK(cudaMemcpyAsync(hist.data(), M.hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        k_pack_hist<<<1, 256, 0, h->stream>>>(M.hist, M.cycle, M.max_hist, nv2, chunk, h->pack.as<double>());
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(pk, h->pack.p, (3 + (size_t)chunk * nv2) * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaMemcpyAsync(pc, M.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
-        if (upto > 0) {
-          const double first = hist[0];
-          const double last = hist[(size_t)(upto - 1) * 2 * nv];
+        if (norms_out)
+          for (int i = 0; i < chunk; ++i)
+            for (int j = 0; j < nv2; ++j)
+              norms_out[((size_t)k * n_cycles + done + i) * nv2 + j] = pk[3 + (size_t)i * nv2 + j];
+        done += chunk;
+        if (pk[0] > 0 && M.max_hist > 0) {
+          const double first = pk[1], last = pk[2];
           if (!std::isfinite(last) || (first > 0 && last > h->cfg.diverge_factor * first)) {
             status = CGKS_ERR_DIVERGED;
             stop = true;
@@ -1150,17 +1170,14 @@ int cgks_vcycle(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int 
           }
         }
       }
-      Counters c{};
-      CK(cudaMemcpy(&c, M.cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
-      if (c.nonfinite > 0) status = CGKS_ERR_DIVERGED;
-      if (norms_out) {
-        for (int i = 0; i < n_cycles; ++i)
-          for (int j = 0; j < 2 * nv; ++j) {
-            const int idx = start + i;
-            norms_out[((size_t)k * n_cycles + i) * 2 * nv + j] =
-                (i < done && idx < M.max_hist) ? hist[(size_t)idx * 2 * nv + j] : -1.0;
-          }
+      if (done == 0) {
+        CK(cudaMemcpyAsync(pc, M.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
       }
+      if (pc->nonfinite > 0) status = CGKS_ERR_DIVERGED;
+      if (norms_out)
+        for (int i = done; i < n_cycles; ++i)
+          for (int j = 0; j < nv2; ++j) norms_out[((size_t)k * n_cycles + i) * nv2 + j] = -1.0;
       if (cycles_done) cycles_done[k] = done;
     }
     if (status != CGKS_OK) h->err = "residual diverged or became non-finite";

@@ -686,6 +686,26 @@ __global__ void k_group_norm(const double* __restrict__ qcell, const int* __rest
 }
 __global__ void k_bump(int* __restrict__ cycle) { *cycle += 1; }
 
+// Packs what the host needs after a chunk of recorded V-cycles, so that one
+// small device-to-host copy serves the convergence test and the norms:
+// out[0] = cycles recorded so far, out[1] / out[2] = density RMS of the first
+// and of the latest recorded cycle, then the rows of the last `chunk` cycles
+// (nv2 values each; -1 where a row lies outside the history).
+__global__ void k_pack_hist(const double* __restrict__ hist, const int* __restrict__ cycle, int max_hist, int nv2,
+                            int chunk, double* __restrict__ out) {
+  const int k = *cycle;
+  const int upto = min(k, max_hist);
+  if (threadIdx.x == 0) {
+    out[0] = k;
+    out[1] = upto > 0 ? hist[0] : 0.0;
+    out[2] = upto > 0 ? hist[(size_t)(upto - 1) * nv2] : 0.0;
+  }
+  for (int t = threadIdx.x; t < chunk * nv2; t += blockDim.x) {
+    const int idx = k - chunk + t / nv2;
+    out[3 + t] = (idx >= 0 && idx < max_hist) ? hist[(size_t)idx * nv2 + t % nv2] : -1.0;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K4 / K5: multi-colour LU-SGS sweeps (Eqs. gpu-forward-relaxation and
 // gpu-backward-relaxation), one launch per colour over cells [lo, hi).
