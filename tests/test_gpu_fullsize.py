@@ -10,7 +10,8 @@ coarse KFVS residuals of sampled coarse cells against the oracle on their
 Whole V-cycles at full size are checked by a property that holds at any size:
 a uniform free stream stays unchanged, in FP64 and in MIXED.  The batched
 sweep (64 cylinders, 7.1M cells in one union mesh, a free stream per member)
-is checked on sampled cells of every kind of member."""
+is checked on sampled cells of every kind of member, and the Navier-Stokes
+configuration of the benchmark on every cell of the cylinder."""
 import numpy as np
 import pytest
 
@@ -238,3 +239,44 @@ def test_batch_fine_residual_sampled(lib):
         np.testing.assert_allclose(Gn[sg] * vol[:, None, None], ro["grad"][sp] * vol[:, None, None], rtol=0,
                                    atol=1e-12 * np.max(np.abs(W[cells])) * Smax)
         np.testing.assert_allclose(al[sg], ro["alpha"][sp], rtol=1e-12, atol=1e-14)
+
+
+def test_navier_stokes_full_cylinder(lib):
+    """The viscous benchmark configuration at full size (65,536 cells, Mach
+    0.15, Re 40, no-slip adiabatic wall, characteristic far field): the
+    residual, slopes and DF factors of every cell and two plain-FP64 V-cycles
+    against the oracle."""
+    m = dict(synth.cylinder_mesh(64, 32, 1.05, n_refine=2))
+    t = np.asarray(m["bface_tag"]).copy()
+    t[t == synth.TAG_WALL] = synth.TAG_NOSLIP_WALL
+    t[t == synth.TAG_FARFIELD] = synth.TAG_FARFIELD_RIEMANN
+    m["bface_tag"] = t
+    mach, mu = 0.15, 0.15 * 2.0 / 40.0
+    w = synth.freestream(mach)
+    W, G = smooth_physical_state(np.random.default_rng(7), m, w)
+    n, nv, dim = len(W), 4, 2
+    ctx = lib.Context(mu=mu)
+    try:
+        ctx.setup(1, m, w, W, G)
+        R, Gn, al = np.zeros((n, nv)), np.zeros((n, nv, dim)), np.zeros(n)
+        ctx.cgks_residual(1, 0, None, R, Gn, al)
+        ncyc = 2
+        norms = np.zeros((ncyc, nv, 2))
+        ctx.cgks_vcycle([1], ncyc, 0, norms)
+        Wd = np.zeros_like(W)
+        ctx.cgks_get_state(1, Wd)
+    finally:
+        ctx.close()
+    cfg = oracle.cfg_vector(dim, winf=w, mu=mu)
+    om = oracle.OracleMesh(m)
+    ro = om.residual(cfg, W, G, np.ones(n))
+    Fs = flux_scale(W, dim)
+    Smax = float(np.max(om.faces(0)["S"]))
+    np.testing.assert_allclose(R, ro["R"], rtol=0, atol=1e-12 * Fs * Smax)
+    vol = om.cells(0)[0]
+    np.testing.assert_allclose(Gn * vol[:, None, None], ro["grad"] * vol[:, None, None], rtol=0,
+                               atol=1e-12 * np.max(np.abs(W)) * Smax)
+    np.testing.assert_allclose(al, ro["alpha"], rtol=1e-12, atol=1e-14)
+    out = om.vcycle(cfg, W, G, np.ones(n), ncyc)
+    np.testing.assert_allclose(norms, out["norms"], rtol=1e-8)
+    np.testing.assert_allclose(Wd, out["W"], rtol=0, atol=1e-9 * np.max(np.abs(W)))
