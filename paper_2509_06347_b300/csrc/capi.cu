@@ -410,9 +410,10 @@ void launch_flux(cgks_t* h, MeshDev& M, bool point = true, bool radius = true) {
 
 // fine residual: slopes_update -> G <- alpha * grad_new; want_diag -> LU-SGS D;
 // want_norm -> norm partials + final (hist when record)
-template <int DIM>
+// TS: precision of a fused forward LU-SGS step of colour 0 (fuse_c0), as in sweeps<DIM, TS>
+template <int DIM, typename TS = double>
 void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bool want_norm, bool record,
-                   double* alpha_out_dev, double* gradnew_dev) {
+                   double* alpha_out_dev, double* gradnew_dev, bool fuse_c0 = false) {
   LevelDev& L = M.lev[0];
   launch_recon<DIM>(h, M);
   // the time-evolved point values only feed the slopes, the spectral radii only the LU-SGS diagonal
@@ -420,12 +421,16 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
   const bool grouped = !M.lgrp.empty();
   // norm partials need whole blocks of kBlock threads
   const int gb = (want_norm && !grouped) ? kBlock : M.blk[B_GATHER];
-  k_gather<DIM><<<blocks_for(L.n, gb), gb, 0, h->stream>>>(
+  const bool fuse = fuse_c0 && want_diag;
+  TS* dWs0 = fuse ? (sizeof(TS) == 8 ? (TS*)L.dWs64 : (TS*)L.dWs32) : nullptr;
+  TS* dW0 = fuse && L.n_colors == 1 ? (sizeof(TS) == 8 ? (TS*)L.dW64 : (TS*)L.dW32) : nullptr;
+  k_gather<DIM, TS><<<blocks_for(L.n, gb), gb, 0, h->stream>>>(
       M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R,
       slopes_update ? M.G : nullptr, alpha_out_dev ? alpha_out_dev : L.alpha, want_diag ? L.D : nullptr,
       gradnew_dev, (want_norm && !grouped) ? M.norm_part : nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg),
       L.rface,
-      (want_norm && grouped) ? M.qcell : nullptr, (grouped && !alpha_out_dev) ? M.active : nullptr);
+      (want_norm && grouped) ? M.qcell : nullptr, (grouped && !alpha_out_dev) ? M.active : nullptr, dWs0, dW0,
+      L.color_off[1]);
   if (want_norm && !grouped)
     k_norm_final<DIM + 2><<<1, kBlock, 0, h->stream>>>(M.norm_part, M.norm_blocks, L.n, record ? M.hist : nullptr,
                                                        record ? M.cycle : nullptr, M.max_hist, M.last_norm);
@@ -436,13 +441,15 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
   }
 }
 
+// c0_done: the forward step of colour 0 already ran inside the kernel that
+// built R and D (fine_residual / coarse_prep with fuse_c0)
 template <int DIM, typename T>
-void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
+void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool c0_done = false) {
   const double* alpha = h->cfg.df_relax == 1 ? L.alpha : L.relax;
   T* dWs = sizeof(T) == 8 ? (T*)L.dWs64 : (T*)L.dWs32;
   T* dW = sizeof(T) == 8 ? (T*)L.dW64 : (T*)L.dW32;
   const int nc = L.n_colors;
-  for (int c = 0; c < nc - 1; ++c) {
+  for (int c = c0_done ? 1 : 0; c < nc - 1; ++c) {
     const int lo = L.color_off[c], hi = L.color_off[c + 1];
     if (hi > lo)
     {
@@ -451,7 +458,7 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
                                                                      L.rface, h->cfg.gamma, dWs, dW);
     }
   }
-  {
+  if (!(c0_done && nc == 1)) {
     const int lo = L.color_off[nc - 1], hi = L.color_off[nc];
     if (hi > lo)
     {
@@ -476,15 +483,19 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf) {
       L.n, h->cfg.gamma, L.W, dW, M.cnt, masked ? M.lgrp[0] : nullptr, masked ? M.active : nullptr);
 }
 
-template <int DIM>
-void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag) {
+// TS / fuse_c0: as in fine_residual
+template <int DIM, typename TS = double>
+void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag, bool fuse_c0 = false) {
   const PhysParams p = phys(h->cfg, DIM);
   const int bf = fit_block(h, L.faces.nf, M.blk[B_FACE]), bc = fit_block(h, L.n, M.blk[B_CELL]);
   k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(
       L.faces, L.W, M.winf, p, L.Fc, want_diag ? L.rface : nullptr);
-  k_coarse_cell<DIM><<<blocks_for(L.n, bc), bc, 0, h->stream>>>(
+  const bool fuse = fuse_c0 && want_diag;
+  TS* dWs0 = fuse ? (sizeof(TS) == 8 ? (TS*)L.dWs64 : (TS*)L.dWs32) : nullptr;
+  TS* dW0 = fuse && L.n_colors == 1 ? (sizeof(TS) == 8 ? (TS*)L.dW64 : (TS*)L.dW32) : nullptr;
+  k_coarse_cell<DIM, TS><<<blocks_for(L.n, bc), bc, 0, h->stream>>>(
       L.topo, L.W, L.Fc, L.rface, Pf, nullptr, h->cfg.df_relax == 1 ? L.alpha : L.relax, h->cfg.gamma, h->cfg.cfl_exp,
-      h->cfg.cfl_imp, L.R, want_diag ? L.D : nullptr);
+      h->cfg.cfl_imp, L.R, want_diag ? L.D : nullptr, dWs0, dW0, L.color_off[1]);
 }
 
 // FAS forcing P = R* - R(W0) on a coarse level
@@ -493,24 +504,26 @@ void coarse_forcing(cgks_t* h, MeshDev& M, LevelDev& L) {
   const PhysParams p = phys(h->cfg, DIM);
   const int bf = fit_block(h, L.faces.nf, M.blk[B_FACE]), bc = fit_block(h, L.n, M.blk[B_CELL]);
   k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, nullptr);
-  k_coarse_cell<DIM><<<blocks_for(L.n, bc), bc, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr,
-                                                                                        nullptr, L.Rstar,
-                                                                    L.alpha, h->cfg.gamma, 0.0, 0.0, L.P, nullptr);
+  k_coarse_cell<DIM, double><<<blocks_for(L.n, bc), bc, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, L.Rstar,
+                                                                 L.alpha, h->cfg.gamma, 0.0, 0.0, L.P, nullptr,
+                                                                 nullptr, nullptr, 0);
 }
 
 // steps 1-3 of the V-cycle: residual + slope update, fine smoothing, residual
 template <int DIM, typename T>
 void vcycle_pre(cgks_t* h, MeshDev& M) {
   LevelDev& L0 = M.lev[0];
-  // 1. residual, norms, slope update with DF, LU-SGS diagonal
-  fine_residual<DIM>(h, M, true, true, true, true, nullptr, nullptr);
+  // 1. residual, norms, slope update with DF, LU-SGS diagonal (and the
+  //    forward LU-SGS step of colour 0, fused into the same kernel)
+  const bool lusgs = h->cfg.fine_smoother != 1;
+  fine_residual<DIM, T>(h, M, true, true, true, true, nullptr, nullptr, lusgs);
   // 2. pre-smoothing: one DF-relaxed LU-SGS step on -R, or the explicit update
-  if (h->cfg.fine_smoother == 1)
+  if (!lusgs)
     k_explicit<DIM><<<blocks_for(L0.n), kBlock, 0, h->stream>>>(
         L0.n, h->cfg.gamma, L0.R, L0.dte, L0.vol, L0.W, M.cnt, M.lgrp.empty() ? nullptr : M.lgrp[0],
         M.lgrp.empty() ? nullptr : M.active);
   else
-    sweeps<DIM, T>(h, M, L0, nullptr);
+    sweeps<DIM, T>(h, M, L0, nullptr, true);
   if (M.nlev == 1) return;
   // 3. residual at the smoothed state (no slope update); its DF is kept
   fine_residual<DIM>(h, M, false, false, false, false, nullptr, nullptr);
@@ -528,8 +541,8 @@ void vcycle_coarse(cgks_t* h, MeshDev& M) {
                                                                 F.R, C.W0, C.W, C.alpha, C.Rstar);
     coarse_forcing<DIM>(h, M, C);
     for (int s = 0; s < h->cfg.n_sweep_coarse; ++s) {
-      coarse_prep<DIM>(h, M, C, C.P, true);
-      sweeps<DIM, T>(h, M, C, nullptr);
+      coarse_prep<DIM, T>(h, M, C, C.P, true, true);
+      sweeps<DIM, T>(h, M, C, nullptr, true);
     }
     if (l + 1 < M.nlev) coarse_prep<DIM>(h, M, C, C.P, false);  // R~ = R(W) + P to restrict
   }
@@ -1006,10 +1019,10 @@ int cgks_residual(cgks_t* h, int mesh_id, int level, const double* W_in, double*
     // R(W) of the level's faces with zero forcing
     if (M.dim == 2) {
       k_face_kfvs<2><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, nullptr);
-      k_coarse_cell<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, nullptr, L.alpha, h->cfg.gamma, 0.0, 0.0, L.Rstar, nullptr);
+      k_coarse_cell<2, double><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, nullptr, L.alpha, h->cfg.gamma, 0.0, 0.0, L.Rstar, nullptr, nullptr, nullptr, 0);
     } else {
       k_face_kfvs<3><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, nullptr);
-      k_coarse_cell<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, nullptr, L.alpha, h->cfg.gamma, 0.0, 0.0, L.Rstar, nullptr);
+      k_coarse_cell<3, double><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, nullptr, L.alpha, h->cfg.gamma, 0.0, 0.0, L.Rstar, nullptr, nullptr, nullptr, 0);
     }
     CK(cudaGetLastError());
     if (R_out) store_rows(h, M, L, M.nv, L.Rstar, on_device, R_out);
@@ -1504,7 +1517,7 @@ int cgks_autotune(cgks_t* h, int mesh_id, int* blocks_out) {
           k_face_kfvs<2><<<blocks_for(C.faces.nf, M.blk[B_FACE]), M.blk[B_FACE], 0, h->stream>>>(C.faces, C.W, M.winf, p, C.Fc, C.rface);
         });
         tune(B_CELL, [&] {
-          k_coarse_cell<2><<<blocks_for(C.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(C.topo, C.W, C.Fc, C.rface, nullptr, nullptr, C.alpha, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, C.R, C.D);
+          k_coarse_cell<2, double><<<blocks_for(C.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(C.topo, C.W, C.Fc, C.rface, nullptr, nullptr, C.alpha, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, C.R, C.D, nullptr, nullptr, 0);
         });
       }
     } else {
@@ -1520,7 +1533,7 @@ int cgks_autotune(cgks_t* h, int mesh_id, int* blocks_out) {
           k_face_kfvs<3><<<blocks_for(C.faces.nf, M.blk[B_FACE]), M.blk[B_FACE], 0, h->stream>>>(C.faces, C.W, M.winf, p, C.Fc, C.rface);
         });
         tune(B_CELL, [&] {
-          k_coarse_cell<3><<<blocks_for(C.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(C.topo, C.W, C.Fc, C.rface, nullptr, nullptr, C.alpha, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, C.R, C.D);
+          k_coarse_cell<3, double><<<blocks_for(C.n, M.blk[B_CELL]), M.blk[B_CELL], 0, h->stream>>>(C.topo, C.W, C.Fc, C.rface, nullptr, nullptr, C.alpha, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, C.R, C.D, nullptr, nullptr, 0);
         });
       }
     }

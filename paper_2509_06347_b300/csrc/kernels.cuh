@@ -515,10 +515,28 @@ __device__ __forceinline__ double lusgs_diag(const Topo& T, int c, const double*
   return alpha * (V / dti + 0.5 * sr) + (1.0 - alpha) * V / dte;
 }
 
+// The forward LU-SGS step of the first colour, fused into the kernel that
+// forms R~ and D: colour 0 has no lower-coloured neighbours, so its step is
+// dW* = -R~ / D, written exactly as k_sweep<MODE 0> would (and to dW as well
+// when colour 0 is the only colour, as k_sweep<MODE 2> would).
+template <int NV, typename T>
+__device__ __forceinline__ void colour0_forward(int c, const double* __restrict__ R, double alpha, double D,
+                                                T* __restrict__ dWs, T* __restrict__ dW) {
+  const T ha = (T)(0.5 * alpha);
+  const T iD = (T)(1.0 / D);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double rhs = -(R[(size_t)c * NV + v] + 0.0);
+    const T x = ((T)rhs - ha * (T)0) * iD;
+    dWs[(size_t)c * NV + v] = x;
+    if (dW) dW[(size_t)c * NV + v] = x;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K3: per-cell gather of residual, new slopes (Sec 2.4) and DF (Sec 3.3)
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, typename TS = double>
 __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const double* __restrict__ Fface,
                                                    const double* __restrict__ Wface, const double* __restrict__ aface,
                                                    const double* __restrict__ W, const double* __restrict__ winf,
@@ -528,7 +546,8 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
                                                    double* __restrict__ Dg, double* __restrict__ gradnew_out,
                                                    double* __restrict__ norm_part, double relax_fixed,
                                                    const double* __restrict__ rface, double* __restrict__ qcell,
-                                                   const int* __restrict__ active) {
+                                                   const int* __restrict__ active, TS* __restrict__ dWs0 = nullptr,
+                                                   TS* __restrict__ dW0 = nullptr, int c0_end = 0) {
   using Dm = Dims<DIM>;
   constexpr int NV = Dm::NV, NFC = Dm::NFC;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -580,7 +599,12 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
     }
     if (live) alpha[c] = a;
     // LU-SGS diagonal with DF, or with the constant of the fixed-factor schemes (relax_fixed >= 0)
-    if (Dg) Dg[c] = lusgs_diag<DIM>(T, c, rface, relax_fixed < 0.0 ? a : relax_fixed, dte[c], dti[c]);
+    if (Dg) {
+      const double rel = relax_fixed < 0.0 ? a : relax_fixed;
+      const double D = lusgs_diag<DIM>(T, c, rface, rel, dte[c], dti[c]);
+      Dg[c] = D;
+      if (dWs0 && c < c0_end) colour0_forward<NV, TS>(c, R, rel, D, dWs0, dW0);
+    }
   }
   if (norm_part) {
     // block reduction in a fixed order: warp shuffles then warp 0
@@ -891,7 +915,7 @@ __global__ void __launch_bounds__(kBlock) k_face_kfvs(FaceSet Fs, const double* 
 
 // ... then per cell: R~ = sum_f +-S F + P (or, with Rstar, the forcing
 // P = R* - R), local time steps and the DF-relaxed LU-SGS diagonal.
-template <int DIM>
+template <int DIM, typename T = double>
 __global__ void __launch_bounds__(kBlock) k_coarse_cell(Topo Tp, const double* __restrict__ W,
                                                         const double* __restrict__ Fface,
                                                         const double* __restrict__ rface,
@@ -899,7 +923,8 @@ __global__ void __launch_bounds__(kBlock) k_coarse_cell(Topo Tp, const double* _
                                                         const double* __restrict__ Rstar,
                                                         const double* __restrict__ alpha, double gamma,
                                                         double cfl_exp, double cfl_imp, double* __restrict__ out,
-                                                        double* __restrict__ Dg) {
+                                                        double* __restrict__ Dg, T* __restrict__ dWs0,
+                                                        T* __restrict__ dW0, int c0_end) {
   constexpr int NV = DIM + 2;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= Tp.n) return;
@@ -933,7 +958,9 @@ __global__ void __launch_bounds__(kBlock) k_coarse_cell(Topo Tp, const double* _
       sum += Tp.S[e] * (fabs(un * ir) + cs);
     }
     const double V = Tp.vol[c];
-    Dg[c] = lusgs_diag<DIM>(Tp, c, rface, alpha[c], cfl_exp * V / sum, cfl_imp * V / sum);
+    const double D = lusgs_diag<DIM>(Tp, c, rface, alpha[c], cfl_exp * V / sum, cfl_imp * V / sum);
+    Dg[c] = D;
+    if (dWs0 && c < c0_end) colour0_forward<NV, T>(c, out, alpha[c], D, dWs0, dW0);
   }
 }
 
