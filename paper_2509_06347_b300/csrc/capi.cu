@@ -247,6 +247,32 @@ void build_fine_device(MeshDev& M) {
   std::vector<double> bsc(n);
   for (int64_t c = 0; c < n; ++c) bsc[c] = std::pow(F.vol[c], 2.0 / dim);
   d.bsc = upload(P, bsc);
+  // per cell, the largest |monomial| of X = x - centroid over its face Gauss
+  // points, in the coefficient order of the reconstruction (X_d, then X_a X_b)
+  {
+    const int ngp = F.ngp, nk = F.nk, nq = nk - dim;
+    const int qa[6] = {0, 0, 0, 1, 1, 2}, qb[6] = {0, 1, 2, 1, 2, 2};
+    const int qa2[3] = {0, 0, 1}, qb2[3] = {0, 1, 1};
+    std::vector<double> gm((size_t)nk * n, 0.0);
+    for (int64_t c = 0; c < n; ++c)
+      for (int k = 0; k < nfc; ++k) {
+        const int64_t f = F.cface[c * nfc + k];
+        const std::vector<double>& X = F.cside[c * nfc + k] > 0 ? F.XL : F.XR;
+        for (int g = 0; g < ngp; ++g) {
+          const double* x = &X[((size_t)f * ngp + g) * dim];
+          for (int d = 0; d < dim; ++d) {
+            double& t = gm[(size_t)d * n + c];
+            t = std::max(t, std::fabs(x[d]));
+          }
+          for (int q = 0; q < nq; ++q) {
+            const int a = dim == 2 ? qa2[q] : qa[q], b = dim == 2 ? qb2[q] : qb[q];
+            double& t = gm[(size_t)(dim + q) * n + c];
+            t = std::max(t, std::fabs(x[a] * x[b]));
+          }
+        }
+      }
+    d.gpmax = upload(P, gm);
+  }
   M.fine = d;
 }
 

@@ -52,6 +52,7 @@ struct DevFine {
   const double* m2;     // [dim*dim][n]
   const double* vol;    // [n]
   const double* bsc;    // [n] |Omega|^(2/dim)
+  const double* gpmax;  // [nk][n] max over the cell's face Gauss points of |X^k| (monomials of X = x - centroid)
   const int* grp;       // [n] batch group of each cell (free stream index), or null
 };
 
@@ -292,10 +293,36 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
 #pragma unroll
     for (int q = 0; q < D::NQ; ++q) P[v][1 + DIM + q] = fh * c2[1 + DIM + q];
   }
-  // positivity at the cell's face Gauss points (reading: first-order fallback)
+  // positivity at the cell's face Gauss points (reading: first-order fallback).
+  // A sufficient condition first: with |X^k| <= gpmax_k at those points,
+  // |P_v - c0_v| <= B_v = sum_k |c_k| gpmax_k, so rho >= c0_rho - B_rho and
+  // p > 0 follows from E_min - |m|_max^2 / (2 rho_min) > 0; only the cells it
+  // does not clear evaluate every Gauss point (same outcome, less FP64 work).
+  bool sure = false;
+  {
+    double B[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double b = 0.0;
+#pragma unroll
+      for (int k = 0; k < NK; ++k) b += fabs(P[v][1 + k]) * M.gpmax[(size_t)k * n + c];
+      B[v] = b;
+    }
+    const double rmin = P[0][0] - B[0];
+    if (rmin > 1e-12 * fabs(P[0][0])) {
+      double mm = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const double t = fabs(P[1 + d][0]) + B[1 + d];
+        mm += t * t;
+      }
+      const double emin = P[NV - 1][0] - B[NV - 1];
+      sure = emin - 0.5 * mm / rmin > 1e-12 * fabs(P[NV - 1][0]);
+    }
+  }
   bool bad = false;
 #pragma unroll 1
-  for (int m = 0; m < NFC && !bad; ++m) {
+  for (int m = 0; m < NFC && !bad && !sure; ++m) {
     const double* X = (sd[m] > 0 ? M.XL : M.XR) + (size_t)fid[m] * D::NGP * DIM;
 #pragma unroll
     for (int g = 0; g < D::NGP; ++g) {
