@@ -173,6 +173,13 @@ int cgks_agglomerate(cgks_t* h, int dim, int64_t n_cells, const int32_t* cell_no
  * (out must hold 4 * n_levels values); *n_levels receives the level count. */
 int cgks_mesh_info(cgks_t* h, int mesh_id, int* n_levels, int64_t* out);
 
+/* The stored numbering of a level (host int32, both nullable): order[k] = the
+ * original id of the k-th stored cell (cells grouped by colour, ascending
+ * colour, original order within a colour, so that each colour is one
+ * contiguous launch); parent[i] = the agglomerate on the next level of
+ * original cell i, in that level's original ids (not for the coarsest level). */
+int cgks_get_hierarchy(cgks_t* h, int mesh_id, int level, int32_t* order, int32_t* parent);
+
 /* Colour (1..Nc) of every cell of a level, original order, host int32 [n]. */
 int cgks_get_coloring(cgks_t* h, int mesh_id, int level, int32_t* colors);
 

@@ -23,7 +23,7 @@ TAG_WALL, TAG_FARFIELD, TAG_NOSLIP_WALL, TAG_FARFIELD_RIEMANN = 1, 2, 3, 4
 
 # every entry point declared in include/cgks.h
 EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_error", "cgks_upload_mesh",
-           "cgks_upload_hierarchy", "cgks_agglomerate", "cgks_mesh_info", "cgks_get_coloring", "cgks_set_freestream",
+           "cgks_upload_hierarchy", "cgks_agglomerate", "cgks_mesh_info", "cgks_get_hierarchy", "cgks_get_coloring", "cgks_set_freestream",
            "cgks_init_state", "cgks_get_state", "cgks_set_state", "cgks_residual", "cgks_reconstruct",
            "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
            "cgks_gks_points", "cgks_kfvs_points", "cgks_run_stage", "cgks_launch_count",
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "cgks_special_selftest": [P, I64, P, P],
         "cgks_mlp_features": [P, I, P],
         "cgks_get_coloring": [P, I, I, P],
+        "cgks_get_hierarchy": [P, I, I, P, P],
         "cgks_set_freestream": [P, I, P],
         "cgks_init_state": [P, I, P, P, I],
         "cgks_get_state": [P, I, P, P, P, I],
@@ -209,6 +210,14 @@ class Context:
         self._check(self._L.cgks_mesh_info(self.h, mesh_id, C.byref(nl), _ptr(out)))
         return [dict(cells=int(out[4 * l]), colors=int(out[4 * l + 1]), faces=int(out[4 * l + 2]),
                      bfaces=int(out[4 * l + 3])) for l in range(nl.value)]
+
+    def cgks_get_hierarchy(self, mesh_id: int, level: int, n: int, with_parent: bool = True):
+        """(order, parent): the stored (colour-major) order of a level as original
+        ids, and each cell's agglomerate on the next level (None on the coarsest)."""
+        order = np.zeros(n, np.int32)
+        parent = np.zeros(n, np.int32) if with_parent else None
+        self._check(self._L.cgks_get_hierarchy(self.h, mesh_id, level, _ptr(order), _ptr(parent)))
+        return order, parent
 
     def cgks_get_coloring(self, mesh_id: int, level: int, n: int):
         out = np.zeros(n, np.int32)

@@ -963,6 +963,23 @@ int cgks_get_coloring(cgks_t* h, int mesh_id, int level, int32_t* colors) {
   });
 }
 
+int cgks_get_hierarchy(cgks_t* h, int mesh_id, int level, int32_t* order, int32_t* parent) {
+  return guarded(h, [&]() -> int {
+    MeshDev& M = get_mesh(h, mesh_id);
+    if (level < 0 || level > (int)M.H.coarse.size()) throw ArgError("invalid level");
+    if (parent && level == (int)M.H.coarse.size()) throw ArgError("the coarsest level has no parent map");
+    const std::vector<int64_t>& ip = level == 0 ? M.H.fine.iperm : M.H.coarse[level - 1].iperm;
+    if (order)
+      for (size_t i = 0; i < ip.size(); ++i) order[i] = (int32_t)ip[i];
+    if (parent) {
+      // parent_of_fine: this level's new ids -> next level's new ids; map both to original ids
+      const CoarseLevel& C = M.H.coarse[level];
+      for (size_t i = 0; i < ip.size(); ++i) parent[ip[i]] = (int32_t)C.iperm[C.parent_of_fine[i]];
+    }
+    return CGKS_OK;
+  });
+}
+
 int cgks_set_freestream(cgks_t* h, int mesh_id, const double* w) {
   return guarded(h, [&]() -> int {
     MeshDev& M = get_mesh(h, mesh_id);

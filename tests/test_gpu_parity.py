@@ -167,7 +167,14 @@ def test_hierarchy_and_coloring_bit_exact(ctx, name):
         assert lv["cells"] == om.n_cells(l)
         assert lv["faces"] == len(om.faces(l)["S"])
         assert lv["colors"] == om.n_colors(l)
-        np.testing.assert_array_equal(ctx.cgks_get_coloring(mid, l, lv["cells"]), om.colors(l))
+        colors = om.colors(l)
+        np.testing.assert_array_equal(ctx.cgks_get_coloring(mid, l, lv["cells"]), colors)
+        # stored order: colour-major, original order within a colour; parents as uploaded
+        last = l == len(info) - 1
+        order, parent = ctx.cgks_get_hierarchy(mid, l, lv["cells"], with_parent=not last)
+        np.testing.assert_array_equal(order, np.argsort(colors, kind="stable"))
+        if not last:
+            np.testing.assert_array_equal(parent, np.asarray(m["parents"][l]))
 
 
 @pytest.mark.parametrize("name", list(MESHES))
