@@ -509,13 +509,16 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool c0_done =
       L.n, h->cfg.gamma, L.W, dW, M.cnt, masked ? M.lgrp[0] : nullptr, masked ? M.active : nullptr);
 }
 
-// TS / fuse_c0: as in fine_residual
+// TS / fuse_c0: as in fine_residual.  faces_ready: L.Fc and L.rface already
+// hold the face fluxes and spectral radii of the current state
 template <int DIM, typename TS = double>
-void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag, bool fuse_c0 = false) {
+void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag, bool fuse_c0 = false,
+                 bool faces_ready = false) {
   const PhysParams p = phys(h->cfg, DIM);
   const int bf = fit_block(h, L.faces.nf, M.blk[B_FACE]), bc = fit_block(h, L.n, M.blk[B_CELL]);
-  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(
-      L.faces, L.W, M.winf, p, L.Fc, want_diag ? L.rface : nullptr);
+  if (!faces_ready)
+    k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(
+        L.faces, L.W, M.winf, p, L.Fc, want_diag ? L.rface : nullptr);
   const bool fuse = fuse_c0 && want_diag;
   TS* dWs0 = fuse ? (sizeof(TS) == 8 ? (TS*)L.dWs64 : (TS*)L.dWs32) : nullptr;
   TS* dW0 = fuse && L.n_colors == 1 ? (sizeof(TS) == 8 ? (TS*)L.dW64 : (TS*)L.dW32) : nullptr;
@@ -524,12 +527,14 @@ void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want
       h->cfg.cfl_imp, L.R, want_diag ? L.D : nullptr, dWs0, dW0, L.color_off[1]);
 }
 
-// FAS forcing P = R* - R(W0) on a coarse level
+// FAS forcing P = R* - R(W0) on a coarse level.  The restriction sets W = W0,
+// so the face fluxes and spectral radii computed here also serve the first
+// smoothing step (coarse_prep with faces_ready).
 template <int DIM>
 void coarse_forcing(cgks_t* h, MeshDev& M, LevelDev& L) {
   const PhysParams p = phys(h->cfg, DIM);
   const int bf = fit_block(h, L.faces.nf, M.blk[B_FACE]), bc = fit_block(h, L.n, M.blk[B_CELL]);
-  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, nullptr);
+  k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(L.faces, L.W0, M.winf, p, L.Fc, L.rface);
   k_coarse_cell<DIM, double><<<blocks_for(L.n, bc), bc, 0, h->stream>>>(L.topo, L.W0, L.Fc, nullptr, nullptr, L.Rstar,
                                                                  L.alpha, h->cfg.gamma, 0.0, 0.0, L.P, nullptr,
                                                                  nullptr, nullptr, 0);
@@ -567,7 +572,7 @@ void vcycle_coarse(cgks_t* h, MeshDev& M) {
                                                                 F.R, C.W0, C.W, C.alpha, C.Rstar);
     coarse_forcing<DIM>(h, M, C);
     for (int s = 0; s < h->cfg.n_sweep_coarse; ++s) {
-      coarse_prep<DIM, T>(h, M, C, C.P, true, true);
+      coarse_prep<DIM, T>(h, M, C, C.P, true, true, s == 0);
       sweeps<DIM, T>(h, M, C, nullptr, true);
     }
     if (l + 1 < M.nlev) coarse_prep<DIM>(h, M, C, C.P, false);  // R~ = R(W) + P to restrict
