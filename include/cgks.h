@@ -69,7 +69,8 @@ typedef struct cgks_config {
   double cfl_imp;         /* CFL of the implicit (DF-weighted) part, Sec 4.3 (10) */
   double cfl_exp;         /* CFL of the explicit part and of the flux time step (0.5) */
   double tau_c1, tau_c2;  /* numerical collision time tau = c1 dt + c2 |dp|/(pl+pr) dt (0.01, 1);
-                             with mu > 0 the c1 dt term gives way to mu / p */
+                             with mu > 0 the c1 dt term gives way to mu / p; c1 > 0 and
+                             c2 >= 0, finite, or cgks_create returns CGKS_ERR_ARG */
   double weno_gamma_high; /* linear weight of the large HWENO stencil (0.95) */
   double weno_eps;        /* WENO epsilon (1e-15) */
   double r_safety;        /* spectral-radius factor of the LU-SGS splitting (1) */

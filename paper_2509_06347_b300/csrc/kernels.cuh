@@ -277,16 +277,16 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
     }
     b2 = b1s * b2 + b2s * b2q;
     // w_H ~ gam_hi (1 + tz / (b2 + eps)), w_L ~ gl (1 + tz / (b1 + eps)), normalised;
-    // both multiplied by (b1 + eps)(b2 + eps) so that one reciprocal remains
+    // both multiplied by (b1 + eps)(b2 + eps) so that one reciprocal remains;
+    // fh = w_H / gam_hi
     const double gl = 1.0 - gam_hi;
     const double tz = fabs(b2 - b1);
     const double e1 = b1 + weps, e2 = b2 + weps;
-    double wh = gam_hi * (e2 + tz) * e1;
+    const double xh = (e2 + tz) * e1;
     double wl = gl * (e1 + tz) * e2;
-    const double iw = 1.0 / (wh + wl);
-    wh *= iw;
+    const double iw = 1.0 / (gam_hi * xh + wl);
     wl *= iw;
-    const double fh = wh / gam_hi;
+    const double fh = xh * iw;
     P[v][0] = fh * (c2[0] - gl * W0[v]) + wl * W0[v];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) P[v][1 + d] = fh * (c2[1 + d] - gl * g1[d]) + wl * g1[d];
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
         mm += t * t;
       }
       const double emin = P[NV - 1][0] - B[NV - 1];
-      sure = emin - 0.5 * mm / rmin > 1e-12 * fabs(P[NV - 1][0]);
+      sure = emin * rmin - 0.5 * mm > 1e-12 * fabs(P[NV - 1][0]) * rmin;  // rmin > 0 here
     }
   }
   bool bad = false;
@@ -480,8 +480,7 @@ __global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(De
     to_local<DIM, S>(fr, Wr, wr);
     grad_to_local<DIM, S>(fr, gl, Gl);
     grad_to_local<DIM, S>(fr, gr, Gr);
-    gks_flux<DIM, POINT, S>(P, wl, Gl, wr, Gr, S(dt), Fl, Wt);
-    af = df_factor<DIM, S>(P.gamma, wl, wr);
+    af = gks_flux<DIM, POINT, S>(P, wl, Gl, wr, Gr, S(dt), Fl, Wt);
     S Fg[NV], Wg[NV];
     to_global<DIM, S>(fr, Fl, Fg);
     to_global<DIM, S>(fr, Wt, Wg);
@@ -1293,10 +1292,10 @@ __global__ void k_gks_points(int n, PhysParams P, const double* __restrict__ Wl,
       gl[d][v] = Gl[((size_t)i * DIM + d) * NV + v];
       gr[d][v] = Gr[((size_t)i * DIM + d) * NV + v];
     }
-  gks_flux<DIM>(P, wl, gl, wr, gr, dt[i], f, w);
+  const double a = gks_flux<DIM>(P, wl, gl, wr, gr, dt[i], f, w);
 #pragma unroll
   for (int v = 0; v < NV; ++v) { F[(size_t)i * NV + v] = f[v]; Wt[(size_t)i * NV + v] = w[v]; }
-  alpha[i] = df_factor<DIM>(P.gamma, wl, wr);
+  alpha[i] = a;
 }
 
 template <int DIM>

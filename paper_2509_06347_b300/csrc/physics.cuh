@@ -32,8 +32,8 @@ struct PhysT {
   S K;       // internal degrees of freedom
   S c1, c2;  // collision-time coefficients
   S mu;      // dynamic viscosity (Navier-Stokes, tau = mu / p); 0 for the Euler equations
-  // derived on the host: N = K + dim, 2/N, 4/N
-  S N, twoOverN, fourOverN;
+  // derived on the host: N = K + dim, 2/N, 4/N, 2/gamma
+  S N, twoOverN, fourOverN, twoOverGamma;
 };
 using PhysParams = PhysT<double>;
 
@@ -47,6 +47,7 @@ inline PhysParams make_phys(double gamma, int dim, double c1, double c2, double 
   p.N = p.K + dim;
   p.twoOverN = 2.0 / p.N;
   p.fourOverN = 4.0 / p.N;
+  p.twoOverGamma = 2.0 / gamma;
   return p;
 }
 
@@ -60,6 +61,7 @@ inline PhysT<dword> phys_dword(const PhysParams& p) {
   q.N = dword(p.N);
   q.twoOverN = dword(p.twoOverN);
   q.fourOverN = dword(p.fourOverN);
+  q.twoOverGamma = dword(p.twoOverGamma);
   return q;
 }
 
@@ -77,24 +79,29 @@ struct Mom {
 // primitive: rho, U[DIM], lambda = rho / (2 p)
 template <int DIM, typename S = double>
 struct Prim {
-  S rho, irho, lam, h;  // h = 1 / (2 lambda)
+  S rho, irho, lam, h;  // h = 1 / (2 lambda) = p / rho
+  S sl;                 // sqrt(lambda)
   S U[DIM];
 };
 
+// With A = rho E - |rho U|^2 / 2 = rho (E - rho |U|^2 / 2) and
+// E - rho |U|^2 / 2 = N rho h / 2 (N = K + DIM), one reciprocal r = 1 / (rho A)
+// gives both 1 / rho = A r and lambda = N rho^2 / (4 A) = (N / 4) rho^3 r.
 template <int DIM, typename S>
 __device__ __forceinline__ Prim<DIM, S> to_prim(const S* W, const PhysT<S>& P) {
   Prim<DIM, S> p;
   p.rho = W[0];
-  p.irho = S(1.0) / W[0];
-  S ke = S(0.0);
+  S m2 = S(0.0);
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    p.U[d] = W[1 + d] * p.irho;
-    ke += p.U[d] * W[1 + d];
-  }
-  // E - rho|U|^2/2 = (K + DIM) rho / (4 lambda) = (K + DIM) rho h / 2
-  p.h = (W[DIM + 1] - S(0.5) * ke) * p.irho * P.twoOverN;
-  p.lam = S(0.5) / p.h;
+  for (int d = 0; d < DIM; ++d) m2 += W[1 + d] * W[1 + d];
+  const S A = p.rho * W[DIM + 1] - S(0.5) * m2;
+  const S r = S(1.0) / (p.rho * A);
+  p.irho = A * r;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) p.U[d] = W[1 + d] * p.irho;
+  p.h = A * p.irho * p.irho * P.twoOverN;
+  p.lam = S(0.25) * P.N * (p.rho * p.rho) * (p.rho * r);
+  p.sl = sqrt(p.lam);
   return p;
 }
 
@@ -130,7 +137,7 @@ __device__ __forceinline__ void normal_moments(const Prim<DIM, S>& p, int half, 
     m.mu[0] = S(1.0);
     m.mu[1] = U;
   } else {
-    const S sl = sqrt(p.lam);
+    const S sl = p.sl;
     const S E = exp_neg(-p.lam * U * U);
     const S te = E * S(0.5 * M_2_SQRTPI) * (sl * h);  // e^{-lam U^2} / (2 sqrt(pi lam))
     const S hs = S(0.5) * erfc_with_exp(S(-half) * sl * U, E);  // erfc(x) from E = e^{-x^2}
@@ -319,11 +326,10 @@ __device__ __forceinline__ void poly_psi_mom(const Mom<DIM, S>& m, const Poly<DI
 // Sum over directions d of (dF_d/dW) . dW_d for the Euler fluxes F_d along the
 // local axes: for a Maxwellian g(W(x)), int u_d psi dg/dx_d = d/dx_d F_d(W), so
 // this equals <psi (a.u)> of the full-space Maxwellian (times rho) without
-// forming the velocity moments.
+// forming the velocity moments.  ir = 1 / W[0], which every caller already holds.
 template <int DIM, typename S>
-__device__ __forceinline__ void euler_flux_divergence(S gamma, const S* W, const S (*dW)[DIM + 2], S* out) {
+__device__ __forceinline__ void euler_flux_divergence(S gamma, const S* W, S ir, const S (*dW)[DIM + 2], S* out) {
   constexpr int NV = DIM + 2;
-  const S ir = S(1.0) / W[0];
   S u[DIM], q2 = S(0.0);
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
@@ -364,10 +370,11 @@ __device__ __forceinline__ void euler_flux_divergence(S gamma, const S* W, const
 //   Q_d^i   = rho U_0 U_d U_i + p (U_0 delta_di + U_d delta_0i + U_i delta_0d)
 //   Q_d^E   = U_0 U_d (rho |U|^2 + (D + 4 + K) p) / 2
 //             + delta_0d (p |U|^2 + (D + 2 + K) p theta) / 2.
+// ir = 1 / W[0].
 template <int DIM, typename S>
-__device__ __forceinline__ void second_moment_divergence(S gamma, S K, const S* W, const S (*dW)[DIM + 2], S* out) {
+__device__ __forceinline__ void second_moment_divergence(S gamma, S K, const S* W, S ir, const S (*dW)[DIM + 2],
+                                                         S* out) {
   constexpr int NV = DIM + 2;
-  const S ir = S(1.0) / W[0];
   S U[DIM], q2 = S(0.0);
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
@@ -413,14 +420,14 @@ __device__ __forceinline__ void second_moment_divergence(S gamma, S K, const S* 
 
 // (dF_n/dW) . v for the Euler flux through the local normal (first axis)
 template <int DIM, typename S>
-__device__ __forceinline__ void euler_flux_jvp_normal(S gamma, const S* W, const S* v, S* out) {
+__device__ __forceinline__ void euler_flux_jvp_normal(S gamma, const S* W, S ir, const S* v, S* out) {
   constexpr int NV = DIM + 2;
   S g[DIM][NV];
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
 #pragma unroll
     for (int i = 0; i < NV; ++i) g[d][i] = d == 0 ? v[i] : S(0.0);
-  euler_flux_divergence<DIM, S>(gamma, W, g, out);
+  euler_flux_divergence<DIM, S>(gamma, W, ir, g, out);
 }
 
 // Out-of-line variants for the double-word flux.  Its code, fully inlined, is
@@ -442,23 +449,24 @@ __device__ __forceinline__ void slope_solve_c(const Prim<DIM, S>& p, const PhysT
   else slope_solve<DIM, S>(p, P, b, a);
 }
 template <int DIM, typename S>
-__device__ __noinline__ void euler_flux_divergence_ool(S gamma, const S* W, const S (*dW)[DIM + 2], S* out) {
-  euler_flux_divergence<DIM, S>(gamma, W, dW, out);
+__device__ __noinline__ void euler_flux_divergence_ool(S gamma, const S* W, S ir, const S (*dW)[DIM + 2], S* out) {
+  euler_flux_divergence<DIM, S>(gamma, W, ir, dW, out);
 }
 template <int DIM, typename S>
-__device__ __forceinline__ void euler_flux_divergence_c(S gamma, const S* W, const S (*dW)[DIM + 2], S* out) {
-  if constexpr (OutOfLine<S>::value) euler_flux_divergence_ool<DIM, S>(gamma, W, dW, out);
-  else euler_flux_divergence<DIM, S>(gamma, W, dW, out);
+__device__ __forceinline__ void euler_flux_divergence_c(S gamma, const S* W, S ir, const S (*dW)[DIM + 2], S* out) {
+  if constexpr (OutOfLine<S>::value) euler_flux_divergence_ool<DIM, S>(gamma, W, ir, dW, out);
+  else euler_flux_divergence<DIM, S>(gamma, W, ir, dW, out);
 }
 template <int DIM, typename S>
-__device__ __noinline__ void second_moment_divergence_ool(S gamma, S K, const S* W, const S (*dW)[DIM + 2], S* out) {
-  second_moment_divergence<DIM, S>(gamma, K, W, dW, out);
+__device__ __noinline__ void second_moment_divergence_ool(S gamma, S K, const S* W, S ir, const S (*dW)[DIM + 2],
+                                                         S* out) {
+  second_moment_divergence<DIM, S>(gamma, K, W, ir, dW, out);
 }
 template <int DIM, typename S>
-__device__ __forceinline__ void second_moment_divergence_c(S gamma, S K, const S* W, const S (*dW)[DIM + 2],
+__device__ __forceinline__ void second_moment_divergence_c(S gamma, S K, const S* W, S ir, const S (*dW)[DIM + 2],
                                                            S* out) {
-  if constexpr (OutOfLine<S>::value) second_moment_divergence_ool<DIM, S>(gamma, K, W, dW, out);
-  else second_moment_divergence<DIM, S>(gamma, K, W, dW, out);
+  if constexpr (OutOfLine<S>::value) second_moment_divergence_ool<DIM, S>(gamma, K, W, ir, dW, out);
+  else second_moment_divergence<DIM, S>(gamma, K, W, ir, dW, out);
 }
 template <int DIM, typename S>
 __device__ __noinline__ void moments_ool(const Prim<DIM, S>& p, S K, int half, Mom<DIM, S>& m) {
@@ -494,12 +502,28 @@ __device__ __forceinline__ void kin_moments_c(const Mom<DIM, S>& m, S c0, S cA, 
 
 // Gas-kinetic flux (time average over [0, dt]) and point value at t = dt in
 // the local frame (u normal).  G?[d][v] = derivative along local direction d.
+// Returns the DF point factor 1 / (1 + D^2) of Sec 3.3, formed from the same
+// primitives: 1 / p = 2 lambda / rho and 1 / c = sqrt(rho / (gamma p)) =
+// sqrt(2 lambda / gamma), so D = |pl - pr| (1/pl + 1/pr) + |Ul/cl - Ur/cr|^2
+// needs no division beyond the final one.
 template <int DIM, bool POINT = true, typename S = double>
-__device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2], const S* Wr, const S (*Gr)[DIM + 2],
-                         S dt, S* F, S* Wt) {
+__device__ S gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2], const S* Wr, const S (*Gr)[DIM + 2],
+                      S dt, S* F, S* Wt) {
   constexpr int NV = DIM + 2;
   const S K = P.K;
   const Prim<DIM, S> pl = to_prim<DIM, S>(Wl, P), pr = to_prim<DIM, S>(Wr, P);
+  const S pL = pl.rho * pl.h, pR = pr.rho * pr.h;
+  S alpha;
+  {
+    S dm2 = S(0.0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const S dm = pl.U[d] * pl.sl - pr.U[d] * pr.sl;
+      dm2 += dm * dm;
+    }
+    const S D = S(2.0) * fabs(pL - pR) * (pl.lam * pl.irho + pr.lam * pr.irho) + P.twoOverGamma * dm2;
+    alpha = S(1.0) / (S(1.0) + D * D);
+  }
   // half-space moments for the kinetic part
   Mom<DIM, S> ml, mr;
   moments_c<DIM, S>(pl, K, +1, ml);
@@ -511,18 +535,18 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
 #pragma unroll
   for (int i = 0; i < NV; ++i) Wc[i] = pl.rho * Wc[i] + pr.rho * t[i];
   // pressure of the interface equilibrium
+  const S irc = S(1.0) / Wc[0];
   S pwc;
   {
     S kc = S(0.0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) kc += Wc[1 + d] * Wc[1 + d];
-    pwc = (P.gamma - S(1.0)) * (Wc[DIM + 1] - S(0.5) * kc / Wc[0]);
+    pwc = (P.gamma - S(1.0)) * (Wc[DIM + 1] - S(0.5) * kc * irc);
   }
   {
     // vacuum (both sides moving apart): no admissible interface equilibrium;
     // take the collisionless limit, i.e. the KFVS flux, point value W^c
-    const S pwl = pl.rho * pl.h, pwr = pr.rho * pr.h;  // p = rho / (2 lambda)
-    if (!(Wc[0] > S(1e-10) * (pl.rho + pr.rho)) || !(pwc > S(1e-10) * (pwl + pwr))) {
+    if (!(Wc[0] > S(1e-10) * (pl.rho + pr.rho)) || !(pwc > S(1e-10) * (pL + pR))) {
       S a[NV], b[NV];
       psi_mom<DIM, 1, 0, 0>(ml, a);
       psi_mom<DIM, 1, 0, 0>(mr, b);
@@ -531,10 +555,9 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
         F[i] = pl.rho * a[i] + pr.rho * b[i];
         Wt[i] = Wc[i];
       }
-      return;
+      return alpha;
     }
   }
-  const S irc = S(1.0) / Wc[0];
   // spatial slopes of the two kinetic Maxwellians (Eq. co); the interface
   // Maxwellian's slopes enter only through closed-form moments below
   S al[DIM][NV], ar[DIM][NV], b[NV];
@@ -553,11 +576,11 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
   S Al[NV], Ar[NV], Ac[NV];
   {
     S s[NV];
-    euler_flux_divergence_c<DIM, S>(P.gamma, Wl, Gl, s);
+    euler_flux_divergence_c<DIM, S>(P.gamma, Wl, pl.irho, Gl, s);
 #pragma unroll
     for (int i = 0; i < NV; ++i) s[i] *= -pl.irho;
     slope_solve_c<DIM, S>(pl, P, s, Al);
-    euler_flux_divergence_c<DIM, S>(P.gamma, Wr, Gr, s);
+    euler_flux_divergence_c<DIM, S>(P.gamma, Wr, pr.irho, Gr, s);
 #pragma unroll
     for (int i = 0; i < NV; ++i) s[i] *= -pr.irho;
     slope_solve_c<DIM, S>(pr, P, s, Ar);
@@ -573,38 +596,47 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
       for (int i = 0; i < NV; ++i) gc[d][i] = S(0.5) * (Gl[d][i] + Gr[d][i]);
-    euler_flux_divergence_c<DIM, S>(P.gamma, Wc, gc, PAc);
-    second_moment_divergence_c<DIM, S>(P.gamma, K, Wc, gc, QAc);
+    euler_flux_divergence_c<DIM, S>(P.gamma, Wc, irc, gc, PAc);
+    second_moment_divergence_c<DIM, S>(P.gamma, K, Wc, irc, gc, QAc);
     S wt[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       PAc[i] *= irc;
       wt[i] = -PAc[i];
     }
-    euler_flux_jvp_normal<DIM, S>(P.gamma, Wc, wt, UAc);
+    euler_flux_jvp_normal<DIM, S>(P.gamma, Wc, irc, wt, UAc);
     // Euler flux of W^c through the local normal
     const S un = Wc[1] * irc;
-    S kc = S(0.0);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) kc += Wc[1 + d] * Wc[1 + d];
-    const S pwc = (P.gamma - S(1.0)) * (Wc[NV - 1] - S(0.5) * kc * irc);
 #pragma unroll
     for (int i = 0; i < NV; ++i) Fc[i] = un * Wc[i];
     Fc[1] += pwc;
     Fc[NV - 1] += un * pwc;
   }
   (void)Ac;
-  // collision time and time integrals
-  const S pL = pl.rho * pl.h, pR = pr.rho * pr.h;
-  // Euler: tau = C1 dt + C2 |dp| / (pl + pr) dt; Navier-Stokes (Sec 2.1): the
-  // physical mu / p of the interface equilibrium in place of C1 dt
-  const S tau = (P.mu > S(0.0) ? P.mu / pwc : P.c1 * dt) + P.c2 * fabs(pL - pR) / (pL + pR) * dt;
-  const S e = exp_neg(-dt / tau);
-  const S T1 = dt - tau * (S(1.0) - e);
-  const S T2 = -tau * dt + S(2.0) * tau * tau - tau * (dt + S(2.0) * tau) * e;
-  const S T3 = S(0.5) * dt * dt - tau * dt + tau * tau * (S(1.0) - e);
-  const S T4 = tau * (S(1.0) - e);
-  const S T5 = tau * tau - tau * (dt + tau) * e;
+  // Collision time.  Euler: tau = C1 dt + C2 |dp| / (pl + pr) dt; Navier-Stokes
+  // (Sec 2.1): the physical mu / p of the interface equilibrium in place of
+  // C1 dt.  Either way tau / dt = a / b, and one reciprocal r = 1 / (a b) gives
+  // s = tau / dt = a^2 r and dt / tau = b^2 r.
+  const S sp = pL + pR, cdp = P.c2 * fabs(pL - pR);
+  S ta, tb;
+  if (P.mu > S(0.0)) {
+    tb = pwc * dt * sp;
+    ta = P.mu * sp + cdp * pwc * dt;
+  } else {
+    tb = sp;
+    ta = P.c1 * sp + cdp;
+  }
+  const S tr = S(1.0) / (ta * tb);
+  const S s = ta * ta * tr;
+  const S tau = s * dt;
+  const S e = exp_neg(-(tb * tb * tr));
+  // the time integrals T1..T5 of the flux divided by dt, so that the flux
+  // needs no final division; the point-value coefficients C1..C3 as they are
+  const S T1 = S(1.0) - s * (S(1.0) - e);
+  const S T2 = tau * (S(2.0) * s - S(1.0) - (S(1.0) + S(2.0) * s) * e);
+  const S T3 = S(0.5) * dt - tau + tau * s * (S(1.0) - e);
+  const S T4 = s * (S(1.0) - e);
+  const S T5 = tau * (s - (S(1.0) + s) * e);
   const S C1 = S(1.0) - e, C2 = (dt + tau) * e - tau, C3 = dt - tau + tau * e;
   // --- equilibrium part (g^c, full space): T1 <u psi> + T2 <u psi (a_c . u)>
   // + T3 <u psi (A_c . psi)>; point value C1 <psi> + (C2 - C3) <psi (A_c . psi)>
@@ -628,9 +660,7 @@ __device__ void gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2],
 #pragma unroll
     for (int i = 0; i < NV; ++i) { F[i] += rho * fx[i]; Wt[i] += rho * wx[i]; }
   }
-  const S idt = S(1.0) / dt;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) F[i] *= idt;
+  return alpha;
 }
 
 // KFVS flux of constant states, local frame
@@ -651,25 +681,6 @@ __device__ __forceinline__ void kfvs_flux(const PhysParams& P, const double* Wl,
   for (int i = 0; i < NV; ++i) F[i] = pl.rho * a[i] + pr.rho * b[i];
 }
 
-// DF point factor 1 / (1 + D^2) from local-frame states (Sec 3.3)
-template <int DIM, typename S = double>
-__device__ __forceinline__ S df_factor(S gamma, const S* Wl, const S* Wr) {
-  S kl = S(0.0), kr = S(0.0);
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) { kl += Wl[1 + d] * Wl[1 + d]; kr += Wr[1 + d] * Wr[1 + d]; }
-  const S pl = (gamma - S(1.0)) * (Wl[DIM + 1] - S(0.5) * kl / Wl[0]);
-  const S pr = (gamma - S(1.0)) * (Wr[DIM + 1] - S(0.5) * kr / Wr[0]);
-  const S il = S(1.0) / (Wl[0] * sqrt(gamma * pl / Wl[0]));  // 1 / (rho c)
-  const S ir = S(1.0) / (Wr[0] * sqrt(gamma * pr / Wr[0]));
-  const S dp = fabs(pl - pr);
-  S D = dp / pl + dp / pr;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    const S dm = Wl[1 + d] * il - Wr[1 + d] * ir;
-    D += dm * dm;
-  }
-  return S(1.0) / (S(1.0) + D * D);
-}
 
 // ---------------------------------------------------------------------------
 // frames: rows n, t1, t2

@@ -83,6 +83,10 @@ def test_errors_are_status_codes(cg):
         cg.Context(df_relax=3)  # no such relaxation scheme
     with pytest.raises(cg.CgksError):
         cg.Context(df_relax=2, relax_beta=1.5)  # the fixed factor lies in [0, 1]
+    with pytest.raises(cg.CgksError):
+        cg.Context(tau_c1=0.0)  # the collision time must stay positive
+    with pytest.raises(cg.CgksError):
+        cg.Context(tau_c2=-1.0)
 
 
 def test_open_mesh_is_rejected(cg):
