@@ -540,6 +540,17 @@ __device__ __forceinline__ double lusgs_diag(const Topo& T, int c, const double*
   const double V = T.vol[c];
   return alpha * (V / dti + 0.5 * sr) + (1.0 - alpha) * V / dte;
 }
+// The same diagonal from the time-step denominator sum = sum_f S_f (|u.n| + c),
+// with dt_exp = cfl_exp V / sum and dt_imp = cfl_imp V / sum:
+// D_i = sum (alpha cfl_exp + (1 - alpha) cfl_imp) / (cfl_imp cfl_exp) + alpha / 2 sum S r,
+// one division where the form above takes four.
+template <int DIM>
+__device__ __forceinline__ double lusgs_diag_sum(const Topo& T, int c, const double* rface, double alpha, double sum,
+                                                 double cfl_exp, double cfl_imp) {
+  double sr = 0.0;
+  for (int e = T.off[c]; e < T.off[c + 1]; ++e) sr += T.S[e] * rface[T.face[e]];
+  return sum * (alpha * cfl_exp + (1.0 - alpha) * cfl_imp) / (cfl_imp * cfl_exp) + 0.5 * alpha * sr;
+}
 
 // The forward LU-SGS step of the first colour, fused into the kernel that
 // forms R~ and D: colour 0 has no lower-coloured neighbours, so its step is
@@ -549,7 +560,7 @@ template <int NV, typename T>
 __device__ __forceinline__ void colour0_forward(int c, const double* __restrict__ R, double alpha, double D,
                                                 T* __restrict__ dWs, T* __restrict__ dW) {
   const T ha = (T)(0.5 * alpha);
-  const T iD = (T)(1.0 / D);
+  const T iD = T(1) / (T)D;  // in the sweep precision: an FP32 reciprocal in the mixed mode
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const double rhs = -(R[(size_t)c * NV + v] + 0.0);
@@ -815,7 +826,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const
     offdiag_term<DIM, T>(Tp, e, W, src, rface, gamma, acc);
   }
   const T ha = (T)(0.5 * alpha[c]);
-  const T iD = (T)(1.0 / Dg[c]);
+  const T iD = T(1) / (T)Dg[c];  // as in colour0_forward
   if (MODE == 1) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) dW[(size_t)c * NV + v] = dWs[(size_t)c * NV + v] - ha * acc[v] * iD;
@@ -983,8 +994,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_cell(Topo Tp, const double* _
       for (int d = 0; d < DIM; ++d) un += Wi[1 + d] * Tp.nrm[(size_t)e * DIM + d];
       sum += Tp.S[e] * (fabs(un * ir) + cs);
     }
-    const double V = Tp.vol[c];
-    const double D = lusgs_diag<DIM>(Tp, c, rface, alpha[c], cfl_exp * V / sum, cfl_imp * V / sum);
+    const double D = lusgs_diag_sum<DIM>(Tp, c, rface, alpha[c], sum, cfl_exp, cfl_imp);
     Dg[c] = D;
     if (dWs0 && c < c0_end) colour0_forward<NV, T>(c, out, alpha[c], D, dWs0, dW0);
   }
