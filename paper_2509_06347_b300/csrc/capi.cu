@@ -421,15 +421,26 @@ void launch_flux(cgks_t* h, MeshDev& M, bool point = true, bool radius = true) {
   constexpr int NGP = Dims<DIM>::NGP, FPW = 32 / NGP;
   const int64_t warps = (M.fine.nf + FPW - 1) / FPW;
   const int64_t threads = warps * 32;
-  const int nb = blocks_for(threads, M.blk[B_FLUX]);
+  const int bs = M.blk[B_FLUX];
+  const int nb = blocks_for(threads, bs);
   const PhysParams P = phys(h->cfg, DIM);
+  // the FP64 kernel loops over its tasks: launch only the blocks that fit at
+  // once; the double-word kernel takes one task per warp (the full grid)
+  auto resident = [&](auto kern) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, 0) != cudaSuccess || occ < 1) {
+      (void)cudaGetLastError();
+      return nb;
+    }
+    return (int)std::min<int64_t>(nb, (int64_t)occ * h->sms);
+  };
   if (h->cfg.flux_precision == 1) {
     auto kern = point ? k_flux<DIM, true, dword> : k_flux<DIM, false, dword>;
-    kern<<<nb, M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef_dw, L.dte, M.winf, phys_dword(P), P.gamma, M.Fface,
+    kern<<<nb, bs, 0, h->stream>>>(M.fine, M.coef_dw, L.dte, M.winf, phys_dword(P), P.gamma, M.Fface,
                                               M.Wface, M.aface, L.W, radius ? L.rface : nullptr);
   } else {
     auto kern = point ? k_flux<DIM, true, double> : k_flux<DIM, false, double>;
-    kern<<<nb, M.blk[B_FLUX], 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, P, P.gamma, M.Fface, M.Wface, M.aface,
+    kern<<<resident(kern), bs, 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, P, P.gamma, M.Fface, M.Wface, M.aface,
                                               L.W, radius ? L.rface : nullptr);
   }
 }

@@ -420,22 +420,18 @@ __device__ __forceinline__ dword shfl_s(dword x, int src) {
   return dword(__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src));
 }
 
-// Gas-kinetic face flux.  S = double: FP64; S = dword: the same arithmetic in
-// double-word on the FP32 pipes (coefficients read as double-word, geometry and
-// time step converted once per Gauss point, results returned in FP64).
-template <int DIM, bool POINT, typename S = double>
-__global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(DevFine M, const S* __restrict__ coef,
-                                                 const double* __restrict__ dte, const double* __restrict__ winf,
-                                                 PhysT<S> P, double gamma, double* __restrict__ Fface,
-                                                 double* __restrict__ Wface, double* __restrict__ aface,
-                                                 const double* __restrict__ Wc, double* __restrict__ rface) {
+// One task of the gas-kinetic face flux: FPW faces, NGP lanes per face.
+template <int DIM, bool POINT, typename S>
+__device__ __forceinline__ void flux_task(const DevFine& M, const S* __restrict__ coef, const double* __restrict__ dte,
+                                          const double* __restrict__ winf, const PhysT<S>& P, double gamma,
+                                          double* __restrict__ Fface, double* __restrict__ Wface,
+                                          double* __restrict__ aface, const double* __restrict__ Wc,
+                                          double* __restrict__ rface, int task, int lane) {
   using D = Dims<DIM>;
   constexpr int NV = D::NV, NC = D::NC, NGP = D::NGP;
   constexpr int FPW = 32 / NGP;  // faces per warp
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int g = lane % NGP;
-  const int f = warp * FPW + lane / NGP;
+  const int f = task * FPW + lane / NGP;
   const bool active = lane < FPW * NGP && f < M.nf;
   S Fs[NV], Ws[NV], af = S(1.0);
 #pragma unroll
@@ -525,6 +521,34 @@ __global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(De
       ghost_state<DIM>(M.ftag[f], winf + NV * (M.grp ? M.grp[L] : 0), n, WL, WR, gamma);
     }
     rface[f] = spectral_radius<DIM, double>(gamma, WL, WR, n);
+  }
+}
+
+// Gas-kinetic face flux.  S = double: FP64; S = dword: the same arithmetic in
+// double-word on the FP32 pipes (coefficients read as double-word, geometry and
+// time step converted once per Gauss point, results returned in FP64).
+// In FP64 each warp loops over tasks of FPW faces.  The grid holds only the
+// blocks that are resident at once, and task t goes to block t mod gridDim.x,
+// so every SM gets the same number of tasks to within one (a grid of one block
+// per face group leaves a partial last wave on a few SMs).  The double-word
+// variant, whose registers are capped for two blocks per SM, keeps one task
+// per warp: the loop costs it stack space and spills.
+template <int DIM, bool POINT, typename S = double>
+__global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(DevFine M, const S* __restrict__ coef,
+                                                 const double* __restrict__ dte, const double* __restrict__ winf,
+                                                 PhysT<S> P, double gamma, double* __restrict__ Fface,
+                                                 double* __restrict__ Wface, double* __restrict__ aface,
+                                                 const double* __restrict__ Wc, double* __restrict__ rface) {
+  constexpr int FPW = 32 / Dims<DIM>::NGP;
+  const int lane = threadIdx.x & 31;
+  const int ntask = (M.nf + FPW - 1) / FPW;
+  if constexpr (OutOfLine<S>::value) {
+    const int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (task < ntask) flux_task<DIM, POINT, S>(M, coef, dte, winf, P, gamma, Fface, Wface, aface, Wc, rface, task, lane);
+  } else {
+    const int nwarp = gridDim.x * (blockDim.x >> 5);
+    for (int task = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; task < ntask; task += nwarp)
+      flux_task<DIM, POINT, S>(M, coef, dte, winf, P, gamma, Fface, Wface, aface, Wc, rface, task, lane);
   }
 }
 
