@@ -407,10 +407,24 @@ void build_levels_device(MeshDev& M, const cgks_config& cfg) {
 }
 
 // ---- kernels sequences ------------------------------------------------------
+// Grid of a kernel whose warps loop over tasks: the blocks of size bs that are
+// resident at once, at most nb (the grid of one task per warp).
+template <typename K>
+int resident_blocks(cgks_t* h, K kern, int bs, int64_t nb) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, 0) != cudaSuccess || occ < 1) {
+    (void)cudaGetLastError();
+    return (int)nb;
+  }
+  return (int)std::min<int64_t>(nb, (int64_t)occ * h->sms);
+}
+
 template <int DIM>
 void launch_recon(cgks_t* h, MeshDev& M) {
   LevelDev& L = M.lev[0];
-  k_recon<DIM><<<blocks_for(L.n, M.blk[B_RECON]), M.blk[B_RECON], 0, h->stream>>>(
+  const int bs = M.blk[B_RECON];
+  const int64_t nb = blocks_for(L.n, bs);  // 3-D: one thread per cell; 2-D: the kernel loops
+  k_recon<DIM><<<DIM == 2 ? resident_blocks(h, k_recon<DIM>, bs, nb) : (int)nb, bs, 0, h->stream>>>(
       M.fine, L.W, M.G, L.alpha, M.winf, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, h->cfg.weno_gamma_high,
       h->cfg.weno_eps, M.coef, L.dte, L.dti, M.cnt, M.coef_dw);
 }
@@ -426,21 +440,13 @@ void launch_flux(cgks_t* h, MeshDev& M, bool point = true, bool radius = true) {
   const PhysParams P = phys(h->cfg, DIM);
   // the FP64 kernel loops over its tasks: launch only the blocks that fit at
   // once; the double-word kernel takes one task per warp (the full grid)
-  auto resident = [&](auto kern) {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, 0) != cudaSuccess || occ < 1) {
-      (void)cudaGetLastError();
-      return nb;
-    }
-    return (int)std::min<int64_t>(nb, (int64_t)occ * h->sms);
-  };
   if (h->cfg.flux_precision == 1) {
     auto kern = point ? k_flux<DIM, true, dword> : k_flux<DIM, false, dword>;
     kern<<<nb, bs, 0, h->stream>>>(M.fine, M.coef_dw, L.dte, M.winf, phys_dword(P), P.gamma, M.Fface,
                                               M.Wface, M.aface, L.W, radius ? L.rface : nullptr);
   } else {
     auto kern = point ? k_flux<DIM, true, double> : k_flux<DIM, false, double>;
-    kern<<<resident(kern), bs, 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, P, P.gamma, M.Fface, M.Wface, M.aface,
+    kern<<<resident_blocks(h, kern, bs, nb), bs, 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, P, P.gamma, M.Fface, M.Wface, M.aface,
                                               L.W, radius ? L.rface : nullptr);
   }
 }

@@ -131,15 +131,14 @@ __device__ __forceinline__ void grad_poly(const S* c, const S* X, S* g) {
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __restrict__ W,
-                                                  const double* __restrict__ Gr, const double* __restrict__ alpha_prev,
-                                                  const double* __restrict__ winf, double gamma, double cfl_exp,
-                                                  double cfl_imp, double gam_hi, double weps, double* __restrict__ coef,
-                                                  double* __restrict__ dte, double* __restrict__ dti,
-                                                  Counters* __restrict__ cnt, dword* __restrict__ coef_dw) {
+__device__ __forceinline__ void recon_cell(DevFine M, const double* __restrict__ W,
+                                           const double* __restrict__ Gr, const double* __restrict__ alpha_prev,
+                                           const double* __restrict__ winf, double gamma, double cfl_exp,
+                                           double cfl_imp, double gam_hi, double weps, double* __restrict__ coef,
+                                           double* __restrict__ dte, double* __restrict__ dti,
+                                           Counters* __restrict__ cnt, dword* __restrict__ coef_dw, int c) {
   using D = Dims<DIM>;
   constexpr int NV = D::NV, NFC = D::NFC, NK = D::NK, NC = D::NC, NCOL = D::NCOL;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= M.n) return;
   const int n = M.n;
   double W0[NV];
@@ -356,6 +355,32 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int k = 0; k < NC; ++k) od[v * NC + k] = dword(P[v][k]);
+  }
+}
+
+// One thread per cell.  In 2-D the grid holds only the resident blocks and
+// warps loop over tasks of 32 cells, task t in block t mod gridDim.x, so that
+// every SM gets the same number of cells to within one task (a grid of one
+// thread per cell leaves a partial last wave on a few SMs).  3-D meshes span
+// hundreds of waves, and the loop would cost the 3-D kernel spills: there the
+// grid has one thread per cell.
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __restrict__ W,
+                                                  const double* __restrict__ Gr, const double* __restrict__ alpha_prev,
+                                                  const double* __restrict__ winf, double gamma, double cfl_exp,
+                                                  double cfl_imp, double gam_hi, double weps, double* __restrict__ coef,
+                                                  double* __restrict__ dte, double* __restrict__ dti,
+                                                  Counters* __restrict__ cnt, dword* __restrict__ coef_dw) {
+  if constexpr (DIM == 3) {
+    recon_cell<DIM>(M, W, Gr, alpha_prev, winf, gamma, cfl_exp, cfl_imp, gam_hi, weps, coef, dte, dti, cnt, coef_dw,
+                    blockIdx.x * blockDim.x + threadIdx.x);
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int ntask = (M.n + 31) / 32;
+    const int nwarp = gridDim.x * (blockDim.x >> 5);
+    for (int task = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; task < ntask; task += nwarp)
+      recon_cell<DIM>(M, W, Gr, alpha_prev, winf, gamma, cfl_exp, cfl_imp, gam_hi, weps, coef, dte, dti, cnt, coef_dw,
+                      task * 32 + lane);
   }
 }
 
