@@ -442,7 +442,39 @@ void launch_flux(cgks_t* h, MeshDev& M, bool point = true, bool radius = true) {
   // once; the double-word kernel takes one task per warp (the full grid)
   if (h->cfg.flux_precision == 1) {
     auto kern = point ? k_flux<DIM, true, dword> : k_flux<DIM, false, dword>;
-    kern<<<nb, bs, 0, h->stream>>>(M.fine, M.coef_dw, L.dte, M.winf, phys_dword(P), P.gamma, M.Fface,
+    // One task per warp.  When the grid's last wave of resident blocks is
+    // less than 95 % full (few waves: the 2-D meshes), take the block size of
+    // 2..8 warps that fills it best among those that keep at least 3/4 of the
+    // resident warps; with many waves the tail does not matter.
+    auto fill_of = [&](int w, int& occ, int64_t& blocks) {
+      occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * w, 0) != cudaSuccess || occ < 1) {
+        (void)cudaGetLastError();
+        return -1.0;
+      }
+      blocks = (warps + w - 1) / w;
+      const double waves = (double)blocks / ((double)occ * h->sms);
+      return waves / std::ceil(waves);
+    };
+    int bw = bs;
+    int64_t bn = nb;
+    int occ_def = 0;
+    int64_t blk_def = 0;
+    const int w_def = bs / 32;
+    double best = fill_of(w_def, occ_def, blk_def);
+    if (best >= 0.0 && best < 0.95) {
+      for (int w = 8; w >= 2; --w) {
+        int occ = 0;
+        int64_t blocks = 0;
+        const double fill = fill_of(w, occ, blocks);
+        if (fill > best + 1e-9 && 4 * occ * w >= 3 * occ_def * w_def) {
+          best = fill;
+          bw = 32 * w;
+          bn = blocks;
+        }
+      }
+    }
+    kern<<<(unsigned)bn, bw, 0, h->stream>>>(M.fine, M.coef_dw, L.dte, M.winf, phys_dword(P), P.gamma, M.Fface,
                                               M.Wface, M.aface, L.W, radius ? L.rface : nullptr);
   } else {
     auto kern = point ? k_flux<DIM, true, double> : k_flux<DIM, false, double>;
