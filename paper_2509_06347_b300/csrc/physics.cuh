@@ -573,7 +573,7 @@ __device__ S gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2], co
   }
   // time slopes from <A + a.u> = 0, with <psi (a.u)> of a full-space
   // Maxwellian given by the Euler-flux divergence of its slopes
-  S Al[NV], Ar[NV], Ac[NV];
+  S Al[NV], Ar[NV];
   {
     S s[NV];
     euler_flux_divergence_c<DIM, S>(P.gamma, Wl, pl.irho, Gl, s);
@@ -612,7 +612,6 @@ __device__ S gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2], co
     Fc[1] += pwc;
     Fc[NV - 1] += un * pwc;
   }
-  (void)Ac;
   // Collision time.  Euler: tau = C1 dt + C2 |dp| / (pl + pr) dt; Navier-Stokes
   // (Sec 2.1): the physical mu / p of the interface equilibrium in place of
   // C1 dt.  Either way tau / dt = a / b, and one reciprocal r = 1 / (a b) gives
@@ -658,7 +657,10 @@ __device__ S gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2], co
     kin_moments_c<DIM, 1, S>(m, T4, -(tau * T4 + T5), -tau * T4, a, Ak, fx);
     if (POINT) kin_moments_c<DIM, 0, S>(m, e, -e * (tau + dt), -e * tau, a, Ak, wx);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) { F[i] += rho * fx[i]; Wt[i] += rho * wx[i]; }
+    for (int i = 0; i < NV; ++i) {
+      F[i] += rho * fx[i];
+      if (POINT) Wt[i] += rho * wx[i];
+    }
   }
   return alpha;
 }
