@@ -66,8 +66,8 @@ enum { CGKS_TAG_WALL = 1, CGKS_TAG_FARFIELD = 2, CGKS_TAG_NOSLIP_WALL = 3, CGKS_
 
 typedef struct cgks_config {
   double gamma;           /* ratio of specific heats (1.4) */
-  double cfl_imp;         /* CFL of the implicit (DF-weighted) part, Sec 4.3 (10) */
-  double cfl_exp;         /* CFL of the explicit part and of the flux time step (0.5) */
+  double cfl_imp;         /* CFL of the implicit (DF-weighted) part, Sec 4.3 (10); > 0 */
+  double cfl_exp;         /* CFL of the explicit part and of the flux time step (0.5); > 0 */
   double tau_c1, tau_c2;  /* numerical collision time tau = c1 dt + c2 |dp|/(pl+pr) dt (0.01, 1);
                              with mu > 0 the c1 dt term gives way to mu / p; c1 > 0 and
                              c2 >= 0, finite, or cgks_create returns CGKS_ERR_ARG */
