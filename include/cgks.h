@@ -72,7 +72,8 @@ typedef struct cgks_config {
                              with mu > 0 the c1 dt term gives way to mu / p; c1 > 0 and
                              c2 >= 0, finite, or cgks_create returns CGKS_ERR_ARG */
   double weno_gamma_high; /* linear weight of the large HWENO stencil (0.95) */
-  double weno_eps;        /* WENO epsilon (1e-15) */
+  double weno_eps;        /* WENO epsilon (1e-15); > 0, it keeps the weights' denominators
+                             positive on flat stencils */
   double r_safety;        /* spectral-radius factor of the LU-SGS splitting (1) */
   int n_sweep_coarse;     /* LU-SGS smoothing steps per coarse level (6) */
   int n_pre, n_post;      /* fine pre/post smoothing steps (1, 0; only these are supported) */

@@ -858,7 +858,8 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
       (h->cfg.df_relax < 0 || h->cfg.df_relax > 2) || (h->cfg.df_prolong != 0 && h->cfg.df_prolong != 1) ||
       !(h->cfg.relax_beta >= 0.0 && h->cfg.relax_beta <= 1.0) || !(h->cfg.mu >= 0.0 && h->cfg.mu < 1e300) ||
       !(h->cfg.tau_c1 > 0.0 && h->cfg.tau_c1 < 1e300) || !(h->cfg.tau_c2 >= 0.0 && h->cfg.tau_c2 < 1e300) ||
-      !(h->cfg.cfl_imp > 0.0 && h->cfg.cfl_imp < 1e300) || !(h->cfg.cfl_exp > 0.0 && h->cfg.cfl_exp < 1e300)) {
+      !(h->cfg.cfl_imp > 0.0 && h->cfg.cfl_imp < 1e300) || !(h->cfg.cfl_exp > 0.0 && h->cfg.cfl_exp < 1e300) ||
+      !(h->cfg.weno_eps > 0.0 && h->cfg.weno_eps < 1e300)) {
     delete h;
     return CGKS_ERR_ARG;
   }

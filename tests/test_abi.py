@@ -37,7 +37,7 @@ def test_default_config_values():
 @pytest.mark.parametrize("kw", [dict(tau_c1=0.0), dict(tau_c1=float("nan")), dict(tau_c2=-1.0), dict(mu=-1.0),
                                 dict(gamma=1.0), dict(df_relax=3), dict(df_relax=2, relax_beta=1.5),
                                 dict(n_pre=2), dict(n_sweep_coarse=0), dict(flux_precision=2),
-                                dict(cfl_imp=0.0), dict(cfl_exp=-0.5)])
+                                dict(cfl_imp=0.0), dict(cfl_exp=-0.5), dict(weno_eps=0.0)])
 def test_invalid_config_rejected_before_any_device_call(kw):
     """cgks_create checks the configuration before it touches the device, so
     every rejection holds on a host without a GPU."""
