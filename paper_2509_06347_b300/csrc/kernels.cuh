@@ -549,6 +549,97 @@ __device__ __forceinline__ void flux_task(const DevFine& M, const S* __restrict_
   }
 }
 
+// All NGP Gauss points of face f in one lane, summed in the order the lane
+// groups of flux_task use.  For the 3-point faces of 3-D meshes: 32 faces per
+// warp use every lane, where 3 lanes per face leave 2 of 32 idle, and the
+// per-face work (indices, frame, spectral radius) runs on every lane.
+template <int DIM, bool POINT, typename S>
+__device__ __forceinline__ void flux_face(const DevFine& M, const S* __restrict__ coef, const double* __restrict__ dte,
+                                          const double* __restrict__ winf, const PhysT<S>& P, double gamma,
+                                          double* __restrict__ Fface, double* __restrict__ Wface,
+                                          double* __restrict__ aface, const double* __restrict__ Wc,
+                                          double* __restrict__ rface, int f) {
+  using D = Dims<DIM>;
+  constexpr int NV = D::NV, NC = D::NC, NGP = D::NGP;
+  if (f >= M.nf) return;
+  const int L = M.fL[f], R = M.fR[f];
+  S n[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) n[d] = S(M.fn[(size_t)f * DIM + d]);
+  const Frame<DIM, S> fr = make_frame<DIM, S>(n);
+  double dt = dte[L];
+  if (R >= 0) dt = fmin(dt, dte[R]);
+  const S w = S(M.fS[f] * (1.0 / NGP));  // equal Gauss weights on every face
+  S Fs[NV], Ws[NV], af = S(1.0);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { Fs[v] = S(0.0); Ws[v] = S(0.0); }
+#pragma unroll 1
+  for (int g = 0; g < NGP; ++g) {
+    S Wl[NV], gl[NV][DIM], Wr[NV], gr[NV][DIM];
+    {
+      const double* X = M.XL + ((size_t)f * NGP + g) * DIM;
+      S x[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) x[d] = S(X[d]);
+      const S* c = coef + (size_t)L * NV * NC;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) eval_grad_c<DIM, S>(c + v * NC, x, Wl[v], gl[v]);
+    }
+    if (R >= 0) {
+      const double* X = M.XR + ((size_t)f * NGP + g) * DIM;
+      S x[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) x[d] = S(X[d]);
+      const S* c = coef + (size_t)R * NV * NC;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) eval_grad_c<DIM, S>(c + v * NC, x, Wr[v], gr[v]);
+    } else {
+      const int tag = M.ftag[f];
+      const double* wd = winf + NV * (M.grp ? M.grp[L] : 0);
+      S wi[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) wi[v] = S(wd[v]);
+      ghost_state<DIM, S>(tag, wi, n, Wl, Wr, P.gamma);
+      ghost_grad<DIM, S>(tag, wi, n, gl, gr);
+    }
+    S wl[NV], wr[NV], Gl[DIM][NV], Gr[DIM][NV], Fl[NV], Wt[NV];
+    to_local<DIM, S>(fr, Wl, wl);
+    to_local<DIM, S>(fr, Wr, wr);
+    grad_to_local<DIM, S>(fr, gl, Gl);
+    grad_to_local<DIM, S>(fr, gr, Gr);
+    af *= gks_flux<DIM, POINT, S>(P, wl, Gl, wr, Gr, S(dt), Fl, Wt);
+    S Fg[NV], Wg[NV];
+    to_global<DIM, S>(fr, Fl, Fg);
+    to_global<DIM, S>(fr, Wt, Wg);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Fs[v] += w * Fg[v];
+      if (POINT) Ws[v] += w * Wg[v];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Fface[(size_t)f * NV + v] = static_cast<double>(Fs[v]);
+    if (POINT) Wface[(size_t)f * NV + v] = static_cast<double>(Ws[v]);
+  }
+  aface[f] = static_cast<double>(af);
+  if (rface) {
+    // spectral radius of the LU-SGS splitting at the mean of the cell means
+    double nd[DIM], WL[NV], WR[NV];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) nd[d] = M.fn[(size_t)f * DIM + d];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) WL[v] = Wc[(size_t)L * NV + v];
+    if (R >= 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) WR[v] = Wc[(size_t)R * NV + v];
+    } else {
+      ghost_state<DIM>(M.ftag[f], winf + NV * (M.grp ? M.grp[L] : 0), nd, WL, WR, gamma);
+    }
+    rface[f] = spectral_radius<DIM, double>(gamma, WL, WR, nd);
+  }
+}
+
 // Gas-kinetic face flux.  S = double: FP64; S = dword: the same arithmetic in
 // double-word on the FP32 pipes (coefficients read as double-word, geometry and
 // time step converted once per Gauss point, results returned in FP64).
@@ -570,6 +661,12 @@ __global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(De
   if constexpr (OutOfLine<S>::value) {
     const int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (task < ntask) flux_task<DIM, POINT, S>(M, coef, dte, winf, P, gamma, Fface, Wface, aface, Wc, rface, task, lane);
+  } else if constexpr (DIM == 3) {
+    // one face per lane, tasks of 32 faces
+    const int nwarp = gridDim.x * (blockDim.x >> 5);
+    const int nt = (M.nf + 31) / 32;
+    for (int task = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; task < nt; task += nwarp)
+      flux_face<DIM, POINT, S>(M, coef, dte, winf, P, gamma, Fface, Wface, aface, Wc, rface, task * 32 + lane);
   } else {
     const int nwarp = gridDim.x * (blockDim.x >> 5);
     for (int task = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; task < ntask; task += nwarp)
