@@ -344,14 +344,23 @@ int cgks_autotune(cgks_t* h, int mesh_id, int* blocks_out);
  *   W_dev [n_level][nv] (device, original coarse-cell order, read),
  *   R_dev [n_level][nv] (device, original order, written): outward KFVS flux
  *   of each coarse cell.
+ * Stream contract: both kernels are enqueued on the context's stream and the
+ * call returns without synchronising.  W_dev must be complete, and nothing
+ * else may still be writing R_dev, when that stream reaches them; a caller
+ * whose buffers come from work on another stream (e.g. torch's current stream
+ * when the context uses its private stream) must order the two, for instance
+ * by creating the context on torch's current stream or by synchronising first.
  * The per-face fluxes go to a fixed device array of 131,072 faces x 5 FP64
  * values (5 MiB) that every GPU loading the library holds until process exit;
- * levels with more faces are rejected with CGKS_ERR_ARG.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), so make
- * the first call on each device before any stream capture.  All calls share
- * the array: calls that overlap on the GPU (other streams, other contexts of
- * this library) race and must be serialised by the caller.  Work is enqueued on
- * the context's stream without synchronising.
+ * levels with more faces are rejected with CGKS_ERR_ARG.  The call runs on the
+ * device that was current at cgks_create (it makes that device current for
+ * its duration and then restores the caller's).  The first call on each
+ * context looks up that array's device address (cudaGetSymbolAddress), so make
+ * the first call on a context before any stream capture.  The address is kept
+ * by the context; after a device reset the context is invalid, like all of its
+ * device buffers, and a new context must be created.  All calls share the
+ * array: calls that overlap on the GPU (other streams, other contexts of this
+ * library) race and must be serialised by the caller.
  */
 int cgks_residual_coarse_noalloc(cgks_t* h, int mesh_id, int level, const double* W_dev, double* R_dev);
 

@@ -3,10 +3,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <map>
-#include <mutex>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -185,6 +185,8 @@ struct cgks_ctx {
   std::string err;
   std::vector<std::unique_ptr<cgks::DBuf>> scratch;  // point-evaluation helpers
   int sms = 148;                                      // SM count of the device (set at creation)
+  int device = 0;                                     // device current at creation; all work runs there
+  double* noalloc_scratch = nullptr;                  // device address of the no-allocation scratch array
   // pinned host buffer for the small per-chunk reads of cgks_vcycle
   double* pin = nullptr;
   size_t pin_cap = 0;
@@ -865,9 +867,11 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
   }
   {
     int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
-      h->sms = sms;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      h->device = dev;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+        h->sms = sms;
+    }
   }
   if (stream) {
     h->stream = (cudaStream_t)stream;
@@ -2045,11 +2049,6 @@ namespace noalloc {
 constexpr int kNoAllocMaxFaces = 131072;
 static __device__ __align__(256) double g_noalloc_face_flux[kNoAllocMaxFaces * 5];
 
-// device address of g_noalloc_face_flux, looked up once per device
-constexpr int kMaxDevices = 64;
-static double* g_noalloc_ptr[kMaxDevices] = {nullptr};
-static std::mutex g_noalloc_mu;
-
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_noalloc_face(FaceSet Fs, const int* __restrict__ iperm,
                                                          const double* __restrict__ W_orig,
@@ -2106,6 +2105,14 @@ int noalloc_fail(cgks_t* h, int code, const char* msg) {
   return code;
 }
 
+// Error message naming the CUDA error, composed in a fixed buffer so that
+// reporting a failure allocates nothing either.
+int noalloc_cuda_fail(cgks_t* h, const char* what, cudaError_t e) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "cgks_residual_coarse_noalloc: %s: %s", what, cudaGetErrorString(e));
+  return noalloc_fail(h, CGKS_ERR_CUDA, buf);
+}
+
 }  // namespace noalloc
 }  // namespace cgks
 
@@ -2126,31 +2133,46 @@ extern "C" int cgks_residual_coarse_noalloc(cgks_t* h, int mesh_id, int level, c
     return noalloc_fail(h, CGKS_ERR_ARG,
                         "cgks_residual_coarse_noalloc: the level has more than 131072 faces, the capacity "
                         "of the fixed face-flux buffer; use cgks_residual instead");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return noalloc_fail(h, CGKS_ERR_CUDA, "cudaGetDevice failed or device index too large");
-  double* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      // first call on this device: resolve the array's device address with the device current
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_face_flux);
-      if (e != cudaSuccess) return noalloc_fail(h, CGKS_ERR_CUDA, "cudaGetSymbolAddress failed");
-      g_noalloc_ptr[dev] = (double*)p;
-    }
-    scratch = g_noalloc_ptr[dev];
+  // All work runs on the context's device: make it current for this call and
+  // put the caller's device back on every return path.
+  int prev_dev = h->device;
+  if (cudaGetDevice(&prev_dev) != cudaSuccess) prev_dev = h->device;
+  if (prev_dev != h->device) {
+    const cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return noalloc_cuda_fail(h, "cudaSetDevice to the context's device failed", e);
   }
+  struct RestoreDevice {
+    int prev, cur;
+    ~RestoreDevice() {
+      if (prev != cur) cudaSetDevice(prev);
+    }
+  } restore{prev_dev, h->device};
+  if (!h->noalloc_scratch) {
+    // First call on this context: the array's device address on the context's
+    // device.  A context never outlives a device reset (its own buffers would
+    // be gone too), so the address is looked up again by any new context.
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_face_flux);
+    if (e != cudaSuccess) return noalloc_cuda_fail(h, "cudaGetSymbolAddress failed", e);
+    h->noalloc_scratch = (double*)p;
+  }
+  double* scratch = h->noalloc_scratch;
   // every face entry the cell kernel reads is written by the face kernel first,
   // so the buffer needs no clearing between calls
   const PhysParams p = phys(h->cfg, M.dim);
-  if (M.dim == 2) {
+  // a non-sticky error left by earlier, unrelated work on this thread is not
+  // this call's failure: clear it so that the checks below see only these launches
+  (void)cudaGetLastError();
+  cudaError_t e;
+  if (M.dim == 2)
     k_noalloc_face<2><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.iperm, W_dev, M.winf, p, scratch);
-    k_noalloc_cell<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.iperm, scratch, R_dev);
-  } else {
+  else
     k_noalloc_face<3><<<blocks_for(L.faces.nf), kBlock, 0, h->stream>>>(L.faces, L.iperm, W_dev, M.winf, p, scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_cuda_fail(h, "face-flux kernel launch failed", e);
+  if (M.dim == 2)
+    k_noalloc_cell<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.iperm, scratch, R_dev);
+  else
     k_noalloc_cell<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.topo, L.iperm, scratch, R_dev);
-  }
-  if (cudaGetLastError() != cudaSuccess) return noalloc_fail(h, CGKS_ERR_CUDA, "kernel launch failed");
+  if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_cuda_fail(h, "cell-sum kernel launch failed", e);
   return CGKS_OK;
 }
