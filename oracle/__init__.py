@@ -10,7 +10,9 @@ Parity status per function (pins live in tests/test_oracle_*.py):
                                                      velocity/time quadrature, symmetry)
   KFVS flux, DF factor, Euler flux ................. pinned (closed forms, limits)
   reconstruction (p2, p1, weights) ................. pinned (quadratic exactness,
-                                                     constants, equal-beta limit)
+                                                     constants; weights: equal-beta
+                                                     limit P = p2, hand-worked cases,
+                                                     indicators by independent quadrature)
   fine residual .................................... pinned (free stream, conservation)
   LU-SGS ........................................... pinned (dense block factorisation,
                                                      alpha = 0 explicit limit)
@@ -76,6 +78,7 @@ def lib():
             "om_get_neighbors": (None, [P, I, ip, ip]),
             "om_gks_point": (None, [I, dp, dp, dp, dp, dp, D, dp, dp, dp]),
             "om_kfvs_point": (None, [I, D, dp, dp, dp]),
+            "om_hweno_combine": (None, [I, D, D, D, D, dp, dp, dp]),
             "om_df_point": (D, [I, D, dp, dp]),
             "om_euler_flux": (None, [I, D, dp, dp, dp]),
             "om_reconstruct": (LL, [P, dp, dp, dp, dp, dp]),
@@ -293,6 +296,16 @@ def gks_point(dim, cfg, Wl, dWl, Wr, dWr, dt):
              Ar=take(5)[:nv], Wc=take(5)[:nv], ac=take(15).reshape(3, 5)[:dim, :nv], Ac=take(5)[:nv],
              tau=take(1)[0])
     return F, Wt, d
+
+
+def hweno_combine(b1, b2, gamma_high, eps, c1, c2):
+    """Nonlinear HWENO combination of the sub-stencil linear polynomial c1 and
+    the large-stencil quadratic c2 (coefficient vectors of equal length) with
+    smoothness indicators b1, b2 (Sec 3.3, reading R9)."""
+    c1, c2 = _c(c1), _c(c2)
+    out = np.zeros_like(c1)
+    lib().om_hweno_combine(c1.size, float(b1), float(b2), float(gamma_high), float(eps), c1, c2, out)
+    return out
 
 
 def kfvs_point(dim, gamma, Wl, Wr):

@@ -998,6 +998,22 @@ static void kmulti(int dim, int idx, int* p, int* q) {
 
 /* reconstruct cell c: coefficients out[nv][ncoef]; returns 1 if the positivity
  * fallback was taken */
+/* Nonlinear combination of the large-stencil quadratic p2 (coefficients c2)
+ * and the Green-Gauss linear p1 (c1), Sec 3.3 with the weights deferred by the
+ * paper (reading: WENO-Z type with one large and one sub stencil):
+ *   tau = |b2 - b1|,  w~H = gH (1 + tau/(b2+eps)),  w~L = gL (1 + tau/(b1+eps)),
+ *   (wH, wL) = (w~H, w~L) / (w~H + w~L),  P = (wH/gH)(p2 - gL p1) + wL p1,
+ * with gL = 1 - gH and b1, b2 the smoothness indicators of p1 and p2. */
+static void hweno_combine(int nco, double b1, double b2, double gh, double eps, const double* c1,
+                          const double* c2, double* out) {
+  double gl = 1.0 - gh;
+  double tz = fabs(b2 - b1);
+  double wh = gh * (1.0 + tz / (b2 + eps)), wl = gl * (1.0 + tz / (b1 + eps));
+  double ws = wh + wl;
+  wh /= ws; wl /= ws;
+  for (int i = 0; i < nco; ++i) out[i] = wh / gh * (c2[i] - gl * c1[i]) + wl * c1[i];
+}
+
 static int reconstruct_cell(const OMesh* M, const OCfg* cfg, const double* W, const double* G,
                             const double* alpha_prev, int c, double* out, int* rank_fallback) {
   const OLevel* L = &M->lev[0];
@@ -1093,13 +1109,7 @@ static int reconstruct_cell(const OMesh* M, const OCfg* cfg, const double* W, co
       }
       for (int d = 0; d < dim; ++d) for (int e = d; e < dim; ++e) b2 += beta_scale2 * V0 * Hs[d][e] * Hs[d][e];
     }
-    /* nonlinear weights (reading: WENO-Z type with one large and one sub stencil) */
-    double gh = cfg->weno_gh, gl = 1.0 - gh, eps = cfg->weno_eps;
-    double tz = fabs(b2 - b1);
-    double wh = gh * (1.0 + tz / (b2 + eps)), wl = gl * (1.0 + tz / (b1 + eps));
-    double ws = wh + wl;
-    wh /= ws; wl /= ws;
-    for (int i = 0; i < nco; ++i) out[v * nco + i] = wh / gh * (c2[i] - gl * c1[i]) + wl * c1[i];
+    hweno_combine(nco, b1, b2, cfg->weno_gh, cfg->weno_eps, c1, c2, out + v * nco);
   }
   /* positivity: density and pressure at every face Gauss point of the cell */
   double pts[MAXF * MAXG * MAXD];
@@ -1476,6 +1486,8 @@ void om_gks_point(int dim, const double* cfgv, const double* Wl, const double* d
   }
 }
 void om_kfvs_point(int dim, double gamma, const double* Wl, const double* Wr, double* F) { kfvs_point(dim, gamma, Wl, Wr, F); }
+void om_hweno_combine(int nco, double b1, double b2, double gh, double eps, const double* c1, const double* c2,
+                      double* out) { hweno_combine(nco, b1, b2, gh, eps, c1, c2, out); }
 double om_df_point(int dim, double gamma, const double* Wl, const double* Wr) { return df_point(dim, gamma, Wl, Wr); }
 void om_euler_flux(int dim, double gamma, const double* W, const double* n, double* T) { euler_flux(dim, gamma, W, n, T); }
 
