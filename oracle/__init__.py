@@ -40,11 +40,13 @@ DEFAULTS = dict(gamma=1.4, cfl_imp=10.0, cfl_exp=0.5, tau_c1=0.01, tau_c2=1.0,
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction)."""
+    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction;
+    OpenMP over independent cells and faces, with every sum in a fixed order so
+    that results do not depend on the thread count)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
                                "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -92,12 +94,25 @@ def lib():
             "om_vcycle": (I, [P, dp, dp, dp, dp, I, dp, lp]),
             "om_prolong": (None, [P, I, dp, dp, dp, dp, dp]),
             "om_ghost_state": (None, [I, dp, I, dp, dp, dp]),
+            "om_set_threads": (None, [I]),
+            "om_get_threads": (I, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
             fn.restype = res
             fn.argtypes = args
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (results are the same for any
+    count); returns the count now in effect."""
+    lib().om_set_threads(int(n))
+    return int(lib().om_get_threads())
+
+
+def get_threads() -> int:
+    return int(lib().om_get_threads())
 
 
 def cfg_vector(dim: int, winf=None, **over) -> np.ndarray:

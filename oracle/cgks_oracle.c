@@ -6,6 +6,9 @@
  * CUDA path: geometry, faces, colouring, reconstruction, the gas-kinetic flux,
  * KFVS, LU-SGS and the multigrid cycle are all written here from the paper
  * (arXiv 2509.06347) in its order and notation, without blocking or fusion.
+ * Loops over independent cells and faces may run on OpenMP threads; every sum
+ * over cells or faces is still formed serially in a fixed order, so results
+ * are the same for any thread count.
  *
  * The gas-kinetic moments are taken the long way: the distribution function is
  * held as a polynomial in (u, v, w, xi^2) times a (half-)Maxwellian and every
@@ -30,6 +33,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define MAXD 3
 #define MAXV 5
@@ -1133,6 +1139,7 @@ static int reconstruct_cell(const OMesh* M, const OCfg* cfg, const double* W, co
 static void time_steps(const OMesh* M, int lev, const OCfg* cfg, const double* W, double* dte, double* dti) {
   const OLevel* L = &M->lev[lev];
   int dim = M->dim, nv = M->nv;
+#pragma omp parallel for schedule(static)
   for (int c = 0; c < L->n_cells; ++c) {
     const double* w = W + c * nv;
     double cs = sqrt(cfg->gamma * pressure(dim, cfg->gamma, w) / w[0]);
@@ -1161,16 +1168,25 @@ static void fine_residual(const OMesh* M, const OCfg* cfg, const double* W, cons
   time_steps(M, 0, cfg, W, dtl, dti);
   if (dte) memcpy(dte, dtl, n * sizeof(double));
   double* P = malloc((size_t)n * nv * nco * sizeof(double));
-  for (int c = 0; c < n; ++c) {
-    int rf = 0;
-    int bad = reconstruct_cell(M, cfg, W, G, alpha_prev, c, P + (size_t)c * nv * nco, &rf);
-    if (st) { st->recon_fallback += bad; st->rank_fallback += rf; }
-  }
+  int* bad = calloc(n, sizeof(int));
+  int* rf = calloc(n, sizeof(int));
+  /* cells are independent: OpenMP threads may share them out */
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int c = 0; c < n; ++c) bad[c] = reconstruct_cell(M, cfg, W, G, alpha_prev, c, P + (size_t)c * nv * nco, &rf[c]);
+  if (st) for (int c = 0; c < n; ++c) { st->recon_fallback += bad[c]; st->rank_fallback += rf[c]; }
+  free(bad); free(rf);
   for (int i = 0; i < n * nv; ++i) R[i] = 0.0;
   for (int i = 0; i < n * nv * dim; ++i) Gnew[i] = 0.0;
   for (int c = 0; c < n; ++c) alpha[c] = 1.0;
   double wq = 1.0 / M->ngp;
-  for (int f = 0; f < L->n_faces; ++f) {
+  /* per-face results (faces are independent), then summed into the cells in
+     face order, so the sums do not depend on the thread count */
+  int nf = L->n_faces;
+  double* FsA = malloc((size_t)nf * nv * sizeof(double));
+  double* WsA = malloc((size_t)nf * nv * sizeof(double));
+  double* afA = malloc((size_t)nf * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int f = 0; f < nf; ++f) {
     int cl = L->fL[f], cr = L->fR[f], tag = L->ftag[f];
     const double* n_ = L->fn + f * dim;
     double Rm[MAXD * MAXD];
@@ -1212,6 +1228,15 @@ static void fine_residual(const OMesh* M, const OCfg* cfg, const double* W, cons
       for (int v = 0; v < nv; ++v) { Fs[v] += wq * Fg[v]; Ws[v] += wq * Wg[v]; }
       af *= df_point(dim, cfg->gamma, wl, wr);
     }
+    for (int v = 0; v < nv; ++v) { FsA[(size_t)f * nv + v] = Fs[v]; WsA[(size_t)f * nv + v] = Ws[v]; }
+    afA[f] = af;
+  }
+  for (int f = 0; f < nf; ++f) {
+    int cl = L->fL[f], cr = L->fR[f];
+    const double* n_ = L->fn + f * dim;
+    const double* Fs = FsA + (size_t)f * nv;
+    const double* Ws = WsA + (size_t)f * nv;
+    double af = afA[f];
     double S = L->fS[f];
     for (int v = 0; v < nv; ++v) {
       R[cl * nv + v] += S * Fs[v];
@@ -1226,6 +1251,7 @@ static void fine_residual(const OMesh* M, const OCfg* cfg, const double* W, cons
       alpha[cr] *= af;
     }
   }
+  free(FsA); free(WsA); free(afA);
   free(P); free(dtl);
 }
 
@@ -1234,22 +1260,30 @@ static void kfvs_residual(const OMesh* M, int lev, const OCfg* cfg, const double
   const OLevel* L = &M->lev[lev];
   int dim = M->dim, nv = M->nv;
   for (int i = 0; i < L->n_cells * nv; ++i) R[i] = 0.0;
+  /* face fluxes (independent), then summed into the cells in face order */
+  double* FgA = malloc((size_t)L->n_faces * nv * sizeof(double));
+#pragma omp parallel for schedule(static)
   for (int f = 0; f < L->n_faces; ++f) {
     int cl = L->fL[f], cr = L->fR[f];
     const double* n_ = L->fn + f * dim;
-    double Rm[MAXD * MAXD], Wr[MAXV], wl[MAXV], wr[MAXV], Fl[MAXV], Fg[MAXV];
+    double Rm[MAXD * MAXD], Wr[MAXV], wl[MAXV], wr[MAXV], Fl[MAXV];
     frame(dim, n_, Rm);
     if (cr >= 0) memcpy(Wr, W + cr * nv, nv * sizeof(double));
     else ghost_mean(cfg, dim, L->ftag[f], n_, W + cl * nv, Wr);
     rot_to(dim, Rm, W + cl * nv, wl);
     rot_to(dim, Rm, Wr, wr);
     kfvs_point(dim, cfg->gamma, wl, wr, Fl);
-    rot_from(dim, Rm, Fl, Fg);
+    rot_from(dim, Rm, Fl, FgA + (size_t)f * nv);
+  }
+  for (int f = 0; f < L->n_faces; ++f) {
+    int cl = L->fL[f], cr = L->fR[f];
+    const double* Fg = FgA + (size_t)f * nv;
     for (int v = 0; v < nv; ++v) {
       R[cl * nv + v] += L->fS[f] * Fg[v];
       if (cr >= 0) R[cr * nv + v] -= L->fS[f] * Fg[v];
     }
   }
+  free(FgA);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1271,13 +1305,19 @@ static void apply_update(int dim, double gamma, double* W, const double* dW, OSt
   for (int it = 0; it <= 10; ++it) {
     for (int v = 0; v < nv; ++v) Wn[v] = W[v] + s * dW[v];
     if (Wn[0] > 0.0 && pressure(dim, gamma, Wn) > 0.0) {
-      if (it > 0 && st) st->update_halved++;
+      if (it > 0 && st) {
+#pragma omp atomic update
+        st->update_halved++;
+      }
       for (int v = 0; v < nv; ++v) W[v] = Wn[v];
       return;
     }
     s *= 0.5;
   }
-  if (st) st->update_zeroed++;
+  if (st) {
+#pragma omp atomic update
+    st->update_zeroed++;
+  }
 }
 
 /* One forward + backward sweep for  D dW + 1/2 alpha sum S [dT - r dW] = rhs
@@ -1290,6 +1330,7 @@ static void lusgs(const OMesh* M, int lev, const OCfg* cfg, double* W, const dou
   double* dWs = calloc((size_t)n * nv, sizeof(double));
   double* dW = calloc((size_t)n * nv, sizeof(double));
   double* r = malloc(L->n_faces * sizeof(double));
+#pragma omp parallel for schedule(static)
   for (int f = 0; f < L->n_faces; ++f) {
     int cl = L->fL[f], cr = L->fR[f];
     double Wg[MAXV];
@@ -1298,6 +1339,7 @@ static void lusgs(const OMesh* M, int lev, const OCfg* cfg, double* W, const dou
     else { ghost_mean(cfg, dim, L->ftag[f], L->fn + f * dim, W + cl * nv, Wg); Wj = Wg; }
     r[f] = spectral_radius(dim, cfg->gamma, cfg->r_safety, W + cl * nv, Wj, L->fn + f * dim);
   }
+#pragma omp parallel for schedule(static)
   for (int c = 0; c < n; ++c) {
     double s = 0;
     for (int k = 0; k < L->cnf[c]; ++k) { int f = L->cface[c * L->maxnf + k]; s += L->fS[f] * r[f]; }
@@ -1310,6 +1352,8 @@ static void lusgs(const OMesh* M, int lev, const OCfg* cfg, double* W, const dou
     int nc = L->n_colors;
     for (int ci = 0; ci < nc; ++ci) {
       int col = pass == 0 ? ci + 1 : nc - ci;
+      /* the cells of one colour are independent of each other */
+#pragma omp parallel for schedule(static)
       for (int c = 0; c < n; ++c) {
         if (L->color[c] != col) continue;
         double sum[MAXV] = {0};
@@ -1333,6 +1377,7 @@ static void lusgs(const OMesh* M, int lev, const OCfg* cfg, double* W, const dou
       }
     }
   }
+#pragma omp parallel for schedule(static)
   for (int c = 0; c < n; ++c) apply_update(dim, cfg->gamma, W + c * nv, dW + c * nv, st);
   if (dW_out) memcpy(dW_out, dW, (size_t)n * nv * sizeof(double));
   free(D); free(dWs); free(dW); free(r);
@@ -1387,6 +1432,7 @@ static void prolong(const OMesh* M, int lev, const OCfg* cfg, double* Wf, const 
                     const double* Wc, const double* Wc0, OStats* st) {
   const OLevel* F = &M->lev[lev];
   int nv = M->nv;
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < F->n_cells; ++i) {
     int I = F->parent[i];
     double d[MAXV];
@@ -1411,6 +1457,22 @@ static void norms_of(const OMesh* M, int lev, const double* R, double* out /* [n
 /* ------------------------------------------------------------------------ */
 static char g_err[256];
 const char* om_last_error(void) { return g_err; }
+/* threads of the OpenMP loops over independent cells and faces (results do not
+ * depend on it: every sum over cells or faces is formed in a fixed order) */
+void om_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+int om_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 void* om_create(int dim, int n_cells, const int* cell_nodes, const double* cell_xyz, int n_bf,
                 const int* bface_nodes, const int* bface_tag) {
