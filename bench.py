@@ -166,37 +166,50 @@ def measured_peaks():
 
 # ----------------------------------------------------------------------------
 def cpu_baseline(mesh, w, W0, budget_s: float = 25.0, what: str = "the"):
-    """The oracle as it stands, single-threaded on the host: whole V-cycles of
-    the workload until about budget_s seconds have been spent."""
+    """The oracle as it stands on the host: whole V-cycles of the workload, on
+    one thread and then on every host core (its OpenMP loops over independent
+    cells and faces; results are the same for any thread count), each for
+    about half of budget_s seconds.  value is the all-cores rate."""
     import oracle
     t0 = time.perf_counter()
     om = oracle.OracleMesh(mesh)
     setup = time.perf_counter() - t0
     n, dim = len(W0), int(mesh["dim"])
     cfg = oracle.cfg_vector(dim, winf=w)
-    W, G, a = W0.copy(), np.zeros((n, dim + 2, dim)), np.ones(n)
-    cycles, spent = 0, 0.0
-    while cycles == 0 or spent < budget_s * 0.5:
-        t0 = time.perf_counter()
-        out = om.vcycle(cfg, W, G, a, 1)
-        spent += time.perf_counter() - t0
-        W, G, a = out["W"], out["grad"], out["alpha"]
-        cycles += 1
-    return {"value": n * cycles / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{cycles} whole V-cycle(s) of {what} {n}-cell workload from the free stream "
-                      f"(FP64, single thread; mesh setup {setup:.1f} s not timed)"}
+    nproc = os.cpu_count() or 1
+
+    def timed(threads, budget):
+        used = oracle.set_threads(threads)
+        W, G, a = W0.copy(), np.zeros((n, dim + 2, dim)), np.ones(n)
+        cycles, spent = 0, 0.0
+        while cycles == 0 or spent < budget:
+            t0 = time.perf_counter()
+            out = om.vcycle(cfg, W, G, a, 1)
+            spent += time.perf_counter() - t0
+            W, G, a = out["W"], out["grad"], out["alpha"]
+            cycles += 1
+        return n * cycles / spent, cycles, used
+
+    one, c1, _ = timed(1, budget_s * 0.25)
+    allc, ca, used = timed(nproc, budget_s * 0.25)
+    return {"value": allc, "unit": UNIT, "cores": used, "nproc": nproc, "kind": "oracle",
+            "single_thread_value": one,
+            "sample": f"{what} {n}-cell workload from the free stream, FP64: {ca} whole V-cycle(s) on "
+                      f"{used} OpenMP threads (value) and {c1} on one thread (single_thread_value); "
+                      f"mesh setup {setup:.1f} s not timed"}
 
 
 def run_reference(args):
-    """Reference arm: the oracle (plain FP64 C, one host thread) on the same
-    workload and metric; each step is one whole V-cycle, capped so the run
-    stays within a few minutes."""
+    """Reference arm: the oracle (plain FP64 C, OpenMP over independent cells
+    and faces on every host core) on the same workload and metric; each step
+    is one whole V-cycle, capped so the run stays within a few minutes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     mesh, w, W0 = workload()
     om = oracle.OracleMesh(mesh)
+    cores = oracle.set_threads(os.cpu_count() or 1)
     n = len(W0)
     cfg = oracle.cfg_vector(2, winf=w)
     W, G, a = W0.copy(), np.zeros((n, 4, 2)), np.ones(n)
@@ -217,7 +230,7 @@ def run_reference(args):
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": n, "levels": 3, "mode": "fp64 (oracle)"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "nproc": os.cpu_count(), "kind": "oracle",
                              "sample": f"{steps} V-cycles after {warm} warm-up cycles "
                                        f"(capped from --steps {args.steps} to stay within minutes)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -98,6 +98,14 @@ typedef struct cgks_config {
                                 C2 |dp|/(pl+pr) dt); mu > 0 the Navier-Stokes equations with
                                 Pr = 1 (Sec 2.1): tau = mu / p + C2 |dp|/(pl+pr) dt on the fine
                                 level, p that of the interface equilibrium (0) */
+  double slope_relax;        /* under-relaxation of the pseudo-time slope update: slopes <-
+                                slopes + slope_relax (DF grad_new - slopes); 1 replaces them
+                                (Sec 2.4, 3.3).  A steady state is a fixed point for any
+                                value in (0, 1] (1) */
+  double alpha_relax;        /* under-relaxation of the stored DF factor: DF <- DF +
+                                alpha_relax (prod of the Gauss-point factors - DF); 1 takes
+                                the product (Sec 3.3).  Same fixed points for any value in
+                                (0, 1] (1) */
 } cgks_config;
 
 typedef struct cgks_ctx cgks_t;
@@ -185,15 +193,27 @@ int cgks_get_hierarchy(cgks_t* h, int mesh_id, int level, int32_t* order, int32_
 /* Colour (1..Nc) of every cell of a level, original order, host int32 [n]. */
 int cgks_get_coloring(cgks_t* h, int mesh_id, int level, int32_t* colors);
 
-/* Free-stream conservative state [nv] (host) used by far-field ghosts. */
+/* Free-stream state for the far-field boundaries of Sec 6 (free stream on
+ * inflow faces, interior state on outflow faces, or the characteristic state
+ * of the Riemann invariants): w [nv] (host, copied) in conservative variables
+ * (rho, rho u, rho v, [rho w], rho E), the unknowns of Sec 2.2.  Replaces the
+ * previous free stream of the mesh; after cgks_set_groups it replaces member
+ * 0's only.  CGKS_ERR_ARG for a null pointer or unknown mesh. */
 int cgks_set_freestream(cgks_t* h, int mesh_id, const double* w);
 
-/* Initial state: W [n][nv], slopes [n][nv][dim] (NULL = zero).  Sets the DF
- * factor to 1 and clears the residual history and counters. */
+/* Initial state of the compact scheme (Sec 2.2: cell averages; Sec 2.4: cell-
+ * averaged slopes): W [n][nv], slopes [n][nv][dim] (NULL = zero), original
+ * order, host or device (on_device), copied.  Sets the DF factor (Sec 3.3) of
+ * every cell to 1 and clears the residual history and counters.  Needs
+ * cgks_upload_hierarchy first (CGKS_ERR_STATE otherwise). */
 int cgks_init_state(cgks_t* h, int mesh_id, const double* W, const double* grad, int on_device);
 
-/* Checkpoint / resume of the fine state (W, slopes, DF factor); any pointer
- * may be NULL.  get_state synchronises the stream when on_device == 0. */
+/* Checkpoint / resume of the whole pseudo-time state of the fine level: the
+ * cell averages and slopes the compact scheme evolves (Sec 2.2, 2.4) and the
+ * DF factor the next reconstruction and LU-SGS step read (Sec 3.3, 4.3).
+ * Arrays as in cgks_init_state; any pointer may be NULL (that part is left
+ * as it is).  get_state synchronises the stream when on_device == 0.
+ * set_state does not clear the residual history. */
 int cgks_get_state(cgks_t* h, int mesh_id, double* W, double* grad, double* alpha, int on_device);
 int cgks_set_state(cgks_t* h, int mesh_id, const double* W, const double* grad, const double* alpha,
                    int on_device);
@@ -232,9 +252,12 @@ int cgks_lusgs(cgks_t* h, int mesh_id, int level, int mode, double* W_inout, con
                const double* alpha, const double* dt_exp, const double* dt_imp, double* dW_out, int on_device);
 
 /*
- * Fine smoothing: n_sweeps x (third-order residual, DF-relaxed multi-colour
- * LU-SGS driven by -R, slope update with DF) on the current fine state.  Only
- * level 0 is accepted; coarse smoothing runs inside cgks_vcycle.
+ * Fine smoothing, the pre-smoother of the V-cycle (Sec 5.2) on its own:
+ * n_sweeps x (third-order residual of Sec 2.2-2.4 and 3, slope update with DF,
+ * one DF-relaxed multi-colour LU-SGS step driven by -R (Sec 4.2-4.3, Eqs.
+ * gpu-forward-relaxation and gpu-backward-relaxation), state update) on the
+ * current fine state.  Only level 0 is accepted (CGKS_ERR_ARG otherwise);
+ * coarse smoothing runs inside cgks_vcycle.
  */
 int cgks_smooth(cgks_t* h, int mesh_id, int level, int n_sweeps);
 
@@ -253,8 +276,10 @@ int cgks_smooth(cgks_t* h, int mesh_id, int level, int n_sweeps);
 int cgks_vcycle(cgks_t* h, const int* mesh_ids, int n_meshes, int n_cycles, int mode, double* norms_out,
                 int* cycles_done);
 
-/* Residual norms of the last fine residual evaluation: out (host) [nv][2] =
- * RMS and max over cells of R/V.  Level 0 only.  Synchronises the stream. */
+/* Residual norms of the last fine residual evaluation, the quantity whose
+ * drop the convergence histories of Sec 6 follow (the paper plots it; the RMS
+ * of the density residual per unit volume is taken here): out (host) [nv][2]
+ * = RMS and max over cells of R/V.  Level 0 only.  Synchronises the stream. */
 int cgks_residual_norms(cgks_t* h, int mesh_id, int level, double* out);
 
 /* Event counters since init_state (host uint64 [4]): reconstruction

@@ -36,7 +36,7 @@ _LIB = os.path.join(_HERE, "_build", "libcgks_oracle.so")
 
 DEFAULTS = dict(gamma=1.4, cfl_imp=10.0, cfl_exp=0.5, tau_c1=0.01, tau_c2=1.0,
                 weno_gamma_high=0.95, weno_eps=1e-15, r_safety=1.0, n_sweep=6,
-                relax=-1.0, df_prolong=1, fine_smoother=0, mu=0.0)
+                relax=-1.0, df_prolong=1, fine_smoother=0, mu=0.0, slope_relax=1.0, alpha_relax=1.0)
 
 
 def build(force: bool = False) -> str:
@@ -121,7 +121,9 @@ def cfg_vector(dim: int, winf=None, **over) -> np.ndarray:
     V-cycle switches: relax (negative: DF relaxes LU-SGS; else this constant
     stands for DF), df_prolong (1: DF-scaled prolongation; 0: plain injection)
     and fine_smoother (0: LU-SGS step; 1: explicit update), then mu (dynamic
-    viscosity; 0 for the Euler equations)."""
+    viscosity; 0 for the Euler equations), then slope_relax and alpha_relax
+    (pseudo-time under-relaxation of the slope update and of a rise of the
+    stored DF factor; 1 replaces them)."""
     c = dict(DEFAULTS)
     c.update(over)
     nv = dim + 2
@@ -133,7 +135,7 @@ def cfg_vector(dim: int, winf=None, **over) -> np.ndarray:
                                                  c["tau_c2"], c["weno_gamma_high"], c["weno_eps"],
                                                  c["r_safety"], float(c["n_sweep"])], w,
                                                 [c["relax"], float(c["df_prolong"]), float(c["fine_smoother"]),
-                                                 c["mu"]]]))
+                                                 c["mu"], c["slope_relax"], c["alpha_relax"]]]))
 
 
 def _c(a, dt=np.float64):

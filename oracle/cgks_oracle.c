@@ -56,6 +56,9 @@ typedef struct {
   int df_prolong;         /* 1: prolongation scaled by DF; 0: plain injection */
   int fine_smoother;      /* 0: DF-relaxed LU-SGS step; 1: explicit update (Eq. smo) */
   double mu;              /* dynamic viscosity: 0 Euler; > 0 Navier-Stokes, Pr = 1 */
+  double slope_relax;     /* reading: pseudo-time slope update G <- G + w (DF Gnew - G); 1 replaces */
+  double alpha_relax;     /* reading: a rise of the stored DF is under-relaxed by this factor;
+                             a fall takes effect at once; 1 takes the product itself */
 } OCfg;
 
 static void cfg_from(const double* c, int nv, OCfg* o) {
@@ -67,6 +70,8 @@ static void cfg_from(const double* c, int nv, OCfg* o) {
   o->df_prolong = (int)c[10 + nv];
   o->fine_smoother = (int)c[11 + nv];
   o->mu = c[12 + nv];
+  o->slope_relax = c[13 + nv];
+  o->alpha_relax = c[14 + nv];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1599,6 +1604,16 @@ void om_coarse_solve(void* h, int lev, const double* cfgv, const double* W0, con
 }
 void om_norms(void* h, int lev, const double* R, double* out) { norms_of((OMesh*)h, lev, R, out); }
 
+/* The DF factor a cell keeps for the next reconstruction, the LU-SGS
+ * relaxation and the prolongation: the product of its Gauss-point factors
+ * (Sec 3.3), or, where that product exceeds the kept value, a step of
+ * alpha_relax towards it (reading: a pseudo-time under-relaxation; a steady
+ * state is a fixed point either way). */
+static double stored_df(const OCfg* cfg, double kept, double product) {
+  if (cfg->alpha_relax < 1.0 && product > kept) return kept + cfg->alpha_relax * (product - kept);
+  return product;
+}
+
 /* V-cycles (Sec 5.2, pre-smooth 1, post-smooth 0).  State (W, G, alpha) is
  * updated in place.  norms[c*nv*2 ...] receives the fine-level residual norms
  * (RMS and max of R/V per variable) measured at the start of cycle c.
@@ -1631,8 +1646,12 @@ int om_vcycle(void* h, const double* cfgv, double* W, double* G, double* alpha, 
     fine_residual(M, &cfg, W, G, alpha, R, Gn, an, dte, dti, &st);
     if (norms) norms_of(M, 0, R, norms + (size_t)cyc * nv * 2);
     for (int c = 0; c < n0; ++c) {
-      for (int i = 0; i < nv * dim; ++i) G[(size_t)c * nv * dim + i] = an[c] * Gn[(size_t)c * nv * dim + i];
-      alpha[c] = an[c];
+      alpha[c] = stored_df(&cfg, alpha[c], an[c]);
+      for (int i = 0; i < nv * dim; ++i) {
+        double* g = &G[(size_t)c * nv * dim + i];
+        double target = alpha[c] * Gn[(size_t)c * nv * dim + i];
+        *g = cfg.slope_relax < 1.0 ? *g + cfg.slope_relax * (target - *g) : target;
+      }
     }
     /* 2. fine pre-smoothing: one DF-relaxed LU-SGS step driven by -R, or the
        explicit local-time-step update W -= dt R / V (Eq. smo) */
@@ -1649,7 +1668,7 @@ int om_vcycle(void* h, const double* cfgv, double* W, double* G, double* alpha, 
     if (nl == 1) continue;
     /* 3. residual at the smoothed state (slopes not updated); its DF is kept */
     fine_residual(M, &cfg, W, G, alpha, R, Gn, an, NULL, NULL, &st);
-    for (int c = 0; c < n0; ++c) alpha[c] = an[c];
+    for (int c = 0; c < n0; ++c) alpha[c] = stored_df(&cfg, alpha[c], an[c]);
     /* 4-7. restriction, forcing and coarse smoothing, level by level */
     const double* Wf = W; const double* af = alpha; const double* Rf = R;
     for (int l = 1; l < nl; ++l) {

@@ -48,7 +48,8 @@ class Config(C.Structure):
                 ("diverge_factor", C.c_double), ("fine_smoother", C.c_int), ("df_relax", C.c_int),
                 ("df_prolong", C.c_int), ("df_gate", C.c_double), ("learned_judge_every", C.c_int),
                 ("learned_max_error", C.c_double), ("flux_precision", C.c_int),
-                ("relax_beta", C.c_double), ("mu", C.c_double)]
+                ("relax_beta", C.c_double), ("mu", C.c_double), ("slope_relax", C.c_double),
+                ("alpha_relax", C.c_double)]
 
 
 _lib = None

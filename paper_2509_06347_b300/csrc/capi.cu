@@ -505,7 +505,7 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
       M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R,
       slopes_update ? M.G : nullptr, alpha_out_dev ? alpha_out_dev : L.alpha, want_diag ? L.D : nullptr,
       gradnew_dev, (want_norm && !grouped) ? M.norm_part : nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg),
-      L.rface,
+      alpha_out_dev ? 1.0 : h->cfg.alpha_relax, h->cfg.slope_relax, L.rface,
       (want_norm && grouped) ? M.qcell : nullptr, (grouped && !alpha_out_dev) ? M.active : nullptr, dWs0, dW0,
       L.color_off[1]);
   if (want_norm && !grouped)
@@ -842,6 +842,8 @@ int cgks_default_config(cgks_config* c) {
   c->flux_precision = 0;
   c->relax_beta = 0.5;
   c->mu = 0.0;
+  c->slope_relax = 1.0;
+  c->alpha_relax = 1.0;
   return CGKS_OK;
 }
 
@@ -861,7 +863,9 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
       !(h->cfg.relax_beta >= 0.0 && h->cfg.relax_beta <= 1.0) || !(h->cfg.mu >= 0.0 && h->cfg.mu < 1e300) ||
       !(h->cfg.tau_c1 > 0.0 && h->cfg.tau_c1 < 1e300) || !(h->cfg.tau_c2 >= 0.0 && h->cfg.tau_c2 < 1e300) ||
       !(h->cfg.cfl_imp > 0.0 && h->cfg.cfl_imp < 1e300) || !(h->cfg.cfl_exp > 0.0 && h->cfg.cfl_exp < 1e300) ||
-      !(h->cfg.weno_eps > 0.0 && h->cfg.weno_eps < 1e300)) {
+      !(h->cfg.weno_eps > 0.0 && h->cfg.weno_eps < 1e300) ||
+      !(h->cfg.slope_relax > 0.0 && h->cfg.slope_relax <= 1.0) ||
+      !(h->cfg.alpha_relax > 0.0 && h->cfg.alpha_relax <= 1.0)) {
     delete h;
     return CGKS_ERR_ARG;
   }
@@ -1439,11 +1443,13 @@ int cgks_run_stage(cgks_t* h, int mesh_id, int stage) {
       if (M.dim == 2)
         k_gather<2><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
             M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.alpha,
-            L.D, nullptr, nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg), L.rface, nullptr, nullptr);
+            L.D, nullptr, nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg), h->cfg.alpha_relax, 1.0,
+            L.rface, nullptr, nullptr);
       else
         k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
             M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.alpha,
-            L.D, nullptr, nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg), L.rface, nullptr, nullptr);
+            L.D, nullptr, nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg), h->cfg.alpha_relax, 1.0,
+            L.rface, nullptr, nullptr);
     }
     CK(cudaGetLastError());
     return CGKS_OK;

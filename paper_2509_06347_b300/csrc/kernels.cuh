@@ -728,6 +728,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
                                                    double* __restrict__ Gout, double* __restrict__ alpha,
                                                    double* __restrict__ Dg, double* __restrict__ gradnew_out,
                                                    double* __restrict__ norm_part, double relax_fixed,
+                                                   double om_alpha, double om_slope,
                                                    const double* __restrict__ rface, double* __restrict__ qcell,
                                                    const int* __restrict__ active, TS* __restrict__ dWs0 = nullptr,
                                                    TS* __restrict__ dW0 = nullptr, int c0_end = 0) {
@@ -763,6 +764,9 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
     }
     const double iV = 1.0 / M.vol[c];
     const bool live = !active || active[M.grp[c]];  // frozen (converged) batch members keep their state
+    // stored DF: the product itself, or, where it rises, under-relaxed towards
+    // it (a fall takes effect at once; same fixed points)
+    const double as = (om_alpha < 1.0 && a > alpha[c]) ? alpha[c] + om_alpha * (a - alpha[c]) : a;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       R[(size_t)c * NV + v] = r[v];
@@ -777,13 +781,16 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
       for (int d = 0; d < DIM; ++d) {
         const double g = gn[v][d] * iV;
         if (gradnew_out) gradnew_out[((size_t)c * NV + v) * DIM + d] = g;
-        if (Gout && live) Gout[((size_t)c * NV + v) * DIM + d] = a * g;  // slope update with DF
+        if (Gout && live) {  // slope update with DF, replaced or under-relaxed
+          const size_t i = ((size_t)c * NV + v) * DIM + d;
+          Gout[i] = om_slope < 1.0 ? Gout[i] + om_slope * (as * g - Gout[i]) : as * g;
+        }
       }
     }
-    if (live) alpha[c] = a;
+    if (live) alpha[c] = as;
     // LU-SGS diagonal with DF, or with the constant of the fixed-factor schemes (relax_fixed >= 0)
     if (Dg) {
-      const double rel = relax_fixed < 0.0 ? a : relax_fixed;
+      const double rel = relax_fixed < 0.0 ? as : relax_fixed;
       const double D = lusgs_diag<DIM>(T, c, rface, rel, dte[c], dti[c]);
       Dg[c] = D;
       if (dWs0 && c < c0_end) colour0_forward<NV, TS>(c, R, rel, D, dWs0, dW0);

@@ -322,6 +322,7 @@ SWITCHES = {
     "fixed_factor_0.5": (dict(df_relax=2, relax_beta=0.5), dict(relax=0.5)),
     "plain_injection": (dict(df_prolong=0), dict(df_prolong=0)),
     "explicit_fine_smoother": (dict(fine_smoother=1), dict(fine_smoother=1)),
+    "relaxed_slopes_and_df": (dict(slope_relax=0.5, alpha_relax=0.3), dict(slope_relax=0.5, alpha_relax=0.3)),
 }
 
 
@@ -331,7 +332,9 @@ def test_vcycle_switches_match_oracle(name, switch):
     """V-cycles (plain FP64) with the relaxation and prolongation switches of
     the ablations: LU-SGS relaxed by 1 or by a fixed factor instead of DF,
     plain injection instead of the DF-scaled prolongation, and the explicit
-    fine smoother; state and norms against the oracle with the same switch."""
+    fine smoother, and the pseudo-time under-relaxation of the slope update and
+    of a rising DF factor; state, slopes, DF and norms against the oracle with
+    the same switch."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2509_06347_b300 import build, cgks
@@ -346,10 +349,12 @@ def test_vcycle_switches_match_oracle(name, switch):
         ncyc = 3
         norms = np.zeros((ncyc, nv, 2))
         c.cgks_vcycle([1], ncyc, cgks.PLAIN_FP64, norms)
-        Wd = np.zeros_like(W)
-        c.cgks_get_state(1, Wd)
+        Wd, Gd, ad = np.zeros_like(W), np.zeros((n, nv, dim)), np.zeros(n)
+        c.cgks_get_state(1, Wd, Gd, ad)
     finally:
         c.close()
     out = oracle.OracleMesh(m).vcycle(oracle.cfg_vector(dim, winf=w, **ora_kw), W, G, np.ones(n), ncyc)
     np.testing.assert_allclose(norms, out["norms"], rtol=1e-8)
     np.testing.assert_allclose(Wd, out["W"], rtol=0, atol=1e-9 * np.max(np.abs(W)))
+    np.testing.assert_allclose(Gd, out["grad"], rtol=0, atol=1e-8 * np.max(np.abs(out["grad"])))
+    np.testing.assert_allclose(ad, out["alpha"], rtol=0, atol=1e-8)

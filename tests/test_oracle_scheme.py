@@ -403,3 +403,51 @@ def test_vcycle_is_its_steps(switch):
     if switch:
         base = om.vcycle(oracle.cfg_vector(2, winf=w), W0, Gq, a0, 1)
         assert np.max(np.abs(base["W"] - out["W"])) > 1e-10
+
+
+def test_vcycle_relaxed_slopes_and_df_are_its_steps():
+    """With pseudo-time under-relaxation of the slope update (slope_relax) and
+    of a rise of the stored DF (alpha_relax), a two-level V-cycle equals its
+    steps: the DF kept after each residual is the Gauss-point product where it
+    does not exceed the kept value, else the kept value plus alpha_relax times
+    the rise; the slopes move slope_relax of the way to DF times the evolved
+    slopes.  A uniform state stays a fixed point."""
+    m = MESHES["cylinder"]
+    om = oracle.OracleMesh(m, levels=2)
+    rng = np.random.default_rng(32)
+    w = synth.freestream(2.0, angle_deg=10.0)
+    Wq, Gq, _, _ = physical_quadratic_state(rng, 2, m["cell_xyz"], scale=0.05)
+    W0 = synth.uniform_state(m, w) + Wq - Wq.mean(0)
+    n = len(W0)
+    a0 = rng.uniform(0.3, 1.0, n)
+    ws, wa = 0.5, 0.3
+    cfg = oracle.cfg_vector(2, winf=w, slope_relax=ws, alpha_relax=wa)
+    out = om.vcycle(cfg, W0, Gq, a0, 1)
+
+    def kept(prev, prod):
+        return np.where(prod > prev, prev + wa * (prod - prev), prod)
+
+    r = om.residual(cfg, W0, Gq, a0)
+    al = kept(a0, r["alpha"])
+    assert np.any(r["alpha"] > a0) and np.any(r["alpha"] < a0)  # both branches taken
+    G = Gq + ws * (al[:, None, None] * r["grad"] - Gq)
+    W, _ = om.lusgs(cfg, W0, -r["R"], al, r["dt_exp"], r["dt_imp"])
+    r2 = om.residual(cfg, W, G, al)
+    al = kept(al, r2["alpha"])
+    Wc0, ac, Rc = om.restrict(0, W, al, r2["R"])
+    Wc = om.coarse_solve(cfg, 1, Wc0, Rc, ac)
+    W = om.prolong(cfg, 0, W, al, Wc, Wc0)
+    np.testing.assert_allclose(out["W"], W, rtol=0, atol=1e-14 * np.max(np.abs(W0)))
+    np.testing.assert_allclose(out["grad"], G, rtol=0, atol=1e-14 * np.max(np.abs(G)))
+    np.testing.assert_allclose(out["alpha"], al, rtol=0, atol=1e-13)
+    base = om.vcycle(oracle.cfg_vector(2, winf=w), W0, Gq, a0, 1)
+    assert np.max(np.abs(base["W"] - out["W"])) > 1e-10
+
+    mv = MESHES["vortex"]
+    omv = oracle.OracleMesh(mv)
+    wu = np.array([1.0, 0.3, -0.2, 2.6])
+    Wu = synth.uniform_state(mv, wu)
+    nu = len(Wu)
+    outu = omv.vcycle(oracle.cfg_vector(2, slope_relax=ws, alpha_relax=wa), Wu, np.zeros((nu, 4, 2)),
+                      np.ones(nu), 2)
+    np.testing.assert_allclose(outu["W"], Wu, rtol=1e-14, atol=1e-14)
