@@ -156,7 +156,47 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_table(torch, ctx, mode, n_cycles=5):
+# DRAM and L2 bytes per V-cycle of each kernel (MIXED), from the ncu captures
+# summarised in profiles/kernels_cylinder65k.md and profiles/kernels_sphere16.md
+# (cold-cache serialised replays, so the DRAM bytes include first-touch traffic
+# that the graph replays find in L2).  The sphere's figures are for the 16^3
+# shell; bench runs of an n^3 shell scale them by (n / 16)^3.
+KERNEL_TRAFFIC_2D = {
+    "k_flux<2, 1, double>": (24798976, 87521776),
+    "k_gather<2, float>": (14686592, 83511904),
+    "k_norm_final<4>": (33792, 244288),
+    "k_sweep<2, float, 2>": (20851200, 56668400),
+    "k_sweep<2, float, 1>": (19325440, 44572544),
+    "k_update<2, float>": (9346816, 28173408),
+    "k_recon<2>": (70775296, 255124384),
+    "k_flux<2, 0, double>": (22682752, 64359008),
+    "k_gather<2, double>": (10227200, 45648288),
+    "k_restrict<2>": (7149568, 30314112),
+    "k_face_kfvs<2>": (12035584, 82827024),
+    "k_coarse_cell<2, double>": (3752064, 16962336),
+    "k_coarse_cell<2, float>": (27821696, 92949056),
+    "k_prolong<2>": (4962176, 14567296),
+}
+KERNEL_TRAFFIC_3D_16 = {
+    "k_flux<3, 1, double>": (142440448, 1003910400),
+    "k_gather<3, float>": (53770112, 325527648),
+    "k_norm_final<5>": (66176, 346704),
+    "k_sweep<3, float, 2>": (27841792, 87614384),
+    "k_sweep<3, float, 1>": (65107328, 176911184),
+    "k_update<3, float>": (19132800, 57963888),
+    "k_recon<3>": (668124288, 3053714416),
+    "k_flux<3, 0, double>": (124839424, 797354912),
+    "k_gather<3, double>": (37566464, 175889344),
+    "k_restrict<3>": (17554944, 68825664),
+    "k_face_kfvs<3>": (32955008, 288717536),
+    "k_coarse_cell<3, double>": (10357248, 45924832),
+    "k_coarse_cell<3, float>": (76880000, 252310720),
+    "k_sweep<3, float, 0>": (36368896, 109901632),
+    "k_prolong<3>": (11208320, 35224640),
+}
+
+
+def kernel_table(torch, ctx, mode, n_cycles=5, traffic=None, hbm_gbs=None):
     """Device time of every kernel of the V-cycle graph, per launch and per
     cycle, from the CUDA activity records of the profiler (CUPTI) over
     n_cycles replays run after the timed region.  None when the profiler
@@ -182,9 +222,18 @@ def kernel_table(torch, ctx, mode, n_cycles=5):
         if not rows:
             return None
         total = sum(r["us_per_cycle"] for r in rows.values())
-        for r in rows.values():
+        for name, r in rows.items():
             r["us_per_launch"] = r["us_per_cycle"] / max(r["launches_per_cycle"], 1e-9)
             r["share"] = r["us_per_cycle"] / total
+            key = name.replace("true", "1").replace("false", "0")
+            if traffic and key in traffic:
+                dram, l2 = traffic[key]
+                r["dram_bytes_per_cycle_ncu"] = dram
+                r["l2_bytes_per_cycle_ncu"] = l2
+                r["dram_gbs"] = dram / (r["us_per_cycle"] * 1e-6) / 1e9
+                r["l2_gbs"] = l2 / (r["us_per_cycle"] * 1e-6) / 1e9
+                if hbm_gbs:
+                    r["dram_frac_of_hbm"] = r["dram_gbs"] / hbm_gbs
         return dict(sorted(rows.items(), key=lambda kv: -kv[1]["us_per_cycle"]))
     except Exception as exc:  # the profiler is optional here
         return {"error": f"{type(exc).__name__}: {exc}"[:200]}
@@ -437,7 +486,14 @@ def run_ours(args):
     e2e = {"value": world * n * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * nv * 8,
            "d2h_bytes_per_step": n * nv * 8 + nv * 2 * 8}
 
-    kernels = kernel_table(torch, ctx, mode)
+    if mode != cgks.MIXED:
+        traffic = None
+    elif dim == 2:
+        traffic = KERNEL_TRAFFIC_2D
+    else:
+        f = (args.sphere_n / 16.0) ** 3
+        traffic = {k: (a * f, b * f) for k, (a, b) in KERNEL_TRAFFIC_3D_16.items()}
+    kernels = kernel_table(torch, ctx, mode, traffic=traffic, hbm_gbs=measured_peaks().get("hbm_gbs"))
     rn = ctx.cgks_residual_norms(1, 0)
     counters = ctx.cgks_counters(1)
     if rank != 0:
@@ -746,39 +802,53 @@ def agglomeration_leg(cgks, stream, settings=((3, 0.1), (3, 0.3))):
 HELD_OUT_MACH = (2.5, 5.5, 7.5)
 
 
-def learned_leg(cgks, stream, n_train_meshes=8, collect_cycles=30, eval_cycles=600):
-    """Learned coarse-grid correction against FP64 and MIXED, bounded so that
-    the default run stays within minutes: the network is trained on GPU
-    trajectories of the first n_train_meshes batch cylinders whose Mach number
-    is more than 0.1 away from 2.5, 5.5 and 7.5, then each mode runs
-    eval_cycles V-cycles at those held-out Mach numbers on the 65,536-cell
-    cylinder."""
+def learned_leg(cgks, stream, collect_at=(0, 20, 80), collect_cycles=2, train_steps=(6000, 3000),
+                eval_cycles=3000, judge_cycles=400, cfg=CYLINDER_CONVERGENCE):
+    """Learned coarse-grid correction against FP64 and MIXED.  Training set:
+    every batch cylinder whose Mach number is more than 0.1 away from 2.5, 5.5
+    and 7.5, solved together; at each cycle count in collect_at the network
+    inputs and the applied coarse corrections of collect_cycles plain cycles are
+    appended (states from the start of the solve and from further on).  The
+    network is trained on the GPU, then, at each held-out Mach number on the
+    65,536-cell cylinder: (1) judge_cycles learned cycles whose judge never
+    disables the network give its relative RMS error against the plain
+    correction every 20 cycles (held-out data); (2) FP64, MIXED and LEARNED
+    (with the fallback policy) run eval_cycles cycles, compared at the deepest
+    decade of residual drop that all three reach.  All runs use cfg."""
     import torch
     t0 = time.perf_counter()
     specs = [s for s in synth.batch_cylinder_specs()
-             if min(abs(s["mach"] - m) for m in HELD_OUT_MACH) > 0.1][:n_train_meshes]
+             if min(abs(s["mach"] - m) for m in HELD_OUT_MACH) > 0.1]
     union, grp, winf, W0 = synth.batch_cylinders(specs)
-    ctx = cgks.Context(stream=stream.cuda_stream)
+    ctx = cgks.Context(stream=stream.cuda_stream, **cfg)
     ctx.cgks_mlp_set_params(synth.mlp_init_params())
     ctx.setup(2, union, winf[0], W0)
     ctx.cgks_set_groups(2, grp, winf)
     t_setup = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx.cgks_mlp_collect(2, collect_cycles, cgks.MIXED)
+    done = 0
+    for at in collect_at:
+        if at > done:
+            ctx.cgks_vcycle_groups(2, at - done, cgks.MIXED, check=False)
+            done = at
+        ctx.cgks_mlp_collect(2, collect_cycles, cgks.MIXED)
+        done += collect_cycles
     torch.cuda.synchronize()
     t_collect = time.perf_counter() - t0
     rows = ctx.cgks_mlp_dataset_size()
     t0 = time.perf_counter()
-    l1 = ctx.cgks_mlp_train(6000, 16384, 1e-3, seed=1)
-    l2 = ctx.cgks_mlp_train(3000, 16384, 3e-4, seed=2)
+    l1 = ctx.cgks_mlp_train(train_steps[0], 16384, 1e-3, seed=1)
+    l2 = ctx.cgks_mlp_train(train_steps[1], 16384, 3e-4, seed=2)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     theta = ctx.cgks_mlp_get_params()
     ctx.close()
-    out = {"train": {"meshes": len(specs), "mach": [round(s["mach"], 3) for s in specs],
-                     "cells": len(W0), "rows": int(rows), "setup_s": t_setup, "collect_s": t_collect,
-                     "train_s": t_train, "steps": 9000, "batch": 16384,
+    out = {"config": cfg,
+           "train": {"meshes": len(specs), "mach": [round(s["mach"], 3) for s in specs],
+                     "cells": len(W0), "rows": int(rows), "collected_at_cycles": list(collect_at),
+                     "cycles_per_collection": collect_cycles, "setup_s": t_setup, "collect_s": t_collect,
+                     "train_s": t_train, "steps": int(sum(train_steps)), "batch": 16384,
                      "loss_first": float(np.mean(l1[:10])), "loss_last": float(np.mean(l2[-50:]))},
            "eval_cycles": eval_cycles}
     mesh = synth.cylinder_mesh(n_theta=64, n_r=32, ratio=1.05, n_refine=2)
@@ -786,16 +856,33 @@ def learned_leg(cgks, stream, n_train_meshes=8, collect_cycles=30, eval_cycles=6
         w = synth.freestream(mach)
         W = synth.uniform_state(mesh, w)
         res = {}
+        # held-out error of the network: judge cycles every 20, never disabled
+        c = cgks.Context(stream=stream.cuda_stream, **dict(cfg, learned_max_error=1e30, learned_judge_every=20))
+        c.cgks_mlp_set_params(theta)
+        c.setup(1, mesh, w, W)
+        errs = []
+        for _ in range(judge_cycles // 20):
+            c.cgks_vcycle([1], 20, cgks.LEARNED, np.zeros((20, 4, 2)), check=False)
+            errs.append(c.cgks_learned_stats(1)["judge_error"])
+        c.close()
+        res["judge_errors"] = errs
+        res["judge_error_median"] = float(np.median(errs))
+        res["explained_fraction_median"] = float(1.0 - np.median(errs) ** 2)
         for name, mode in (("fp64", cgks.PLAIN_FP64), ("mixed", cgks.MIXED), ("learned", cgks.LEARNED)):
-            c = cgks.Context(stream=stream.cuda_stream)
+            c = cgks.Context(stream=stream.cuda_stream, **cfg)
             c.cgks_mlp_set_params(theta)
             r, _ = _solve_to_drop_ctx(c, mesh, w, W, None, mode, eval_cycles)
             if mode == cgks.LEARNED:
                 r["learned_stats"] = c.cgks_learned_stats(1)
             c.close()
             res[name] = r
-        res["learned_vs_fp64_wall_ratio"] = res["fp64"]["wall_s"] / res["learned"]["wall_s"]
-        res["learned_vs_fp64_final_drop_ratio"] = res["learned"]["final_drop"] / res["fp64"]["final_drop"]
+        deep = max([k for k in range(1, 11) if all(f"cycles_to_1e-{k}" in res[m] for m in ("fp64", "mixed", "learned"))],
+                   default=0)
+        if deep:
+            key = f"wall_s_to_1e-{deep}"
+            res["common_drop"] = f"1e-{deep}"
+            res["wall_ratio_fp64_over_learned"] = res["fp64"][key] / res["learned"][key]
+            res["wall_ratio_fp64_over_mixed"] = res["fp64"][key] / res["mixed"][key]
         out[f"mach_{mach}"] = res
     return out
 

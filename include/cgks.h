@@ -393,16 +393,24 @@ int cgks_residual_coarse_noalloc(cgks_t* h, int mesh_id, int level, const double
  * Learned coarse-grid correction (a per-cell network predicting the correction
  * the coarse levels would make).  The paper has no learned component; the
  * network, its inputs and its training are this library's design.
- * Network: 68 inputs -> 64 -> GELU -> 64 -> GELU -> 4, parameters as one flat
- * FP32 vector of 8,836 values [W1 (64x68 row-major), b1, W2 (64x64), b2,
+ * Network: 76 inputs -> 64 -> GELU -> 64 -> GELU -> 4, parameters as one flat
+ * FP32 vector of 9,348 values [W1 (64x76 row-major), b1, W2 (64x64), b2,
  * W3 (4x64), b3] (FP32 master copy, BF16 compute copy, FP32 accumulation).
  */
-int cgks_mlp_set_params(cgks_t* h, const float* theta /* host [8836]; resets Adam */);
-int cgks_mlp_get_params(cgks_t* h, float* theta /* host [8836] */);
-/* Inference on device rows: X bf16 [n][68] (uint16 bit patterns), P fp32 [n][4]. */
+int cgks_mlp_set_params(cgks_t* h, const float* theta /* host [9348]; resets Adam */);
+int cgks_mlp_get_params(cgks_t* h, float* theta /* host [9348] */);
+/* Inference on device rows: X bf16 [n][76] (uint16 bit patterns), P fp32 [n][4]. */
 int cgks_mlp_forward(cgks_t* h, int64_t n, const uint16_t* X, float* P);
-/* Mean-squared-error gradient at device rows X [n][68] (bf16), Y [n][4] (fp32):
- * grad (device fp32 [8836]); loss (host, nullable). */
+/* Forward implementation of every later network evaluation on h (inference,
+ * learned cycles and training): 0 (default) = one fused kernel per 128 rows,
+ * layers 1-2 as tcgen05.mma with FP32 accumulators in tensor memory and layer
+ * 3 on the CUDA cores; 1 = the mma.sync GEMM chain.  Same arithmetic (BF16
+ * operands, FP32 sums) up to the order of the sums.  A tensor-core forward
+ * whose bounded wait for its MMAs gives up is reported as CGKS_ERR_TIMEOUT by
+ * the next cgks_synchronize, cgks_mlp_train or learned cgks_vcycle. */
+int cgks_mlp_select(cgks_t* h, int impl);
+/* Mean-squared-error gradient at device rows X [n][76] (bf16), Y [n][4] (fp32):
+ * grad (device fp32 [9348]); loss (host, nullable). */
 int cgks_mlp_grad(cgks_t* h, int64_t n, const uint16_t* X, const float* Y, float* grad, float* loss);
 /* Training set held by the library: append rows (host or device pointers),
  * query its size, clear it. */
@@ -421,14 +429,18 @@ int cgks_mlp_train(cgks_t* h, int n_steps, int batch, double lr, uint64_t seed, 
 int cgks_mlp_collect(cgks_t* h, int mesh_id, int n_cycles, int mode);
 
 /* The network input of every fine cell at the current state of a 2-D mesh:
- * X_out (host, [n][68] bfloat16 bit patterns, original cell order).  Per cell
+ * X_out (host, [n][76] bfloat16 bit patterns, original cell order).  Per cell
  * 17 values scaled by the free stream's rho, rho c, rho c, rho c^2: W (4),
  * slopes times |Omega|^(1/2) (8), R dt_imp / |Omega| (4) and the DF factor,
  * for the cell and then its 3 face neighbours in stored face order (face k
  * opposite vertex k); across a boundary face the ghost state and slopes, zero
- * residual and the cell's own DF factor and size.  R, dt_imp and DF come from
- * a residual evaluation at the current state (as cgks_residual; the state is
- * not changed).  Needs cgks_mlp_set_params. */
+ * residual and the cell's own DF factor and size.  Then 8 more: the fine
+ * residual summed over the cell's level-1 parent and over its level-2
+ * grandparent (the restriction of Sec 5.2), each times dt_imp
+ * (|Omega_I| / |Omega|)^(1/2) / |Omega_I| and scaled like W (zero on meshes
+ * of fewer than 3 levels).  R, dt_imp and DF come from a residual evaluation
+ * at the current state (as cgks_residual; the state is not changed).  Needs
+ * cgks_mlp_set_params. */
 int cgks_mlp_features(cgks_t* h, int mesh_id, uint16_t* X_out);
 
 /* Learned-cycle statistics of the last cgks_vcycle(..., CGKS_LEARNED, ...):

@@ -3,11 +3,11 @@
 TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline).  Plain numpy,
 written from the definition, sharing no code with the CUDA kernels.
 
-Network (a per-cell multilayer perceptron): 68 inputs -> Linear(64) -> GELU ->
+Network (a per-cell multilayer perceptron): 76 inputs -> Linear(64) -> GELU ->
 Linear(64) -> GELU -> Linear(4); GELU(x) = x Phi(x) with the exact normal CDF.
 Parameters are laid out in one flat vector
-    [W1 (64x68, row-major out x in), b1 (64), W2 (64x64), b2 (64), W3 (4x64), b3 (4)]
-= 8,836 values.  Loss: mean squared error over samples and outputs.  Adam with
+    [W1 (64x76, row-major out x in), b1 (64), W2 (64x64), b2 (64), W3 (4x64), b3 (4)]
+= 9,348 values.  Loss: mean squared error over samples and outputs.  Adam with
 bias correction (Kingma and Ba, "Adam: a method for stochastic optimization",
 ICLR 2015).
 """
@@ -17,7 +17,7 @@ import math
 
 import numpy as np
 
-SIZES = [(64, 68), (64, 64), (4, 64)]
+SIZES = [(64, 76), (64, 64), (4, 64)]
 N_PARAMS = sum(o * i + o for o, i in SIZES)
 
 

@@ -29,9 +29,14 @@ EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_erro
            "cgks_gks_points", "cgks_kfvs_points", "cgks_run_stage", "cgks_launch_count",
            "cgks_vcycle_launch", "cgks_dword_selftest", "cgks_special_selftest", "cgks_fma_probe", "cgks_set_groups", "cgks_vcycle_groups",
            "cgks_autotune", "cgks_residual_coarse_noalloc", "cgks_mlp_set_params", "cgks_mlp_get_params",
-           "cgks_mlp_forward", "cgks_mlp_grad", "cgks_mlp_dataset_append", "cgks_mlp_dataset_size",
+           "cgks_mlp_forward", "cgks_mlp_select", "cgks_mlp_grad", "cgks_mlp_dataset_append", "cgks_mlp_dataset_size",
            "cgks_mlp_dataset_clear", "cgks_mlp_train", "cgks_mlp_collect", "cgks_mlp_features", "cgks_learned_stats",
            "cgks_synchronize"]
+
+
+# the per-cell network: inputs and parameter count
+N_IN = 76
+N_PARAMS = 64 * N_IN + 64 + 64 * 64 + 64 + 4 * 64 + 4  # 9,348
 
 
 class CgksError(RuntimeError):
@@ -101,6 +106,7 @@ def load_library(path: str = LIB_PATH):
         "cgks_mlp_set_params": [P, P],
         "cgks_mlp_get_params": [P, P],
         "cgks_mlp_forward": [P, I64, P, P],
+        "cgks_mlp_select": [P, I],
         "cgks_mlp_grad": [P, I64, P, P, P, P],
         "cgks_mlp_dataset_append": [P, I64, P, P],
         "cgks_mlp_dataset_size": [P, P],
@@ -354,9 +360,13 @@ class Context:
         self._check(self._L.cgks_mlp_set_params(self.h, _ptr(t)))
 
     def cgks_mlp_get_params(self):
-        out = np.zeros(8836, np.float32)
+        out = np.zeros(N_PARAMS, np.float32)
         self._check(self._L.cgks_mlp_get_params(self.h, _ptr(out)))
         return out
+
+    def cgks_mlp_select(self, impl: int):
+        """Network forward implementation: 0 tcgen05 (tensor memory), 1 mma.sync."""
+        self._check(self._L.cgks_mlp_select(self.h, int(impl)))
 
     def cgks_mlp_forward(self, X_bf16_dev, P_dev):
         self._check(self._L.cgks_mlp_forward(self.h, X_bf16_dev.shape[0], _ptr(X_bf16_dev), _ptr(P_dev)))
@@ -387,9 +397,9 @@ class Context:
         self._check(self._L.cgks_mlp_collect(self.h, mesh_id, n_cycles, mode))
 
     def cgks_mlp_features(self, mesh_id: int):
-        """Network inputs [n, 68] of the current state, as float32."""
+        """Network inputs [n, 76] of the current state, as float32."""
         n = self.meshes[mesh_id]["n"]
-        bits = np.zeros((n, 68), np.uint16)
+        bits = np.zeros((n, N_IN), np.uint16)
         self._check(self._L.cgks_mlp_features(self.h, mesh_id, _ptr(bits)))
         return (bits.astype(np.uint32) << 16).view(np.float32)
 

@@ -16,6 +16,7 @@
 #include "host_mesh.hpp"
 #include "kernels.cuh"
 #include "mlp.cuh"
+#include "mlp_tc.cuh"
 
 namespace cgks {
 namespace {
@@ -27,6 +28,9 @@ struct ArgError : std::runtime_error {
   using std::runtime_error::runtime_error;
 };
 struct StateError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct TimeoutError : std::runtime_error {
   using std::runtime_error::runtime_error;
 };
 
@@ -125,6 +129,7 @@ struct MeshDev {
   __nv_bfloat16* X = nullptr;
   float *Pl = nullptr, *Yl = nullptr;
   double *Wsave = nullptr, *judge_part = nullptr, *judge_out = nullptr;
+  double *Rp1 = nullptr, *Rp2 = nullptr;  // restricted fine residual on levels 1 and 2 (network inputs)
   // learned-cycle policy statistics
   double lstats[6] = {0, 0, 0, 0, 0, -1};  // learned, plain, judge, fallbacks, disabled, last judge error
   // batched members (groups of cells with their own free stream)
@@ -159,6 +164,10 @@ struct MlpState {
   float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
   __nv_bfloat16* theta_bf = nullptr;
   int step = 0;
+  // forward implementation: 0 = fused tcgen05 kernel (tensor memory), 1 = mma.sync GEMM chain
+  int impl = 0;
+  int* tc_err = nullptr;  // set by the tcgen05 kernel if a bounded wait gave up
+  bool tc_attr = false;   // dynamic shared-memory size set for the tcgen05 kernel
   // work buffers (rows = work_rows)
   float *Z1 = nullptr, *Z2 = nullptr, *P = nullptr, *dP = nullptr, *part = nullptr, *loss = nullptr;
   __nv_bfloat16 *A1 = nullptr, *A2 = nullptr, *dPb = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
@@ -167,7 +176,7 @@ struct MlpState {
   int* idx = nullptr;
   float* split = nullptr;  // split-K partials
   size_t split_elems = 0;
-  // training set (rows of 68 bf16 features and 4 fp32 targets)
+  // training set (rows of 76 bf16 features and 4 fp32 targets)
   std::vector<std::unique_ptr<DBuf>> data;
   __nv_bfloat16* X = nullptr;
   float* Y = nullptr;
@@ -727,6 +736,8 @@ int guarded(cgks_t* h, F&& f) {
     return fail(h, CGKS_ERR_ARG, e.what());
   } catch (const StateError& e) {
     return fail(h, CGKS_ERR_STATE, e.what());
+  } catch (const TimeoutError& e) {
+    return fail(h, CGKS_ERR_TIMEOUT, e.what());
   } catch (const CudaError& e) {
     return fail(h, CGKS_ERR_CUDA, e.what());
   } catch (const std::bad_alloc&) {
@@ -737,6 +748,17 @@ int guarded(cgks_t* h, F&& f) {
 }
 
 void enqueue_kind(cgks_t* h, MeshDev& M, int kind, int prec);
+
+// after a synchronisation: did a tensor-core network forward give up waiting?
+void check_tc_error(cgks_t* h) {
+  if (!h->mlp.tc_err) return;
+  int e = 0;
+  CK(cudaMemcpy(&e, h->mlp.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CK(cudaMemset(h->mlp.tc_err, 0, sizeof(int)));
+    throw TimeoutError("the tensor-core network forward gave up waiting for its MMAs");
+  }
+}
 
 // learned V-cycles with the fallback policy (host-side state machine)
 int run_learned(cgks_t* h, MeshDev& M, int n_cycles, double* norms_out, int* cycles_done) {
@@ -807,6 +829,7 @@ int run_learned(cgks_t* h, MeshDev& M, int n_cycles, double* norms_out, int* cyc
         norms_out[(size_t)i * 2 * nv + j] = i < done ? hist[(size_t)i * 2 * nv + j] : -1.0;
   }
   if (cycles_done) *cycles_done = done;
+  check_tc_error(h);
   return status;
 }
 
@@ -906,6 +929,7 @@ const char* cgks_last_error(cgks_t* h) { return h ? h->err.c_str() : "null handl
 int cgks_synchronize(cgks_t* h) {
   return guarded(h, [&]() -> int {
     CK(cudaStreamSynchronize(h->stream));
+    check_tc_error(h);
     return CGKS_OK;
   });
 }
@@ -1688,6 +1712,12 @@ void mlp_ensure(cgks_t* h) {
   S.v = dalloc<float>(S.pool, kParams);
   S.grad = dalloc<float>(S.pool, kParams);
   S.theta_bf = dalloc<__nv_bfloat16>(S.pool, kParams);
+  S.tc_err = dalloc<int>(S.pool, 1);
+  CK(cudaMemsetAsync(S.tc_err, 0, sizeof(int), h->stream));
+  if (!S.tc_attr) {
+    CK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    S.tc_attr = true;
+  }
   S.ready = true;
 }
 
@@ -1730,10 +1760,18 @@ GemmArgs gargs(int M, int N, int K, const __nv_bfloat16* A, int lda, int ta, con
 }
 
 // forward pass on rows of X (bf16 [rows][68]) -> P (fp32 [rows][4]); keeps Z1, A1, Z2, A2
-void mlp_forward(cgks_t* h, int64_t rows, const __nv_bfloat16* X, float* P) {
+// for the backward pass when keep (the mma.sync chain always keeps them)
+void mlp_forward(cgks_t* h, int64_t rows, const __nv_bfloat16* X, float* P, bool keep = true) {
   MlpState& S = h->mlp;
   const __nv_bfloat16* W = S.theta_bf;
   const int M = (int)rows;
+  if (S.impl == 0) {
+    const int nb = (int)((rows + kTcRows - 1) / kTcRows);
+    k_mlp_forward_tc<<<nb, kTcThreads, kTcSmem, h->stream>>>(M, X, W, S.theta, keep ? S.Z1 : nullptr,
+                                                            keep ? S.A1 : nullptr, keep ? S.Z2 : nullptr,
+                                                            keep ? S.A2 : nullptr, P, S.tc_err);
+    return;
+  }
   gemm(h->stream, gargs(M, kH, kIn, X, kIn, 0, W + oW1, kIn, 1, S.Z1, S.theta + ob1, S.A1, nullptr, kEpiGeluBf16));
   gemm(h->stream, gargs(M, kH, kH, S.A1, kH, 0, W + oW2, kH, 1, S.Z2, S.theta + ob2, S.A2, nullptr, kEpiGeluBf16));
   gemm(h->stream, gargs(M, kOut, kH, S.A2, kH, 0, W + oW3, kH, 1, P, S.theta + ob3, nullptr, nullptr, kEpiStore));
@@ -1788,14 +1826,29 @@ void ensure_learned(cgks_t* h, MeshDev& M) {
     M.Wsave = dalloc<double>(M.lpool, n * M.nv);
     M.judge_part = dalloc<double>(M.lpool, 2 * blocks_for(n));
     M.judge_out = dalloc<double>(M.lpool, 2);
+    if (M.nlev >= 3) {
+      M.Rp1 = dalloc<double>(M.lpool, (size_t)M.lev[1].n * 4);
+      M.Rp2 = dalloc<double>(M.lpool, (size_t)M.lev[2].n * 4);
+    }
   }
   mlp_work(h, n);
 }
 
+static_assert(kFeat == kIn, "network input width");
+
 void features(cgks_t* h, MeshDev& M) {
   LevelDev& L = M.lev[0];
-  k_features2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(M.fine, L.W, M.G, L.R, L.dti, L.alpha, M.winf, h->cfg.gamma,
-                                                          M.X);
+  const bool coarse = M.nlev >= 3;
+  if (coarse) {
+    LevelDev& C1 = M.lev[1];
+    LevelDev& C2 = M.lev[2];
+    k_sum_children<<<blocks_for(C1.n), kBlock, 0, h->stream>>>(C1.n, C1.ch_off, C1.ch_idx, L.R, M.Rp1);
+    k_sum_children<<<blocks_for(C2.n), kBlock, 0, h->stream>>>(C2.n, C2.ch_off, C2.ch_idx, M.Rp1, M.Rp2);
+  }
+  k_features2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(
+      M.fine, L.W, M.G, L.R, L.dti, L.alpha, M.winf, h->cfg.gamma, coarse ? L.parent : nullptr,
+      coarse ? M.lev[1].parent : nullptr, M.Rp1, M.Rp2, coarse ? M.lev[1].vol : nullptr,
+      coarse ? M.lev[2].vol : nullptr, M.X);
 }
 
 template <typename T>
@@ -1803,7 +1856,7 @@ void enqueue_learned(cgks_t* h, MeshDev& M, bool judge) {
   LevelDev& L = M.lev[0];
   vcycle_pre<2, T>(h, M);
   features(h, M);
-  mlp_forward(h, L.n, M.X, M.Pl);
+  mlp_forward(h, L.n, M.X, M.Pl, false);
   const int* grp = M.lgrp.empty() ? nullptr : M.lgrp[0];
   if (!judge) {
     k_apply_learned2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, M.Pl, L.alpha, h->cfg.df_gate, grp, M.winf,
@@ -1927,8 +1980,19 @@ int cgks_mlp_forward(cgks_t* h, int64_t n, const uint16_t* X, float* P) {
     if (n <= 0 || n > (1ll << 30) || !X || !P) throw ArgError("invalid forward arguments");
     if (!h->mlp.ready) throw StateError("no network parameters");
     mlp_work(h, n);
-    mlp_forward(h, n, (const __nv_bfloat16*)X, P);
+    mlp_forward(h, n, (const __nv_bfloat16*)X, P, false);
     CK(cudaGetLastError());
+    return CGKS_OK;
+  });
+}
+
+int cgks_mlp_select(cgks_t* h, int impl) {
+  return guarded(h, [&]() -> int {
+    if (impl != 0 && impl != 1) throw ArgError("impl must be 0 (tcgen05) or 1 (mma.sync)");
+    if (h->mlp.impl != impl) {
+      h->mlp.impl = impl;
+      for (auto& kv : h->meshes) kv.second->drop_graphs();  // learned graphs hold the old kernels
+    }
     return CGKS_OK;
   });
 }
@@ -2030,6 +2094,7 @@ int cgks_mlp_train(cgks_t* h, int n_steps, int batch, double lr, uint64_t seed, 
     }
     if (losses) std::memcpy(losses, lh.data(), n_steps * sizeof(float));
     CK(cudaGetLastError());
+    check_tc_error(h);
     return CGKS_OK;
   });
 }

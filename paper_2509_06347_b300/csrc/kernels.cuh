@@ -1294,17 +1294,65 @@ __device__ __forceinline__ void cell_features(const double* W, const double (*g)
   out[16] = __float2bfloat16((float)a);
 }
 
+// Inputs per cell: 17 for the cell and each of its 3 face neighbours (68),
+// then the restricted residuals of its level-1 parent and level-2 grandparent
+// (8): the coarse-grid defects that drive the correction the network predicts.
+constexpr int kFeat = 76;
+
+// Rc[I] = sum of Rf over the children of coarse cell I (4 variables, in the
+// children's stored order)
+__global__ void k_sum_children(int nc, const int* __restrict__ ch_off, const int* __restrict__ ch_idx,
+                               const double* __restrict__ Rf, double* __restrict__ Rc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int e = ch_off[I]; e < ch_off[I + 1]; ++e) {
+    const int i = ch_idx[e];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) s[v] += Rf[(size_t)i * 4 + v];
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) Rc[(size_t)I * 4 + v] = s[v];
+}
+
+// parent1/parent2: level-1 parent of each fine cell and level-2 parent of each
+// level-1 cell (stored order); R1, R2 the restricted residuals and vol1, vol2
+// the volumes of those levels (all null on a mesh of fewer than 3 levels: the
+// 8 inputs are then zero).  Each coarse residual enters as an increment: times
+// the cell's implicit time step scaled by the length ratio to the coarse
+// cell, sqrt(V_I / V_c), over V_I.
 __global__ void __launch_bounds__(kBlock) k_features2(DevFine M, const double* __restrict__ W,
                                                       const double* __restrict__ G, const double* __restrict__ R,
                                                       const double* __restrict__ dti, const double* __restrict__ alpha,
                                                       const double* __restrict__ winf, double gamma,
+                                                      const int* __restrict__ parent1, const int* __restrict__ parent2,
+                                                      const double* __restrict__ R1, const double* __restrict__ R2,
+                                                      const double* __restrict__ vol1, const double* __restrict__ vol2,
                                                       __nv_bfloat16* __restrict__ X) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= M.n) return;
   const double* wi = winf + 4 * (M.grp ? M.grp[c] : 0);
   double sc[4];
   fs_scales(wi, gamma, sc);
-  __nv_bfloat16* out = X + (size_t)c * 68;
+  __nv_bfloat16* out = X + (size_t)c * kFeat;
+  {
+    double f1[4] = {0.0, 0.0, 0.0, 0.0}, f2[4] = {0.0, 0.0, 0.0, 0.0};
+    if (parent1 && parent2) {
+      const int I = parent1[c], J = parent2[I];
+      const double k1 = dti[c] * sqrt(vol1[I] / M.vol[c]) / vol1[I];
+      const double k2 = dti[c] * sqrt(vol2[J] / M.vol[c]) / vol2[J];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        f1[v] = R1[(size_t)I * 4 + v] * k1 / sc[v];
+        f2[v] = R2[(size_t)J * 4 + v] * k2 / sc[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      out[68 + v] = __float2bfloat16((float)f1[v]);
+      out[72 + v] = __float2bfloat16((float)f2[v]);
+    }
+  }
   double Wc[4], gc[4][2];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {

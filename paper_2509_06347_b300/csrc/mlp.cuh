@@ -1,8 +1,8 @@
-// Learned coarse-grid correction: per-cell MLP 68 -> 64 -> 64 -> 4 (GELU),
+// Learned coarse-grid correction: per-cell MLP 76 -> 64 -> 64 -> 4 (GELU),
 // BF16 operands on the tensor cores with FP32 accumulation, trained on the GPU
 // (forward, backward, Adam on FP32 master weights with BF16 copies).
 //
-// The dense layers are small (N <= 64, K <= 68) over many rows (cells), so one
+// The dense layers are small (N <= 76, K <= 76) over many rows (cells), so one
 // tiled GEMM kernel serves inference, back-propagation and (split over K)
 // the weight gradients: 64 x 64 block tiles, 4 warps of 32 x 32, each warp
 // issuing mma.sync.m16n8k16 (bf16 x bf16 -> f32) per 16-wide K step.
@@ -13,8 +13,8 @@
 namespace cgks {
 namespace mlp {
 
-constexpr int kIn = 68, kH = 64, kOut = 4;
-constexpr int kParams = kH * kIn + kH + kH * kH + kH + kOut * kH + kOut;  // 8836
+constexpr int kIn = 76, kH = 64, kOut = 4;
+constexpr int kParams = kH * kIn + kH + kH * kH + kH + kOut * kH + kOut;  // 9348
 // offsets in the flat parameter vector
 constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
               ob3 = oW3 + kOut * kH;

@@ -459,12 +459,12 @@ def concat_meshes(meshes):
     return union, np.concatenate(grp)
 
 
-MLP_LAYERS = ((64, 68), (64, 64), (4, 64))  # (outputs, inputs) of the per-cell network
+MLP_LAYERS = ((64, 76), (64, 64), (4, 64))  # (outputs, inputs) of the per-cell network
 
 
 def mlp_init_params(seed: int = DEFAULT_SEED + 4):
     """Seeded He-style initial weights of the per-cell network, flat
-    [W1 (64x68 row-major), b1, W2 (64x64), b2, W3 (4x64), b3] = 8,836 values,
+    [W1 (64x76 row-major), b1, W2 (64x64), b2, W3 (4x64), b3] = 9,348 values,
     biases zero."""
     rng = np.random.default_rng(seed)
     parts = []

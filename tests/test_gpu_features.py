@@ -1,10 +1,12 @@
-"""GPU parity of the learned correction's input features (68 per cell) against a
+"""GPU parity of the learned correction's input features (76 per cell) against a
 numpy reconstruction from the state, the residual and the mesh.  Per cell: W,
 slopes times |Omega|^(1/2), R dt_imp / |Omega| and the DF factor, scaled by the
 free stream (rho, rho c, rho c, rho c^2); then the three face neighbours in
 stored face order (face k opposite vertex k), with wall (mirror) and far-field
-(free stream on inflow, copy on outflow) ghosts across boundary faces.  The
-GPU rounds to bfloat16, so the bound is 2^-8 relative."""
+(free stream on inflow, copy on outflow) ghosts across boundary faces; then
+the fine residual summed over the cell's parent and grandparent, times
+dt_imp (|Omega_I| / |Omega|)^(1/2) / |Omega_I|, scaled like W.  The GPU rounds
+to bfloat16, so the bound is 2^-8 relative."""
 import numpy as np
 import pytest
 
@@ -76,7 +78,7 @@ def test_features_match_numpy(cg):
     cn = np.asarray(m["cell_nodes"], np.int64)
     nb, faces = face_neighbours(cn)
     btag = {tuple(sorted(r)): int(t) for r, t in zip(np.asarray(m["bface_nodes"]), m["bface_tag"])}
-    E = np.empty((n, 68))
+    E = np.empty((n, 76))
     for i in range(n):
         E[i, :17] = block(W[i], G[i], h[i], R[i] * dti[i] / V[i], al[i])
         for k in range(3):
@@ -92,6 +94,19 @@ def test_features_match_numpy(cg):
             tag = btag[tuple(sorted(faces[i, k]))]
             Wg, Gg = _ghost(tag, w, nrm, W[i], G[i])
             E[i, 17 * (k + 1):17 * (k + 2)] = block(Wg, Gg, h[i], np.zeros(4), al[i])
+    # restricted residuals of the parent (level 1) and grandparent (level 2)
+    p1 = np.asarray(m["parents"][0], np.int64)
+    p2 = np.asarray(m["parents"][1], np.int64)
+    n1, n2 = p1.max() + 1, p2.max() + 1
+    R1, V1 = np.zeros((n1, 4)), np.zeros(n1)
+    np.add.at(R1, p1, R)
+    np.add.at(V1, p1, V)
+    R2, V2 = np.zeros((n2, 4)), np.zeros(n2)
+    np.add.at(R2, p2, R1)
+    np.add.at(V2, p2, V1)
+    I, J = p1, p2[p1]
+    E[:, 68:72] = R1[I] * (dti * np.sqrt(V1[I] / V) / V1[I])[:, None] / sc
+    E[:, 72:76] = R2[J] * (dti * np.sqrt(V2[J] / V) / V2[J])[:, None] / sc
     err = np.abs(X - E)
     bound = 2.0 ** -8 * np.abs(E) + 1e-30
     assert np.all(err <= bound), (np.unravel_index(np.argmax(err - bound), err.shape), np.max(err / (np.abs(E) + 1e-30)))

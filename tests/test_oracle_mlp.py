@@ -9,7 +9,7 @@ from oracle import mlp
 
 
 def test_parameter_count():
-    assert mlp.N_PARAMS == 8836
+    assert mlp.N_PARAMS == 9348
 
 
 def test_gelu_values_and_derivative():
@@ -25,12 +25,12 @@ def test_gelu_values_and_derivative():
 def test_gradient_against_finite_differences():
     rng = np.random.default_rng(3)
     theta = mlp.init_params(1) + 0.01 * rng.standard_normal(mlp.N_PARAMS)
-    X = rng.standard_normal((16, 68))
+    X = rng.standard_normal((16, 76))
     Y = rng.standard_normal((16, 4))
     g = mlp.grad(theta, X, Y)
     idx = rng.choice(mlp.N_PARAMS, 60, replace=False)
     # include every bias block and the last layer
-    idx = np.concatenate([idx, [64 * 68, 64 * 68 + 63, 8836 - 1, 8836 - 5, 8836 - 10]])
+    idx = np.concatenate([idx, [64 * 76, 64 * 76 + 63, 9348 - 1, 9348 - 5, 9348 - 10]])
     h = 1e-6
     for k in idx:
         e = np.zeros_like(theta)
