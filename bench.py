@@ -843,8 +843,33 @@ def learned_leg(cgks, stream, collect_at=(0, 20, 80), collect_cycles=2, train_st
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     theta = ctx.cgks_mlp_get_params()
+    # the network forward on the 65,536 rows of one learned cycle: the fused
+    # tcgen05 kernel (tensor memory) against the mma.sync GEMM chain
+    nrow, reps = 65536, 50
+    Xd = torch.randn((nrow, cgks.N_IN), device="cuda").to(torch.bfloat16).contiguous()
+    Pd = torch.empty((nrow, 4), dtype=torch.float32, device="cuda")
+    fwd = {}
+    with torch.cuda.stream(stream):
+        for impl, name in ((0, "tcgen05"), (1, "mma_sync")):
+            ctx.cgks_mlp_select(impl)
+            for _ in range(5):
+                ctx.cgks_mlp_forward(Xd, Pd)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.cgks_mlp_forward(Xd, Pd)
+            e1.record(stream)
+            e1.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / reps
+            flops = 2.0 * nrow * (cgks.N_IN * 64 + 64 * 64 + 64 * 4)
+            fwd[name] = {"us": us, "tflops": flops / (us * 1e-6) / 1e12,
+                         "input_gbs": nrow * (cgks.N_IN * 2 + 16) / (us * 1e-6) / 1e9}
+    ctx.cgks_mlp_select(0)
+    ctx.cgks_synchronize()
+    fwd["rows"] = nrow
+    fwd["speedup_tcgen05"] = fwd["mma_sync"]["us"] / fwd["tcgen05"]["us"]
     ctx.close()
-    out = {"config": cfg,
+    out = {"config": cfg, "forward": fwd,
            "train": {"meshes": len(specs), "mach": [round(s["mach"], 3) for s in specs],
                      "cells": len(W0), "rows": int(rows), "collected_at_cycles": list(collect_at),
                      "cycles_per_collection": collect_cycles, "setup_s": t_setup, "collect_s": t_collect,
