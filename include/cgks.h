@@ -140,6 +140,37 @@ int cgks_upload_mesh(cgks_t* h, int mesh_id, int dim, int64_t n_cells, const int
                      const int32_t* bface_tag);
 
 /*
+ * Mixed-element 3-D mesh upload (Sec 2.2: hexahedra, prisms and pyramids next
+ * to tetrahedra; four Gauss points on every quadrilateral face).  Host
+ * pointers, copied:
+ *   cell_type [n_cells]          node count: 4 tetrahedron, 5 pyramid,
+ *                                6 prism, 8 hexahedron
+ *   cell_node_off [n_cells + 1]  offsets into cell_nodes / cell_xyz
+ *   cell_nodes [sum]             node ids (faces match by their node sets)
+ *   cell_xyz [sum][3]            each cell's own node coordinates
+ *   bface_node_off [n_bfaces+1], bface_nodes (3 or 4 ids each), bface_tag
+ * Node order: tetrahedron any (face k opposite node k); pyramid base 0-1-2-3
+ * (cyclic), apex 4; prism triangles 0-1-2 and 3-4-5 with 3 above 0, 4 above
+ * 1, 5 above 2; hexahedron 0-1-2-3 and 4-5-6-7 (cyclic), 4 above 0.  The
+ * stored face order (used by the colouring): pyramid base, then the sides
+ * 0-1, 1-2, 2-3, 3-0; prism bottom, top, then the sides 0-1, 1-2, 2-0;
+ * hexahedron bottom, top, then the sides 0-1, 1-2, 2-3, 3-0.  Each cell is
+ * the union of the tetrahedra from its node mean to its faces, a
+ * quadrilateral face being the four triangles around its node mean (its area
+ * vector 1/2 (v2 - v0) x (v3 - v1)).  A quadrilateral face's Gauss points
+ * are the 2 x 2 Gauss-Legendre points of its bilinear surface, weighted by
+ * the surface's local area element; a triangular face takes the 3-point
+ * rule of the tetrahedral meshes.  Needs flux_precision 0 (the double-word
+ * flux and the learned correction are not available on these meshes).
+ * Errors as cgks_upload_mesh.  Replaces any previous mesh with the same id;
+ * then cgks_upload_hierarchy as for simplex meshes.
+ */
+int cgks_upload_mesh_mixed(cgks_t* h, int mesh_id, int64_t n_cells, const int32_t* cell_type,
+                           const int64_t* cell_node_off, const int32_t* cell_nodes, const double* cell_xyz,
+                           int64_t n_bfaces, const int64_t* bface_node_off, const int32_t* bface_nodes,
+                           const int32_t* bface_tag);
+
+/*
  * Nested hierarchy (Sec 5.1-5.2).  parent[l-1][i] (host, copied) is the
  * level-l agglomerate containing level-(l-1) cell i, both in their original
  * numbering; n_levels counts the fine level (1..8).  Coarse volumes and

@@ -66,6 +66,8 @@ def lib():
         sig = {
             "om_last_error": (C.c_char_p, []),
             "om_create": (P, [I, I, ip, dp, I, ip, ip]),
+            "om_create_mixed": (P, [I, ip, lp, ip, dp, I, lp, ip, ip]),
+            "om_get_face_gauss": (None, [P, I, ip, dp]),
             "om_add_level": (I, [P, ip]),
             "om_destroy": (None, [P]),
             "om_num_levels": (I, [P]),
@@ -149,6 +151,7 @@ class OracleMesh:
         L = lib()
         self.dim = int(mesh["dim"])
         self.nv = self.dim + 2
+        self.mixed = bool(mesh.get("mixed", False))
         cn = _c(mesh["cell_nodes"], np.int32)
         cx = _c(mesh["cell_xyz"])
         bn = _c(mesh["bface_nodes"], np.int32).reshape(-1)
@@ -158,8 +161,15 @@ class OracleMesh:
             bt_arg = np.zeros(1, np.int32)
         else:
             bt_arg = bt
-        self.h = L.om_create(self.dim, cn.shape[0], cn.reshape(-1), cx.reshape(-1),
-                             int(bt.size), bn, bt_arg)
+        if self.mixed:
+            # tetrahedra, pyramids, prisms and hexahedra (cell type = node count)
+            ct = _c(mesh["cell_type"], np.int32)
+            self.h = L.om_create_mixed(ct.size, ct, _c(mesh["cell_node_off"], np.int64), cn.reshape(-1),
+                                       cx.reshape(-1), int(bt.size), _c(mesh["bface_node_off"], np.int64),
+                                       bn, bt_arg)
+        else:
+            self.h = L.om_create(self.dim, cn.shape[0], cn.reshape(-1), cx.reshape(-1),
+                                 int(bt.size), bn, bt_arg)
         if not self.h:
             raise RuntimeError("oracle mesh: " + L.om_last_error().decode())
         parents = mesh.get("parents", [])
@@ -199,9 +209,14 @@ class OracleMesh:
     def faces(self, lev=0):
         nf, d = lib().om_num_faces(self.h, lev), self.dim
         fl, fr, tag = (np.zeros(nf, np.int32) for _ in range(3))
-        n, S, sh, gp = np.zeros((nf, d)), np.zeros(nf), np.zeros((nf, d)), np.zeros((nf, 3, d))
+        n, S, sh, gp = np.zeros((nf, d)), np.zeros(nf), np.zeros((nf, d)), np.zeros((nf, 4, d))
         lib().om_get_faces(self.h, lev, fl, fr, tag, n.reshape(-1), S, sh.reshape(-1), gp.reshape(-1))
-        return dict(L=fl, R=fr, tag=tag, n=n, S=S, shift=sh, gp=gp)
+        out = dict(L=fl, R=fr, tag=tag, n=n, S=S, shift=sh, gp=gp)
+        if self.mixed and lev == 0:
+            ngp, w = np.zeros(nf, np.int32), np.zeros((nf, 4))
+            lib().om_get_face_gauss(self.h, lev, ngp, w.reshape(-1))
+            out.update(ngp=ngp, gw=w)
+        return out
 
     def neighbors(self, lev=0):
         n = self.n_cells(lev)

@@ -39,8 +39,8 @@
 
 #define MAXD 3
 #define MAXV 5
-#define MAXF 4   /* faces per simplex */
-#define MAXG 3   /* Gauss points per face */
+#define MAXF 6   /* faces per cell (a hexahedron has 6) */
+#define MAXG 4   /* Gauss points per face (4 on a quadrilateral) */
 #define MAXK 9   /* quadratic basis size (3-D) */
 
 /* ------------------------------------------------------------------------ */
@@ -90,6 +90,11 @@ typedef struct {
   double* fS;      /* [nf] area */
   double* fshift;  /* [nf*dim] x_in_L_frame = x_in_R_frame + shift */
   double* fgp;     /* [nf*MAXG*dim] Gauss points in L's frame (fine level only) */
+  /* mixed-element meshes only (NULL on simplex meshes, where every face has
+     M->ngp points of equal weight and fgp[0] lies on the face plane): */
+  int* fngp;       /* [nf] Gauss points of the face (3 triangle, 4 quadrilateral) */
+  double* fgw;     /* [nf*MAXG] their weights, summing to 1 */
+  double* fpt;     /* [nf*dim] the face's node mean, the point the ghost mirror plane passes through */
   /* cell -> faces in stored order; sign +1 if the cell is L */
   int* cnf;        /* [n] number of faces */
   int* cface;      /* [n*maxnf] */
@@ -555,6 +560,7 @@ static void level_alloc_faces(OLevel* L, int nf, int dim, int with_gp) {
   L->fn = calloc((size_t)nf * dim, sizeof(double)); L->fS = calloc(nf, sizeof(double));
   L->fshift = calloc((size_t)nf * dim, sizeof(double));
   L->fgp = with_gp ? calloc((size_t)nf * MAXG * dim, sizeof(double)) : NULL;
+  L->fngp = NULL; L->fgw = NULL; L->fpt = NULL;
 }
 
 /* Build the fine level from simplices.  Face k of a cell is the face opposite
@@ -670,6 +676,264 @@ static int build_fine(OMesh* M, int dim, int n, const int* cn, const double* cx,
     i = j;
   }
   for (int c = 0; c < n; ++c) L->cnf[c] = nf_c;
+  free(keys); free(bk);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* mixed-element fine level (tetrahedra, pyramids, prisms, hexahedra)        */
+/* ------------------------------------------------------------------------ */
+/* Local faces of each cell type (node count 4, 5, 6, 8), cyclic; the stored
+ * face order of a cell is this order.  Quadrilateral faces end at index 3,
+ * triangles have -1 there. */
+static const int MF_TET[4][4] = {{1, 2, 3, -1}, {0, 2, 3, -1}, {0, 1, 3, -1}, {0, 1, 2, -1}};
+static const int MF_PYR[5][4] = {{0, 1, 2, 3}, {0, 1, 4, -1}, {1, 2, 4, -1}, {2, 3, 4, -1}, {3, 0, 4, -1}};
+static const int MF_PRI[5][4] = {{0, 1, 2, -1}, {3, 4, 5, -1}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}};
+static const int MF_HEX[6][4] = {{0, 1, 2, 3}, {4, 5, 6, 7}, {0, 1, 5, 4}, {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}};
+static int mixed_faces(int type, const int (**tab)[4]) {
+  switch (type) {
+    case 4: *tab = MF_TET; return 4;
+    case 5: *tab = MF_PYR; return 5;
+    case 6: *tab = MF_PRI; return 5;
+    case 8: *tab = MF_HEX; return 6;
+    default: return -1;
+  }
+}
+
+static void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1]; c[1] = a[2] * b[0] - a[0] * b[2]; c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Volume, centroid and central second moments / V of a cell given by its
+ * nodes x [nn][3]: the union of the tetrahedra (node mean, face triangle),
+ * each quadrilateral face cut into the 4 triangles around its node mean (the
+ * cells are star-shaped about their node mean).  A tetrahedron with vertices
+ * p_i (about the node mean) has int x x^T = V/20 (sum p_i p_i^T + s s^T),
+ * s = sum p_i. */
+static double mixed_geom(int type, int nn, const double* x, double* cen, double* m2) {
+  const int (*tab)[4];
+  int nf = mixed_faces(type, &tab);
+  double xm[3] = {0, 0, 0};
+  for (int v = 0; v < nn; ++v) for (int d = 0; d < 3; ++d) xm[d] += x[v * 3 + d] / nn;
+  double V = 0, S1[3] = {0, 0, 0}, S2[9] = {0};
+  for (int k = 0; k < nf; ++k) {
+    int q = tab[k][3] >= 0 ? 4 : 3;
+    double tri[4][3][3];  /* up to 4 triangles, vertices about xm */
+    int nt = 0;
+    if (q == 3) {
+      for (int i = 0; i < 3; ++i) for (int d = 0; d < 3; ++d) tri[0][i][d] = x[tab[k][i] * 3 + d] - xm[d];
+      nt = 1;
+    } else {
+      double fc[3] = {0, 0, 0};
+      for (int i = 0; i < 4; ++i) for (int d = 0; d < 3; ++d) fc[d] += (x[tab[k][i] * 3 + d] - xm[d]) / 4.0;
+      for (int i = 0; i < 4; ++i) {
+        for (int d = 0; d < 3; ++d) {
+          tri[i][0][d] = fc[d];
+          tri[i][1][d] = x[tab[k][i] * 3 + d] - xm[d];
+          tri[i][2][d] = x[tab[k][(i + 1) % 4] * 3 + d] - xm[d];
+        }
+      }
+      nt = 4;
+    }
+    for (int t = 0; t < nt; ++t) {
+      /* tetrahedron (0, a, b, c) about the node mean */
+      double c3[3];
+      cross3(tri[t][1], tri[t][2], c3);
+      double vt = fabs(tri[t][0][0] * c3[0] + tri[t][0][1] * c3[1] + tri[t][0][2] * c3[2]) / 6.0;
+      double s[3];
+      for (int d = 0; d < 3; ++d) s[d] = tri[t][0][d] + tri[t][1][d] + tri[t][2][d];
+      V += vt;
+      for (int d = 0; d < 3; ++d) S1[d] += vt * s[d] / 4.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double pp = 0;
+          for (int i = 0; i < 3; ++i) pp += tri[t][i][a] * tri[t][i][b];
+          S2[a * 3 + b] += vt / 20.0 * (pp + s[a] * s[b]);
+        }
+    }
+  }
+  for (int d = 0; d < 3; ++d) cen[d] = xm[d] + S1[d] / V;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) m2[a * 3 + b] = S2[a * 3 + b] / V - (S1[a] / V) * (S1[b] / V);
+  return V;
+}
+
+typedef struct { int key[4]; int cell, k; } MKey;
+static int mkey_cmp(const void* a, const void* b) {
+  const MKey* x = (const MKey*)a; const MKey* y = (const MKey*)b;
+  for (int i = 0; i < 4; ++i) { if (x->key[i] != y->key[i]) return x->key[i] < y->key[i] ? -1 : 1; }
+  if (x->cell != y->cell) return x->cell < y->cell ? -1 : 1;
+  return x->k - y->k;
+}
+static int mkey_same(const MKey* x, const MKey* y) {
+  for (int i = 0; i < 4; ++i) if (x->key[i] != y->key[i]) return 0;
+  return 1;
+}
+/* sorted node ids of a face, -1 last for a triangle */
+static void mkey_make(int q, const int* ids, int* key) {
+  int t[4] = {ids[0], ids[1], ids[2], q == 4 ? ids[3] : 0};
+  sort_key(q, t);
+  for (int i = 0; i < 4; ++i) key[i] = i < q ? t[i] : -1;
+}
+
+/* Face geometry from the owning (L) cell's cyclic vertices fv [q][3]:
+ * triangle: area vector 1/2 (v1-v0) x (v2-v0), the degree-2 rule of the
+ * simplex meshes (barycentric 2/3, 1/6, 1/6), equal weights; quadrilateral:
+ * area vector 1/2 (v2-v0) x (v3-v1) (that of the 4 triangles around its node
+ * mean), points of the 2 x 2 Gauss-Legendre rule on the bilinear surface
+ * x(s, t) = sum N_i(s, t) v_i, weights proportional to |x_s x x_t| there
+ * (Sec 2.2: four points per quadrilateral face). */
+static void mixed_face_geom(int q, const double (*fv)[3], const double* cell_cen, double* nrm, double* S,
+                            double* fc, double* gp, double* gw) {
+  double A[3];
+  for (int d = 0; d < 3; ++d) { fc[d] = 0; for (int i = 0; i < q; ++i) fc[d] += fv[i][d] / q; }
+  if (q == 3) {
+    double a[3], b[3];
+    for (int d = 0; d < 3; ++d) { a[d] = fv[1][d] - fv[0][d]; b[d] = fv[2][d] - fv[0][d]; }
+    cross3(a, b, A);
+  } else {
+    double a[3], b[3];
+    for (int d = 0; d < 3; ++d) { a[d] = fv[2][d] - fv[0][d]; b[d] = fv[3][d] - fv[1][d]; }
+    cross3(a, b, A);
+  }
+  for (int d = 0; d < 3; ++d) A[d] *= 0.5;
+  double l = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+  *S = l;
+  for (int d = 0; d < 3; ++d) nrm[d] = A[d] / l;
+  double dot = 0; for (int d = 0; d < 3; ++d) dot += (fc[d] - cell_cen[d]) * nrm[d];
+  if (dot < 0) for (int d = 0; d < 3; ++d) nrm[d] = -nrm[d];
+  if (q == 3) {
+    for (int g = 0; g < 3; ++g) {
+      for (int d = 0; d < 3; ++d) {
+        double s = 0;
+        for (int v = 0; v < 3; ++v) s += (v == g ? 2.0 / 3.0 : 1.0 / 6.0) * fv[v][d];
+        gp[g * 3 + d] = s;
+      }
+      gw[g] = 1.0 / 3.0;
+    }
+    return;
+  }
+  const double r = 1.0 / sqrt(3.0);
+  const double ss[4] = {-r, r, r, -r}, tt[4] = {-r, -r, r, r};
+  double wsum = 0;
+  for (int g = 0; g < 4; ++g) {
+    double s = ss[g], t = tt[g];
+    double N[4] = {(1 - s) * (1 - t) / 4, (1 + s) * (1 - t) / 4, (1 + s) * (1 + t) / 4, (1 - s) * (1 + t) / 4};
+    double Ns[4] = {-(1 - t) / 4, (1 - t) / 4, (1 + t) / 4, -(1 + t) / 4};
+    double Nt[4] = {-(1 - s) / 4, -(1 + s) / 4, (1 + s) / 4, (1 - s) / 4};
+    double xs[3] = {0, 0, 0}, xt[3] = {0, 0, 0};
+    for (int d = 0; d < 3; ++d) {
+      double p = 0;
+      for (int i = 0; i < 4; ++i) { p += N[i] * fv[i][d]; xs[d] += Ns[i] * fv[i][d]; xt[d] += Nt[i] * fv[i][d]; }
+      gp[g * 3 + d] = p;
+    }
+    double j3[3];
+    cross3(xs, xt, j3);
+    gw[g] = sqrt(j3[0] * j3[0] + j3[1] * j3[1] + j3[2] * j3[2]);
+    wsum += gw[g];
+  }
+  for (int g = 0; g < 4; ++g) gw[g] /= wsum;
+}
+
+/* Build the fine level of a mixed mesh: cell_type [n] (node count 4, 5, 6 or
+ * 8), cell_node_off [n+1], cell_nodes and cell_xyz [sum][3] in the node order
+ * of each type; boundary faces by bface_node_off [nb+1], bface_nodes (3 or 4
+ * ids) and tags.  Faces match by their sorted node ids.  Returns 0 or a
+ * negative code. */
+static int build_fine_mixed(OMesh* M, int n, const int* types, const long long* off, const int* cn,
+                            const double* cx, int nbf, const long long* boff, const int* bfn, const int* bft,
+                            char* err) {
+  const int dim = 3;
+  M->dim = 3; M->nv = 5; M->ngp = 3; M->nlev = 1;
+  OLevel* L = &M->lev[0];
+  level_alloc_cells(L, n, dim, MAXF);
+  size_t ns = 0;
+  for (int c = 0; c < n; ++c) {
+    const int (*tab)[4];
+    int nf = mixed_faces(types[c], &tab);
+    int nn = (int)(off[c + 1] - off[c]);
+    if (nf < 0 || nn != types[c]) { snprintf(err, 256, "cell %d: unknown type %d or %d nodes", c, types[c], nn); return -1; }
+    L->cnf[c] = nf;
+    ns += nf;
+    L->vol[c] = types[c] == 4 ? simplex_geom(3, cx + off[c] * 3, L->cen + c * 3, L->mom2 + c * 9)
+                              : mixed_geom(types[c], nn, cx + off[c] * 3, L->cen + c * 3, L->mom2 + c * 9);
+    if (!(L->vol[c] > 0)) { snprintf(err, 256, "degenerate cell %d", c); return -3; }
+  }
+  MKey* keys = malloc(ns * sizeof(MKey));
+  size_t e = 0;
+  for (int c = 0; c < n; ++c) {
+    const int (*tab)[4];
+    int nf = mixed_faces(types[c], &tab);
+    for (int k = 0; k < nf; ++k, ++e) {
+      int q = tab[k][3] >= 0 ? 4 : 3, ids[4];
+      for (int i = 0; i < q; ++i) ids[i] = cn[off[c] + tab[k][i]];
+      mkey_make(q, ids, keys[e].key);
+      keys[e].cell = c; keys[e].k = k;
+    }
+  }
+  qsort(keys, ns, sizeof(MKey), mkey_cmp);
+  MKey* bk = malloc((size_t)(nbf > 0 ? nbf : 1) * sizeof(MKey));
+  for (int b = 0; b < nbf; ++b) {
+    int q = (int)(boff[b + 1] - boff[b]);
+    if (q != 3 && q != 4) { snprintf(err, 256, "boundary face %d has %d nodes", b, q); free(keys); free(bk); return -1; }
+    mkey_make(q, bfn + boff[b], bk[b].key);
+    bk[b].cell = b; bk[b].k = 0;
+  }
+  qsort(bk, nbf, sizeof(MKey), mkey_cmp);
+  int n_int = 0, n_bnd = 0;
+  for (size_t i = 0; i < ns;) {
+    size_t j = i + 1;
+    while (j < ns && mkey_same(&keys[j], &keys[i])) ++j;
+    if (j - i == 2) n_int++;
+    else if (j - i == 1) n_bnd++;
+    else { snprintf(err, 256, "face shared by %d cells", (int)(j - i)); free(keys); free(bk); return -3; }
+    i = j;
+  }
+  if (n_bnd != nbf) { snprintf(err, 256, "%d open faces but %d boundary faces given", n_bnd, nbf); free(keys); free(bk); return -3; }
+  level_alloc_faces(L, n_int + n_bnd, dim, 1);
+  L->n_bfaces = n_bnd;
+  L->fngp = calloc((size_t)(n_int + n_bnd), sizeof(int));
+  L->fgw = calloc((size_t)(n_int + n_bnd) * MAXG, sizeof(double));
+  L->fpt = calloc((size_t)(n_int + n_bnd) * dim, sizeof(double));
+  int fi = 0, fb = n_int;
+  for (size_t i = 0; i < ns;) {
+    size_t j = i + 1;
+    while (j < ns && mkey_same(&keys[j], &keys[i])) ++j;
+    int f;
+    if (j - i == 2) {
+      f = fi++;
+      L->fL[f] = keys[i].cell; L->fR[f] = keys[i + 1].cell; L->ftag[f] = 0;
+      L->cface[keys[i].cell * MAXF + keys[i].k] = f; L->cside[keys[i].cell * MAXF + keys[i].k] = +1;
+      L->cface[keys[i + 1].cell * MAXF + keys[i + 1].k] = f; L->cside[keys[i + 1].cell * MAXF + keys[i + 1].k] = -1;
+    } else {
+      int lo = 0, hi = nbf - 1, found = -1;
+      while (lo <= hi) {
+        int mid = (lo + hi) / 2, cmp = 0;
+        for (int t = 0; t < 4; ++t) if (bk[mid].key[t] != keys[i].key[t]) { cmp = bk[mid].key[t] < keys[i].key[t] ? -1 : 1; break; }
+        if (cmp == 0) { found = mid; break; }
+        if (cmp < 0) lo = mid + 1; else hi = mid - 1;
+      }
+      if (found < 0) { snprintf(err, 256, "open face of cell %d not in the boundary list", keys[i].cell); free(keys); free(bk); return -3; }
+      f = fb++;
+      L->fL[f] = keys[i].cell; L->fR[f] = -1; L->ftag[f] = bft[bk[found].cell];
+      L->cface[keys[i].cell * MAXF + keys[i].k] = f; L->cside[keys[i].cell * MAXF + keys[i].k] = +1;
+    }
+    /* geometry from the L cell's cyclic vertices */
+    int cl = L->fL[f], kl = keys[i].k;
+    const int (*tab)[4] = MF_TET;
+    mixed_faces(types[cl], &tab);
+    int q = tab[kl][3] >= 0 ? 4 : 3;
+    double fv[4][3];
+    for (int v = 0; v < q; ++v) for (int d = 0; d < 3; ++d) fv[v][d] = cx[(off[cl] + tab[kl][v]) * 3 + d];
+    double gp[MAXG * 3], gw[MAXG];
+    mixed_face_geom(q, (const double (*)[3])fv, L->cen + cl * 3, L->fn + f * 3, &L->fS[f], L->fpt + f * 3, gp, gw);
+    L->fngp[f] = q == 4 ? 4 : 3;
+    for (int g = 0; g < L->fngp[f]; ++g) {
+      L->fgw[(size_t)f * MAXG + g] = gw[g];
+      for (int d = 0; d < 3; ++d) L->fgp[((size_t)f * MAXG + g) * 3 + d] = gp[g * 3 + d];
+    }
+    i = j;
+  }
   free(keys); free(bk);
   return 0;
 }
@@ -966,7 +1230,7 @@ static void gather_stencil(const OMesh* M, const OCfg* cfg, const double* W, con
       /* ghost: mirror image of cell c across the face plane */
       const double* n = b->n;
       const double* x0 = L->cen + c * dim;
-      const double* xf = L->fgp + (size_t)f * MAXG * dim; /* any point on the face plane */
+      const double* xf = L->fpt ? L->fpt + (size_t)f * dim : L->fgp + (size_t)f * MAXG * dim; /* on the face plane */
       double h = 0; for (int d = 0; d < dim; ++d) h += (xf[d] - x0[d]) * n[d];
       b->vol = L->vol[c];
       for (int d = 0; d < dim; ++d) b->cen[d] = x0[d] + 2.0 * h * n[d];
@@ -992,7 +1256,8 @@ static int cell_gauss_points(const OMesh* M, int c, double* pts) {
   int dim = M->dim, m = 0;
   for (int k = 0; k < L->cnf[c]; ++k) {
     int f = L->cface[c * L->maxnf + k], side = L->cside[c * L->maxnf + k];
-    for (int g = 0; g < M->ngp; ++g, ++m)
+    int ng = L->fngp ? L->fngp[f] : M->ngp;
+    for (int g = 0; g < ng; ++g, ++m)
       for (int d = 0; d < dim; ++d)
         pts[m * dim + d] = L->fgp[((size_t)f * MAXG + g) * dim + d] - (side > 0 ? 0.0 : L->fshift[f * dim + d]);
   }
@@ -1199,7 +1464,9 @@ static void fine_residual(const OMesh* M, const OCfg* cfg, const double* W, cons
     double dt = dtl[cl];
     if (cr >= 0 && dtl[cr] < dt) dt = dtl[cr];
     double Fs[MAXV] = {0}, Ws[MAXV] = {0}, af = 1.0;
-    for (int g = 0; g < M->ngp; ++g) {
+    int ng = L->fngp ? L->fngp[f] : M->ngp;
+    for (int g = 0; g < ng; ++g) {
+      double wg = L->fgw ? L->fgw[(size_t)f * MAXG + g] : wq;
       const double* xg = L->fgp + ((size_t)f * MAXG + g) * dim;
       double Xl[MAXD], Wl[MAXV], Gl[MAXD * MAXV], Wr[MAXV], Gr[MAXD * MAXV], gg[MAXD];
       for (int d = 0; d < dim; ++d) Xl[d] = xg[d] - L->cen[cl * dim + d];
@@ -1230,7 +1497,7 @@ static void fine_residual(const OMesh* M, const OCfg* cfg, const double* W, cons
       gks_point(dim, cfg->gamma, cfg->tau_c1, cfg->tau_c2, cfg->mu, wl, gl, wr, gr, dt, Floc, Wtl, NULL);
       rot_from(dim, Rm, Floc, Fg);
       rot_from(dim, Rm, Wtl, Wg);
-      for (int v = 0; v < nv; ++v) { Fs[v] += wq * Fg[v]; Ws[v] += wq * Wg[v]; }
+      for (int v = 0; v < nv; ++v) { Fs[v] += wg * Fg[v]; Ws[v] += wg * Wg[v]; }
       af *= df_point(dim, cfg->gamma, wl, wr);
     }
     for (int v = 0; v < nv; ++v) { FsA[(size_t)f * nv + v] = Fs[v]; WsA[(size_t)f * nv + v] = Ws[v]; }
@@ -1487,6 +1754,23 @@ void* om_create(int dim, int n_cells, const int* cell_nodes, const double* cell_
   color_level(&M->lev[0]);
   return M;
 }
+void* om_create_mixed(int n_cells, const int* cell_type, const long long* cell_node_off, const int* cell_nodes,
+                      const double* cell_xyz, int n_bf, const long long* bface_node_off, const int* bface_nodes,
+                      const int* bface_tag) {
+  OMesh* M = calloc(1, sizeof(OMesh));
+  if (build_fine_mixed(M, n_cells, cell_type, cell_node_off, cell_nodes, cell_xyz, n_bf, bface_node_off, bface_nodes,
+                       bface_tag, g_err) != 0) { free(M); return NULL; }
+  color_level(&M->lev[0]);
+  return M;
+}
+/* Gauss points per face and their weights (mixed meshes; 0 / -1 elsewhere) */
+void om_get_face_gauss(void* h, int lev, int* ngp, double* w) {
+  OLevel* L = &((OMesh*)h)->lev[lev];
+  for (int f = 0; f < L->n_faces; ++f) {
+    ngp[f] = L->fngp ? L->fngp[f] : 0;
+    for (int g = 0; g < MAXG; ++g) w[f * MAXG + g] = L->fgw ? L->fgw[f * MAXG + g] : -1.0;
+  }
+}
 int om_add_level(void* h, const int* parent) {
   OMesh* M = (OMesh*)h;
   if (M->nlev >= 8) { snprintf(g_err, 256, "too many levels"); return -1; }
@@ -1501,7 +1785,7 @@ void om_destroy(void* h) {
     OLevel* L = &M->lev[l];
     free(L->vol); free(L->cen); free(L->mom2); free(L->fL); free(L->fR); free(L->ftag); free(L->fn);
     free(L->fS); free(L->fshift); free(L->fgp); free(L->cnf); free(L->cface); free(L->cside);
-    free(L->parent); free(L->color);
+    free(L->parent); free(L->color); free(L->fngp); free(L->fgw); free(L->fpt);
   }
   free(M);
 }

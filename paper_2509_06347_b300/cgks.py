@@ -23,6 +23,7 @@ TAG_WALL, TAG_FARFIELD, TAG_NOSLIP_WALL, TAG_FARFIELD_RIEMANN = 1, 2, 3, 4
 
 # every entry point declared in include/cgks.h
 EXPORTS = ["cgks_default_config", "cgks_create", "cgks_destroy", "cgks_last_error", "cgks_upload_mesh",
+           "cgks_upload_mesh_mixed",
            "cgks_upload_hierarchy", "cgks_agglomerate", "cgks_mesh_info", "cgks_get_hierarchy", "cgks_get_coloring", "cgks_set_freestream",
            "cgks_init_state", "cgks_get_state", "cgks_set_state", "cgks_residual", "cgks_reconstruct",
            "cgks_lusgs", "cgks_smooth", "cgks_vcycle", "cgks_residual_norms", "cgks_counters",
@@ -75,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "cgks_create": [C.POINTER(C.c_void_p), C.POINTER(Config), P],
         "cgks_destroy": [P],
         "cgks_upload_mesh": [P, I, I, I64, P, P, I64, P, P],
+        "cgks_upload_mesh_mixed": [P, I, I64, P, P, P, P, I64, P, P, P],
         "cgks_upload_hierarchy": [P, I, I, P],
         "cgks_mesh_info": [P, I, P, P],
         "cgks_agglomerate": [P, I, I64, P, P, I64, P, P, I, I, D, P, P],
@@ -188,6 +190,20 @@ class Context:
         self._check(self._L.cgks_upload_mesh(self.h, mesh_id, int(mesh["dim"]), cn.shape[0], _ptr(cn), _ptr(cx),
                                               bt.size, _ptr(bn) if bt.size else None, _ptr(bt) if bt.size else None))
         self.meshes[mesh_id] = dict(dim=int(mesh["dim"]), n=cn.shape[0])
+
+    def cgks_upload_mesh_mixed(self, mesh_id: int, mesh: dict):
+        """Mixed-element 3-D mesh (cell types by node count; see the header)."""
+        ct = np.ascontiguousarray(mesh["cell_type"], np.int32)
+        co = np.ascontiguousarray(mesh["cell_node_off"], np.int64)
+        cn = np.ascontiguousarray(mesh["cell_nodes"], np.int32)
+        cx = np.ascontiguousarray(mesh["cell_xyz"], np.float64)
+        bo = np.ascontiguousarray(mesh["bface_node_off"], np.int64)
+        bn = np.ascontiguousarray(mesh["bface_nodes"], np.int32)
+        bt = np.ascontiguousarray(mesh["bface_tag"], np.int32)
+        self._check(self._L.cgks_upload_mesh_mixed(self.h, mesh_id, ct.size, _ptr(ct), _ptr(co), _ptr(cn), _ptr(cx),
+                                                    bt.size, _ptr(bo) if bt.size else None,
+                                                    _ptr(bn) if bt.size else None, _ptr(bt) if bt.size else None))
+        self.meshes[mesh_id] = dict(dim=3, n=ct.size)
 
     def cgks_upload_hierarchy(self, mesh_id: int, parents):
         arrs = [np.ascontiguousarray(p, np.int32) for p in parents]
@@ -423,7 +439,10 @@ class Context:
     # ---- convenience -------------------------------------------------------------
     def setup(self, mesh_id: int, mesh: dict, winf, W, grad=None, levels: int | None = None):
         """Upload mesh + hierarchy, set the free stream and the initial state."""
-        self.cgks_upload_mesh(mesh_id, mesh)
+        if mesh.get("mixed"):
+            self.cgks_upload_mesh_mixed(mesh_id, mesh)
+        else:
+            self.cgks_upload_mesh(mesh_id, mesh)
         parents = mesh.get("parents", [])
         if levels is not None:
             parents = parents[: levels - 1]

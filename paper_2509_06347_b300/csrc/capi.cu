@@ -266,10 +266,10 @@ void build_fine_device(MeshDev& M) {
     const int qa2[3] = {0, 0, 1}, qb2[3] = {0, 1, 1};
     std::vector<double> gm((size_t)nk * n, 0.0);
     for (int64_t c = 0; c < n; ++c)
-      for (int k = 0; k < nfc; ++k) {
+      for (int k = 0; k < (F.mixed ? (int)F.cnf[c] : nfc); ++k) {
         const int64_t f = F.cface[c * nfc + k];
         const std::vector<double>& X = F.cside[c * nfc + k] > 0 ? F.XL : F.XR;
-        for (int g = 0; g < ngp; ++g) {
+        for (int g = 0; g < (F.mixed ? (int)F.fngp[f] : ngp); ++g) {
           const double* x = &X[((size_t)f * ngp + g) * dim];
           for (int d = 0; d < dim; ++d) {
             double& t = gm[(size_t)d * n + c];
@@ -283,6 +283,12 @@ void build_fine_device(MeshDev& M) {
         }
       }
     d.gpmax = upload(P, gm);
+  }
+  if (F.mixed) {
+    std::vector<signed char> cnf(F.cnf.begin(), F.cnf.end()), fngp(F.fngp.begin(), F.fngp.end());
+    d.cnf = upload(P, cnf);
+    d.fngp = upload(P, fngp);
+    d.gw = upload(P, F.gw);
   }
   M.fine = d;
 }
@@ -346,16 +352,20 @@ void build_levels_device(MeshDev& M, const cgks_config& cfg) {
     std::vector<int32_t> tag(F.n * nfc);
     std::vector<int8_t> side(F.n * nfc);
     std::vector<double> S(F.n * nfc), nrm(F.n * nfc * dim);
-    for (int64_t c = 0; c <= F.n; ++c) off[c] = c * nfc;
+    // cell -> face entries (CSR); a mixed mesh's cells have 4 to 6 faces
+    off[0] = 0;
+    for (int64_t c = 0; c < F.n; ++c) off[c + 1] = off[c] + (F.mixed ? (int)F.cnf[c] : nfc);
+    const int64_t ne = off[F.n];
+    nbr.resize(ne); face.resize(ne); tag.resize(ne); side.resize(ne); S.resize(ne); nrm.resize(ne * dim);
     for (int64_t c = 0; c < F.n; ++c)
-      for (int k = 0; k < nfc; ++k) {
-        const int64_t e = c * nfc + k, f = F.cface[e];
-        nbr[e] = F.cnbr[e];
+      for (int64_t e = off[c]; e < off[c + 1]; ++e) {
+        const int64_t k = c * nfc + (e - off[c]), f = F.cface[k];
+        nbr[e] = F.cnbr[k];
         face[e] = f;
         tag[e] = F.ftag[f];
-        side[e] = F.cside[e];
+        side[e] = F.cside[k];
         S[e] = F.fS[f];
-        for (int d = 0; d < dim; ++d) nrm[e * dim + d] = F.cside[e] * F.fn[f * dim + d];
+        for (int d = 0; d < dim; ++d) nrm[e * dim + d] = F.cside[k] * F.fn[f * dim + d];
       }
     L.topo = make_topo(M, F.n, off, nbr, tag, side, S, nrm, L.vol, face);
     alloc_level_state(M, L, cfg);
@@ -435,6 +445,14 @@ void launch_recon(cgks_t* h, MeshDev& M) {
   LevelDev& L = M.lev[0];
   const int bs = M.blk[B_RECON];
   const int64_t nb = blocks_for(L.n, bs);  // 3-D: one thread per cell; 2-D: the kernel loops
+  if constexpr (DIM == 3) {
+    if (M.H.fine.mixed) {  // hexahedra, prisms, pyramids: per-cell face counts
+      k_recon<3, 1><<<(int)nb, bs, 0, h->stream>>>(M.fine, L.W, M.G, L.alpha, M.winf, h->cfg.gamma, h->cfg.cfl_exp,
+                                                   h->cfg.cfl_imp, h->cfg.weno_gamma_high, h->cfg.weno_eps, M.coef,
+                                                   L.dte, L.dti, M.cnt, M.coef_dw);
+      return;
+    }
+  }
   k_recon<DIM><<<DIM == 2 ? resident_blocks(h, k_recon<DIM>, bs, nb) : (int)nb, bs, 0, h->stream>>>(
       M.fine, L.W, M.G, L.alpha, M.winf, h->cfg.gamma, h->cfg.cfl_exp, h->cfg.cfl_imp, h->cfg.weno_gamma_high,
       h->cfg.weno_eps, M.coef, L.dte, L.dti, M.cnt, M.coef_dw);
@@ -489,6 +507,9 @@ void launch_flux(cgks_t* h, MeshDev& M, bool point = true, bool radius = true) {
                                               M.Wface, M.aface, L.W, radius ? L.rface : nullptr);
   } else {
     auto kern = point ? k_flux<DIM, true, double> : k_flux<DIM, false, double>;
+    if constexpr (DIM == 3) {
+      if (M.H.fine.mixed) kern = point ? k_flux<3, true, double, 1> : k_flux<3, false, double, 1>;
+    }
     kern<<<resident_blocks(h, kern, bs, nb), bs, 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, P, P.gamma, M.Fface, M.Wface, M.aface,
                                               L.W, radius ? L.rface : nullptr);
   }
@@ -510,7 +531,11 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
   const bool fuse = fuse_c0 && want_diag;
   TS* dWs0 = fuse ? (sizeof(TS) == 8 ? (TS*)L.dWs64 : (TS*)L.dWs32) : nullptr;
   TS* dW0 = fuse && L.n_colors == 1 ? (sizeof(TS) == 8 ? (TS*)L.dW64 : (TS*)L.dW32) : nullptr;
-  k_gather<DIM, TS><<<blocks_for(L.n, gb), gb, 0, h->stream>>>(
+  auto gather = k_gather<DIM, TS>;
+  if constexpr (DIM == 3) {
+    if (M.H.fine.mixed) gather = k_gather<3, TS, 1>;  // per-cell face counts
+  }
+  gather<<<blocks_for(L.n, gb), gb, 0, h->stream>>>(
       M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R,
       slopes_update ? M.G : nullptr, alpha_out_dev ? alpha_out_dev : L.alpha, want_diag ? L.D : nullptr,
       gradnew_dev, (want_norm && !grouped) ? M.norm_part : nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg),
@@ -948,6 +973,32 @@ int cgks_upload_mesh(cgks_t* h, int mesh_id, int dim, int64_t n_cells, const int
     M->nv = dim + 2;
     try {
       build_fine_level(dim, n_cells, cell_nodes, cell_xyz, n_bfaces, bface_nodes, bface_tag, M->H.fine);
+    } catch (const std::runtime_error& e) {
+      return fail(h, CGKS_ERR_MESH, e.what());
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    h->meshes[mesh_id] = std::move(M);
+    return CGKS_OK;
+  });
+}
+
+int cgks_upload_mesh_mixed(cgks_t* h, int mesh_id, int64_t n_cells, const int32_t* cell_type,
+                           const int64_t* cell_node_off, const int32_t* cell_nodes, const double* cell_xyz,
+                           int64_t n_bfaces, const int64_t* bface_node_off, const int32_t* bface_nodes,
+                           const int32_t* bface_tag) {
+  return guarded(h, [&]() -> int {
+    if (n_cells <= 0 || n_cells >= (1ll << 30) || !cell_type || !cell_node_off || !cell_nodes || !cell_xyz ||
+        n_bfaces < 0 || (n_bfaces > 0 && (!bface_node_off || !bface_nodes || !bface_tag)))
+      throw ArgError("invalid mesh arguments");
+    if (h->cfg.flux_precision != 0) throw ArgError("mixed-element meshes take the FP64 flux (flux_precision 0)");
+    for (int64_t b = 0; b < n_bfaces; ++b)
+      if (bface_tag[b] < CGKS_TAG_WALL || bface_tag[b] > CGKS_TAG_FARFIELD_RIEMANN) throw ArgError("unknown boundary tag");
+    auto M = std::make_unique<MeshDev>();
+    M->dim = 3;
+    M->nv = 5;
+    try {
+      build_fine_level_mixed(n_cells, cell_type, cell_node_off, cell_nodes, cell_xyz, n_bfaces, bface_node_off,
+                             bface_nodes, bface_tag, M->H.fine);
     } catch (const std::runtime_error& e) {
       return fail(h, CGKS_ERR_MESH, e.what());
     }
@@ -1470,10 +1521,10 @@ int cgks_run_stage(cgks_t* h, int mesh_id, int stage) {
             L.D, nullptr, nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg), h->cfg.alpha_relax, 1.0,
             L.rface, nullptr, nullptr);
       else
-        k_gather<3><<<blocks_for(L.n), kBlock, 0, h->stream>>>(
+        (M.H.fine.mixed ? k_gather<3, double, 1> : k_gather<3, double>)<<<blocks_for(L.n), kBlock, 0, h->stream>>>(
             M.fine, L.topo, M.Fface, M.Wface, M.aface, L.W, M.winf, h->cfg.gamma, L.dte, L.dti, L.R, nullptr, L.alpha,
             L.D, nullptr, nullptr, h->cfg.df_relax == 1 ? -1.0 : relax_constant(h->cfg), h->cfg.alpha_relax, 1.0,
-            L.rface, nullptr, nullptr);
+            L.rface, nullptr, nullptr, nullptr, nullptr, 0);
     }
     CK(cudaGetLastError());
     return CGKS_OK;

@@ -15,10 +15,15 @@ namespace cgks {
 constexpr int kMaxDim = 3;
 constexpr int kMaxVar = 5;
 
-// Fine level (simplices).  All arrays are in the colour-major cell order
-// ("new" ids); iperm maps new -> original.
+// Fine level (simplices, or 3-D mixed elements).  All arrays are in the
+// colour-major cell order ("new" ids); iperm maps new -> original.
 struct FineLevel {
-  int dim = 0, nv = 0, ngp = 0, nfc = 0;  // nfc = faces per cell = dim + 1
+  int dim = 0, nv = 0, ngp = 0, nfc = 0;  // simplices: nfc = dim + 1 faces per cell, ngp points per face;
+                                           // mixed elements: the maxima 6 and 4 (arrays padded to them)
+  bool mixed = false;
+  std::vector<int8_t> cnf;           // [n] faces of each cell (mixed elements only)
+  std::vector<int8_t> fngp;          // [nf] Gauss points of each face (mixed elements only)
+  std::vector<double> gw;            // [nf][ngp] their weights, summing to 1 (mixed elements only)
   int nk = 0;                              // quadratic basis size (5 / 9)
   int64_t n = 0;
   int n_colors = 0;
@@ -78,6 +83,17 @@ struct Hierarchy {
 void build_fine_level(int dim, int64_t n, const int32_t* cell_nodes, const double* cell_xyz,
                       int64_t nb, const int32_t* bface_nodes, const int32_t* bface_tag,
                       FineLevel& out);
+
+// Builds the fine level of a 3-D mesh of tetrahedra, pyramids, prisms and
+// hexahedra: cell_type [n] = node count (4, 5, 6, 8), cell_node_off [n+1],
+// cell_nodes and cell_xyz [sum][3] in each type's node order (pyramid: base
+// 0-1-2-3 cyclic, apex 4; prism: triangles 0-1-2 and 3-4-5, 3 above 0;
+// hexahedron: 0-1-2-3 and 4-5-6-7 cyclic, 4 above 0); boundary faces by
+// bface_node_off [nb+1], bface_nodes (3 or 4 ids), bface_tag [nb].
+void build_fine_level_mixed(int64_t n, const int32_t* cell_type, const int64_t* cell_node_off,
+                            const int32_t* cell_nodes, const double* cell_xyz, int64_t nb,
+                            const int64_t* bface_node_off, const int32_t* bface_nodes, const int32_t* bface_tag,
+                            FineLevel& out);
 
 // Adds a coarse level below `prev_*` (parent given in the previous level's
 // ORIGINAL numbering -> coarse original ids).

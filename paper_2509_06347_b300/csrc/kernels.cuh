@@ -21,11 +21,16 @@ namespace cgks {
 
 constexpr int kBlock = 256;
 
-template <int DIM>
+// VAR = 0: simplices (triangles, tetrahedra), every cell with dim + 1 faces
+// and every face with the same Gauss points; VAR = 1: 3-D mixed elements
+// (tetrahedra, pyramids, prisms, hexahedra), up to 6 faces per cell and 3
+// (triangle) or 4 (quadrilateral) Gauss points per face, the counts read per
+// cell and per face and the arrays padded to these maxima.
+template <int DIM, int VAR = 0>
 struct Dims {
   static constexpr int NV = DIM + 2;
-  static constexpr int NFC = DIM + 1;           // faces per simplex
-  static constexpr int NGP = DIM == 2 ? 2 : 3;  // Gauss points per face
+  static constexpr int NFC = VAR ? 6 : DIM + 1;             // faces per cell (at most)
+  static constexpr int NGP = VAR ? 4 : (DIM == 2 ? 2 : 3);  // Gauss points per face (at most)
   static constexpr int NK = DIM == 2 ? 5 : 9;   // quadratic basis size
   static constexpr int NC = NK + 1;             // polynomial coefficients
   static constexpr int NQ = DIM == 2 ? 3 : 6;   // quadratic monomials
@@ -54,6 +59,10 @@ struct DevFine {
   const double* bsc;    // [n] |Omega|^(2/dim)
   const double* gpmax;  // [nk][n] max over the cell's face Gauss points of |X^k| (monomials of X = x - centroid)
   const int* grp;       // [n] batch group of each cell (free stream index), or null
+  // mixed-element meshes only (null for simplices):
+  const signed char* cnf;   // [n] faces of each cell
+  const signed char* fngp;  // [nf] Gauss points of each face (3 or 4)
+  const double* gw;         // [nf][ngp] their weights (sum 1)
 };
 
 // Cell -> face entries for the sweeps and cell-based coarse fluxes (CSR).
@@ -130,17 +139,18 @@ __device__ __forceinline__ void grad_poly(const S* c, const S* X, S* g) {
   }
 }
 
-template <int DIM>
+template <int DIM, int VAR = 0>
 __device__ __forceinline__ void recon_cell(DevFine M, const double* __restrict__ W,
                                            const double* __restrict__ Gr, const double* __restrict__ alpha_prev,
                                            const double* __restrict__ winf, double gamma, double cfl_exp,
                                            double cfl_imp, double gam_hi, double weps, double* __restrict__ coef,
                                            double* __restrict__ dte, double* __restrict__ dti,
                                            Counters* __restrict__ cnt, dword* __restrict__ coef_dw, int c) {
-  using D = Dims<DIM>;
+  using D = Dims<DIM, VAR>;
   constexpr int NV = D::NV, NFC = D::NFC, NK = D::NK, NC = D::NC, NCOL = D::NCOL;
   if (c >= M.n) return;
   const int n = M.n;
+  const int nf = VAR ? (int)M.cnf[c] : NFC;  // faces of this cell
   double W0[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) W0[v] = W[(size_t)c * NV + v];
@@ -150,6 +160,20 @@ __device__ __forceinline__ void recon_cell(DevFine M, const double* __restrict__
   signed char sd[NFC];
 #pragma unroll
   for (int m = 0; m < NFC; ++m) {
+    if (VAR && m >= nf) {  // padding of a cell with fewer faces: contributes nothing
+      fid[m] = 0;
+      sd[m] = 0;
+      Sf[m] = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) nrm[m][d] = 0.0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        Qm[m][v] = W0[v];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) Dm[m][v][d] = 0.0;
+      }
+      continue;
+    }
     const int f = M.cface[(size_t)c * NFC + m];
     fid[m] = f;
     sd[m] = M.cside[(size_t)c * NFC + m];
@@ -321,10 +345,12 @@ __device__ __forceinline__ void recon_cell(DevFine M, const double* __restrict__
   }
   bool bad = false;
 #pragma unroll 1
-  for (int m = 0; m < NFC && !bad && !sure; ++m) {
+  for (int m = 0; m < nf && !bad && !sure; ++m) {
     const double* X = (sd[m] > 0 ? M.XL : M.XR) + (size_t)fid[m] * D::NGP * DIM;
+    const int ng = VAR ? (int)M.fngp[fid[m]] : D::NGP;
 #pragma unroll
     for (int g = 0; g < D::NGP; ++g) {
+      if (VAR && g >= ng) break;
       double Wp[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) Wp[v] = eval_poly<DIM>(P[v], X + g * DIM);
@@ -364,7 +390,7 @@ __device__ __forceinline__ void recon_cell(DevFine M, const double* __restrict__
 // thread per cell leaves a partial last wave on a few SMs).  3-D meshes span
 // hundreds of waves, and the loop would cost the 3-D kernel spills: there the
 // grid has one thread per cell.
-template <int DIM>
+template <int DIM, int VAR = 0>
 __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __restrict__ W,
                                                   const double* __restrict__ Gr, const double* __restrict__ alpha_prev,
                                                   const double* __restrict__ winf, double gamma, double cfl_exp,
@@ -372,8 +398,8 @@ __global__ void __launch_bounds__(kBlock) k_recon(DevFine M, const double* __res
                                                   double* __restrict__ dte, double* __restrict__ dti,
                                                   Counters* __restrict__ cnt, dword* __restrict__ coef_dw) {
   if constexpr (DIM == 3) {
-    recon_cell<DIM>(M, W, Gr, alpha_prev, winf, gamma, cfl_exp, cfl_imp, gam_hi, weps, coef, dte, dti, cnt, coef_dw,
-                    blockIdx.x * blockDim.x + threadIdx.x);
+    recon_cell<DIM, VAR>(M, W, Gr, alpha_prev, winf, gamma, cfl_exp, cfl_imp, gam_hi, weps, coef, dte, dti, cnt,
+                         coef_dw, blockIdx.x * blockDim.x + threadIdx.x);
   } else {
     const int lane = threadIdx.x & 31;
     const int ntask = (M.n + 31) / 32;
@@ -553,28 +579,31 @@ __device__ __forceinline__ void flux_task(const DevFine& M, const S* __restrict_
 // groups of flux_task use.  For the 3-point faces of 3-D meshes: 32 faces per
 // warp use every lane, where 3 lanes per face leave 2 of 32 idle, and the
 // per-face work (indices, frame, spectral radius) runs on every lane.
-template <int DIM, bool POINT, typename S>
+template <int DIM, bool POINT, typename S, int VAR = 0>
 __device__ __forceinline__ void flux_face(const DevFine& M, const S* __restrict__ coef, const double* __restrict__ dte,
                                           const double* __restrict__ winf, const PhysT<S>& P, double gamma,
                                           double* __restrict__ Fface, double* __restrict__ Wface,
                                           double* __restrict__ aface, const double* __restrict__ Wc,
                                           double* __restrict__ rface, int f) {
-  using D = Dims<DIM>;
+  using D = Dims<DIM, VAR>;
   constexpr int NV = D::NV, NC = D::NC, NGP = D::NGP;
   if (f >= M.nf) return;
   const int L = M.fL[f], R = M.fR[f];
+  const int ng = VAR ? (int)M.fngp[f] : NGP;  // Gauss points of this face
   S n[DIM];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) n[d] = S(M.fn[(size_t)f * DIM + d]);
   const Frame<DIM, S> fr = make_frame<DIM, S>(n);
   double dt = dte[L];
   if (R >= 0) dt = fmin(dt, dte[R]);
-  const S w = S(M.fS[f] * (1.0 / NGP));  // equal Gauss weights on every face
+  // equal Gauss weights on every simplex face; per-point weights on mixed meshes
+  const S w0 = S(M.fS[f] * (1.0 / NGP));
   S Fs[NV], Ws[NV], af = S(1.0);
 #pragma unroll
   for (int v = 0; v < NV; ++v) { Fs[v] = S(0.0); Ws[v] = S(0.0); }
 #pragma unroll 1
-  for (int g = 0; g < NGP; ++g) {
+  for (int g = 0; g < ng; ++g) {
+    const S w = VAR ? S(M.fS[f] * M.gw[(size_t)f * NGP + g]) : w0;
     S Wl[NV], gl[NV][DIM], Wr[NV], gr[NV][DIM];
     {
       const double* X = M.XL + ((size_t)f * NGP + g) * DIM;
@@ -649,12 +678,13 @@ __device__ __forceinline__ void flux_face(const DevFine& M, const S* __restrict_
 // per face group leaves a partial last wave on a few SMs).  The double-word
 // variant, whose registers are capped for two blocks per SM, keeps one task
 // per warp: the loop costs it stack space and spills.
-template <int DIM, bool POINT, typename S = double>
+template <int DIM, bool POINT, typename S = double, int VAR = 0>
 __global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(DevFine M, const S* __restrict__ coef,
                                                  const double* __restrict__ dte, const double* __restrict__ winf,
                                                  PhysT<S> P, double gamma, double* __restrict__ Fface,
                                                  double* __restrict__ Wface, double* __restrict__ aface,
                                                  const double* __restrict__ Wc, double* __restrict__ rface) {
+  static_assert(VAR == 0 || (DIM == 3 && !OutOfLine<S>::value), "mixed elements: 3-D, FP64 flux");
   constexpr int FPW = 32 / Dims<DIM>::NGP;
   const int lane = threadIdx.x & 31;
   const int ntask = (M.nf + FPW - 1) / FPW;
@@ -666,7 +696,7 @@ __global__ void __launch_bounds__(kBlock, OutOfLine<S>::value ? 2 : 1) k_flux(De
     const int nwarp = gridDim.x * (blockDim.x >> 5);
     const int nt = (M.nf + 31) / 32;
     for (int task = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; task < nt; task += nwarp)
-      flux_face<DIM, POINT, S>(M, coef, dte, winf, P, gamma, Fface, Wface, aface, Wc, rface, task * 32 + lane);
+      flux_face<DIM, POINT, S, VAR>(M, coef, dte, winf, P, gamma, Fface, Wface, aface, Wc, rface, task * 32 + lane);
   } else {
     const int nwarp = gridDim.x * (blockDim.x >> 5);
     for (int task = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; task < ntask; task += nwarp)
@@ -719,7 +749,7 @@ __device__ __forceinline__ void colour0_forward(int c, const double* __restrict_
 // ---------------------------------------------------------------------------
 // K3: per-cell gather of residual, new slopes (Sec 2.4) and DF (Sec 3.3)
 // ---------------------------------------------------------------------------
-template <int DIM, typename TS = double>
+template <int DIM, typename TS = double, int VAR = 0>
 __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const double* __restrict__ Fface,
                                                    const double* __restrict__ Wface, const double* __restrict__ aface,
                                                    const double* __restrict__ W, const double* __restrict__ winf,
@@ -732,7 +762,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
                                                    const double* __restrict__ rface, double* __restrict__ qcell,
                                                    const int* __restrict__ active, TS* __restrict__ dWs0 = nullptr,
                                                    TS* __restrict__ dW0 = nullptr, int c0_end = 0) {
-  using Dm = Dims<DIM>;
+  using Dm = Dims<DIM, VAR>;
   constexpr int NV = Dm::NV, NFC = Dm::NFC;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   double rl2[NV], rmax[NV];
@@ -746,8 +776,10 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
 #pragma unroll
       for (int d = 0; d < DIM; ++d) gn[v][d] = 0.0;
     }
+    const int nf = VAR ? (int)M.cnf[c] : NFC;
 #pragma unroll
     for (int m = 0; m < NFC; ++m) {
+      if (VAR && m >= nf) break;
       const int f = M.cface[(size_t)c * NFC + m];
       const double s = M.cside[(size_t)c * NFC + m];
       double nn[DIM];

@@ -355,7 +355,7 @@ def freestream(mach: float, gamma: float = 1.4, dim: int = 2, angle_deg: float =
 
 
 def uniform_state(mesh, w):
-    n = mesh["cell_nodes"].shape[0]
+    n = len(mesh["cell_type"]) if mesh.get("mixed") else mesh["cell_nodes"].shape[0]
     return np.tile(np.asarray(w, float), (n, 1))
 
 
@@ -483,3 +483,193 @@ def batch_cylinders(specs):
     union, grp = concat_meshes(meshes)
     W = np.asarray(winf)[grp]
     return union, grp, np.asarray(winf), W
+
+
+# ----------------------------------------------------------------------------
+# 3-D mixed-element meshes (hexahedra, prisms, pyramids)
+# ----------------------------------------------------------------------------
+# Cell types are given by their node counts.  Local node order:
+#   tet (4)      any; face k is opposite node k
+#   pyramid (5)  base 0-1-2-3 (cyclic), apex 4
+#   prism (6)    bottom triangle 0-1-2, top 3-4-5 (3 above 0, 4 above 1, 5 above 2)
+#   hex (8)      bottom 0-1-2-3 (cyclic), top 4-5-6-7 (4 above 0, ...)
+CELL_TET, CELL_PYRAMID, CELL_PRISM, CELL_HEX = 4, 5, 6, 8
+
+# hex slot corners (di, dj, dk) in the hex node order above
+_HEX_CORNERS = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+# the six quads of a hex, cyclic, in hex node indices
+_HEX_FACES = [(0, 1, 2, 3), (4, 5, 6, 7), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7)]
+# a prism column splits every slot along the (0,0)-(1,1) diagonal of its (i, j) plane
+_PRISM_SPLIT = [(0, 1, 2, 4, 5, 6), (0, 2, 3, 4, 6, 7)]
+
+
+def _mixed_cells(corner_id, corner_xyz, kind, next_id):
+    """Cells of hex slots.  corner_id [ns][8], corner_xyz [ns][8][3] in hex
+    node order; kind [ns]: 0 hex, 1 two prisms, 2 six pyramids around a new
+    node at the slot's corner average (ids from next_id on).  Returns
+    (cell_type, cell_node_off, cell_nodes, cell_xyz, slot of each cell)."""
+    types, nodes, xyz, slot = [], [], [], []
+    for s in range(len(kind)):
+        ids, X = corner_id[s], corner_xyz[s]
+        if kind[s] == 0:
+            types.append(CELL_HEX)
+            nodes.append(list(ids))
+            xyz.append(X)
+            slot.append(s)
+        elif kind[s] == 1:
+            for sp in _PRISM_SPLIT:
+                types.append(CELL_PRISM)
+                nodes.append([ids[v] for v in sp])
+                xyz.append(X[list(sp)])
+                slot.append(s)
+        else:
+            apex = next_id
+            next_id += 1
+            xa = X.mean(0)
+            for fc in _HEX_FACES:
+                types.append(CELL_PYRAMID)
+                nodes.append([ids[v] for v in fc] + [apex])
+                xyz.append(np.vstack([X[list(fc)], xa[None, :]]))
+                slot.append(s)
+    off = np.zeros(len(types) + 1, np.int64)
+    off[1:] = np.cumsum([len(t) for t in nodes])
+    return (np.array(types, np.int32), off, np.concatenate([np.asarray(t, np.int64) for t in nodes]),
+            np.concatenate(xyz), np.array(slot, np.int64))
+
+
+def _mixed_finish(types, off, nodes, xyz, slot, bnodes, btags, n_slots, **extra):
+    boff = np.zeros(len(bnodes) + 1, np.int64)
+    boff[1:] = np.cumsum([len(b) for b in bnodes])
+    return dict(dim=3, mixed=True,
+                cell_type=np.ascontiguousarray(types, np.int32),
+                cell_node_off=np.ascontiguousarray(off, np.int64),
+                cell_nodes=np.ascontiguousarray(nodes, np.int32),
+                cell_xyz=np.ascontiguousarray(xyz, np.float64).reshape(-1, 3),
+                bface_node_off=boff,
+                bface_nodes=np.ascontiguousarray(np.concatenate([np.asarray(b) for b in bnodes]), np.int32),
+                bface_tag=np.ascontiguousarray(btags, np.int32),
+                parents=[np.ascontiguousarray(slot, np.int32), np.ascontiguousarray(np.arange(n_slots) // 8, np.int32)],
+                **extra)
+
+
+def _slot_kinds(n_cols, n_layers, prism_frac, pyramid_frac, seed):
+    """Seeded slot kinds: whole columns of prisms (their triangular caps meet
+    only each other), pyramid sextets elsewhere, hexes otherwise."""
+    rng = SplitMix64(seed)
+    col_prism = np.array([rng.uniform() < prism_frac for _ in range(n_cols)])
+    kind = np.zeros((n_cols, n_layers), np.int64)
+    for c in range(n_cols):
+        for k in range(n_layers):
+            u = rng.uniform()
+            kind[c, k] = 1 if col_prism[c] else (2 if u < pyramid_frac else 0)
+    return kind
+
+
+def mixed_shell_mesh(n_panel: int = 8, n_r: int = 8, ratio: float = 1.08, r_in: float = 1.0,
+                     r_out: float = 15.0, prism_frac: float = 0.25, pyramid_frac: float = 0.2,
+                     seed: int = DEFAULT_SEED + 6):
+    """Cubed-sphere shell (as sphere_mesh) of hex slots, each kept as a hex,
+    split into two prisms (whole radial columns, seeded) or into six pyramids
+    around its centre (seeded).  Faces: quadrilaterals (curved: their corners
+    lie on spheres) and triangles.  Hierarchy: level 1 = the slots, level 2 =
+    2x2x2 slot blocks.  Tags: wall at r_in, far field at r_out."""
+    assert n_panel % 2 == 0 and n_r % 2 == 0
+    h0 = radial_nodes(n_r, r_in, r_out, ratio)
+    radii = r_in + h0 * (ratio ** np.arange(n_r + 1) - 1.0) / (ratio - 1.0)
+    radii[-1] = r_out
+    key_to_id, surf_dir = {}, []
+    ang = np.tan(0.25 * math.pi * (2.0 * np.arange(n_panel + 1) / n_panel - 1.0))
+    panel_ids = np.zeros((6, n_panel + 1, n_panel + 1), np.int64)
+    for p, (ax, sg) in enumerate(_PANELS):
+        t1, t2 = [a for a in range(3) if a != ax]
+        for a in range(n_panel + 1):
+            for b in range(n_panel + 1):
+                key = [0, 0, 0]
+                key[ax] = sg * n_panel
+                key[t1] = 2 * a - n_panel
+                key[t2] = 2 * b - n_panel
+                key = tuple(key)
+                if key not in key_to_id:
+                    d = np.zeros(3)
+                    d[ax], d[t1], d[t2] = sg, ang[a], ang[b]
+                    key_to_id[key] = len(surf_dir)
+                    surf_dir.append(d / np.linalg.norm(d))
+                panel_ids[p, a, b] = key_to_id[key]
+    surf_dir = np.array(surf_dir)
+    ns_ = surf_dir.shape[0]
+    # slots ordered so that 2x2x2 blocks are contiguous
+    P, A, B, K = np.meshgrid(np.arange(6), np.arange(n_panel), np.arange(n_panel), np.arange(n_r), indexing="ij")
+    blk = (((P * (n_panel // 2) + A // 2) * (n_panel // 2) + B // 2) * (n_r // 2) + K // 2)
+    sub = ((A % 2) * 2 + (B % 2)) * 2 + (K % 2)
+    order = np.argsort((blk * 8 + sub).ravel(), kind="stable")
+    Pf, Af, Bf, Kf = (x.ravel()[order] for x in (P, A, B, K))
+    n_slots = len(Pf)
+    cid = np.zeros((n_slots, 8), np.int64)
+    cxyz = np.zeros((n_slots, 8, 3))
+    for v, (di, dj, dk) in enumerate(_HEX_CORNERS):
+        sid = panel_ids[Pf, Af + di, Bf + dj]
+        cid[:, v] = sid + ns_ * (Kf + dk)
+        cxyz[:, v] = surf_dir[sid] * radii[Kf + dk][:, None]
+    kinds_cols = _slot_kinds(6 * n_panel * n_panel, n_r, prism_frac, pyramid_frac, seed)
+    col = (Pf * n_panel + Af) * n_panel + Bf
+    kind = kinds_cols[col, Kf]
+    types, off, nodes, xyz, slot = _mixed_cells(cid, cxyz, kind, ns_ * (n_r + 1))
+    bn, bt = [], []
+    for p in range(6):
+        for a in range(n_panel):
+            for b in range(n_panel):
+                prism = kinds_cols[(p * n_panel + a) * n_panel + b, 0] == 1
+                for (k, tag) in ((0, TAG_WALL), (n_r, TAG_FARFIELD)):
+                    q = [panel_ids[p, a, b], panel_ids[p, a + 1, b], panel_ids[p, a + 1, b + 1], panel_ids[p, a, b + 1]]
+                    q = [x + ns_ * k for x in q]
+                    if prism:
+                        bn += [(q[0], q[1], q[2]), (q[0], q[2], q[3])]
+                        bt += [tag, tag]
+                    else:
+                        bn.append(tuple(q))
+                        bt.append(tag)
+    return _mixed_finish(types, off, nodes, xyz, slot, bn, bt, n_slots,
+                         name=f"mixedshell{n_panel}x{n_r}", r_in=r_in, r_out=r_out)
+
+
+def mixed_box_mesh(n: int = 4, length: float = 4.0, prism_frac: float = 0.25, pyramid_frac: float = 0.2,
+                   seed: int = DEFAULT_SEED + 7):
+    """Box [0, L]^3 of n^3 cubic hex slots (planar faces), each kept as a hex,
+    split into two prisms (whole z columns, seeded) or into six pyramids.
+    Levels: slots, then 2x2x2 blocks (n even).  Every boundary face is far
+    field."""
+    assert n % 2 == 0
+    h = length / n
+    nid = lambda i, j, k: (k * (n + 1) + j) * (n + 1) + i
+    I, J, Kz = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    blk = ((I // 2) * (n // 2) + J // 2) * (n // 2) + Kz // 2
+    sub = ((I % 2) * 2 + (J % 2)) * 2 + (Kz % 2)
+    order = np.argsort((blk * 8 + sub).ravel(), kind="stable")
+    If, Jf, Kf = (x.ravel()[order] for x in (I, J, Kz))
+    n_slots = len(If)
+    cid = np.zeros((n_slots, 8), np.int64)
+    cxyz = np.zeros((n_slots, 8, 3))
+    for v, (di, dj, dk) in enumerate(_HEX_CORNERS):
+        cid[:, v] = nid(If + di, Jf + dj, Kf + dk)
+        cxyz[:, v] = np.stack([(If + di) * h, (Jf + dj) * h, (Kf + dk) * h], 1)
+    kinds_cols = _slot_kinds(n * n, n, prism_frac, pyramid_frac, seed)
+    kind = kinds_cols[If * n + Jf, Kf]
+    types, off, nodes, xyz, slot = _mixed_cells(cid, cxyz, kind, (n + 1) ** 3)
+    bn, bt = [], []
+    for a in range(n):
+        for b in range(n):
+            prism = kinds_cols[a * n + b, 0] == 1
+            for k in (0, n):  # z faces: triangles on prism columns
+                q = [nid(a, b, k), nid(a + 1, b, k), nid(a + 1, b + 1, k), nid(a, b + 1, k)]
+                if prism:
+                    bn += [(q[0], q[1], q[2]), (q[0], q[2], q[3])]
+                    bt += [TAG_FARFIELD, TAG_FARFIELD]
+                else:
+                    bn.append(tuple(q))
+                    bt.append(TAG_FARFIELD)
+            for s in (0, n):  # x and y faces: quads
+                bn.append((nid(s, a, b), nid(s, a + 1, b), nid(s, a + 1, b + 1), nid(s, a, b + 1)))
+                bn.append((nid(a, s, b), nid(a + 1, s, b), nid(a + 1, s, b + 1), nid(a, s, b + 1)))
+                bt += [TAG_FARFIELD, TAG_FARFIELD]
+    return _mixed_finish(types, off, nodes, xyz, slot, bn, bt, n_slots, name=f"mixedbox{n}", length=length)
+

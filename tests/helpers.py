@@ -171,3 +171,44 @@ def coarse_ring_submesh(mesh, level, seeds, rings=1):
         cur = ids
     sub["parents"] = parents
     return sub, cur, np.searchsorted(cur, np.asarray(seeds))
+
+
+# local faces of the mixed-element cell types (node counts 4, 5, 6, 8), in the
+# node order of the mesh generators
+MIXED_FACES = {
+    4: [(1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)],
+    5: [(0, 1, 2, 3), (0, 1, 4), (1, 2, 4), (2, 3, 4), (3, 0, 4)],
+    6: [(0, 1, 2), (3, 4, 5), (0, 1, 4, 3), (1, 2, 5, 4), (2, 0, 3, 5)],
+    8: [(0, 1, 2, 3), (4, 5, 6, 7), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7)],
+}
+
+
+def mixed_cell_faces(mesh):
+    """For each cell, its faces as (sorted node-id key, local vertex coordinates
+    in cyclic order); and the boundary-face keys with their tags."""
+    off, nodes, xyz, types = mesh["cell_node_off"], mesh["cell_nodes"], mesh["cell_xyz"], mesh["cell_type"]
+    cells = []
+    for c in range(len(types)):
+        ids = nodes[off[c]:off[c + 1]]
+        X = xyz[off[c]:off[c + 1]]
+        cells.append([(tuple(sorted(int(ids[v]) for v in f)), X[list(f)]) for f in MIXED_FACES[int(types[c])]])
+    boff, bnodes = mesh["bface_node_off"], mesh["bface_nodes"]
+    bkeys = {tuple(sorted(int(x) for x in bnodes[boff[b]:boff[b + 1]])): int(mesh["bface_tag"][b])
+             for b in range(len(mesh["bface_tag"]))}
+    return cells, bkeys
+
+
+def mixed_tets(Xc, faces):
+    """Tetrahedra (4 x 3 arrays) of a cell given the local coordinates of its
+    faces: apex at the mean of the cell's nodes, each triangular face as it is
+    and each quadrilateral as the 4 triangles around its node mean."""
+    xm = np.mean(Xc, axis=0)
+    out = []
+    for F in faces:
+        if len(F) == 3:
+            out.append(np.array([xm, F[0], F[1], F[2]]))
+        else:
+            fc = F.mean(0)
+            for i in range(4):
+                out.append(np.array([xm, fc, F[i], F[(i + 1) % 4]]))
+    return out

@@ -99,12 +99,10 @@ def test_bad_network_is_disabled_by_the_judge(cg):
     np.testing.assert_array_equal(nl, np_)
 
 
-def test_trained_network_gain_is_measured(cg, capsys):
-    """Train on trajectories at Mach 2 and 4, evaluate at the held-out Mach 3:
-    report the network's judge error and the residual / time of learned versus
-    plain cycles.  The fallback policy must keep the learned run at least as
-    good as 2x the plain residual."""
-    import time
+@pytest.fixture(scope="module")
+def trained(cg):
+    """A network trained on trajectories at Mach 2 and 4 (this file's small
+    cylinder), for evaluation at the held-out Mach 3."""
     m = mesh()
     ctx = cg.Context()
     ctx.cgks_mlp_set_params(mlp.init_params(1))
@@ -114,17 +112,55 @@ def test_trained_network_gain_is_measured(cg, capsys):
         ctx.setup(10 + i, m, w, synth.uniform_state(m, w))
         ctx.cgks_mlp_collect(10 + i, 60, 1)
     losses = ctx.cgks_mlp_train(1500, 4096, 1e-3, seed=5)
-    assert losses[-50:].mean() < losses[:5].mean()
     theta = ctx.cgks_mlp_get_params()
     ctx.close()
+    return theta, losses
+
+
+def test_trained_network_gain_is_measured(cg, trained, capsys):
+    """Evaluate the trained network at the held-out Mach 3: report its judge
+    error and the residual / time of learned versus plain cycles.  The policy
+    must hold either way: a judge error above 0.5 disables the network on the
+    first judge cycle and the run then equals the plain MIXED run; otherwise
+    learned cycles run."""
+    import time
+    theta, losses = trained
+    assert losses[-50:].mean() < losses[:5].mean()
     out = {}
     for mode in (cg.MIXED, cg.LEARNED):
         torch.cuda.synchronize()
         t0 = time.time()
         rc, W, norms, st = run(cg, 3.0, 200, mode, theta=theta)
-        out[mode] = (time.time() - t0, norms[-1, 0, 0] / norms[0, 0, 0], st)
+        out[mode] = (time.time() - t0, norms[-1, 0, 0] / norms[0, 0, 0], st, norms)
         assert rc == 0
+    st = out[cg.LEARNED][2]
     with capsys.disabled():
         print(f"\nlearned-correction gain at held-out Mach 3: plain {out[cg.MIXED][:2]}, "
-              f"learned {out[cg.LEARNED]}")
+              f"learned {out[cg.LEARNED][:3]}")
+    if st["judge_error"] > 0.5:
+        assert st["disabled"] and st["learned"] == 0
+        np.testing.assert_array_equal(out[cg.LEARNED][3], out[cg.MIXED][3])
+    else:
+        assert not st["disabled"] and st["learned"] > 0
     assert out[cg.LEARNED][1] <= 2.0 * out[cg.MIXED][1]
+
+
+def test_learned_cycles_run_when_not_disabled(cg, trained):
+    """With the judge kept from disabling the network, the trained network's
+    corrections are applied (learned cycles run, judge cycles every 20) and
+    the state stays finite."""
+    theta, _ = trained
+    rc, W, norms, st = run(cg, 3.0, 60, cg.LEARNED, theta=theta, learned_max_error=1e30)
+    assert st["learned"] > 0 and st["judge"] >= 3 and not st["disabled"]
+    assert np.all(np.isfinite(W)) and np.all(np.isfinite(norms))
+
+
+@pytest.mark.xfail(strict=False, reason="measured: at held-out Mach the trained per-cell network explains "
+                   "about a third of the coarse correction (judge error 0.78-0.83 on the 65,536-cell "
+                   "cylinder at Mach 2.5/5.5/7.5), above the 0.5 the judge accepts")
+def test_trained_network_passes_the_judge(cg, trained):
+    """The goal the learned correction does not reach yet: a trained network
+    whose held-out judge error is below the 0.5 that keeps it enabled."""
+    theta, _ = trained
+    rc, W, norms, st = run(cg, 3.0, 40, cg.LEARNED, theta=theta)
+    assert st["judge_error"] <= 0.5 and st["learned"] > 0
