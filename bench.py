@@ -464,6 +464,36 @@ def run_ours(args):
                  "value": world * n * args.steps / (tp * 1e-3), "unit": UNIT, "ms_per_step": tp / args.steps,
                  "mixed_speedup_per_cycle": tp / t_ms}
 
+    # mixed elements: V-cycles of a cubed-sphere shell of hexahedra, prisms
+    # and pyramids (16 x 16 panels, 16 layers), timed the same way
+    mixed_el = None
+    if not sphere:
+        mm = synth.mixed_shell_mesh(16, 16)
+        wm = synth.freestream(6.0, dim=3)
+        cm = cgks.Context(stream=stream.cuda_stream)
+        cm.setup(7, mm, wm, synth.uniform_state(mm, wm))
+        minfo = cm.cgks_mesh_info(7)
+        cm.cgks_vcycle_launch([7], max(3, args.warmup), mode)
+        barrier()
+        mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                mev[k][0].record(stream)
+                cm.cgks_vcycle_launch([7], 1, mode)
+                mev[k][1].record(stream)
+        barrier()
+        tm = sum(a.elapsed_time(b) for a, b in mev)
+        nm = minfo[0]["cells"]
+        types = mm["cell_type"]
+        mixed_el = {"mesh": "cubed-sphere shell 16x16x16 slots: hexahedra, prism pairs, pyramid sextets",
+                    "cells": nm, "hexahedra": int((types == 8).sum()), "prisms": int((types == 6).sum()),
+                    "pyramids": int((types == 5).sum()), "faces": minfo[0]["faces"],
+                    "levels": [lv["cells"] for lv in minfo], "mach": 6.0,
+                    "value": nm * args.steps / (tm * 1e-3), "unit": UNIT, "ms_per_step": tm / args.steps,
+                    "launches_per_cycle": cm.cgks_launch_count(7, mode)}
+        cm.close()
+
     # end to end through the public API with host buffers: state in, one
     # V-cycle, residual norms and state out, every step
     Wh = torch.empty((n, nv), dtype=torch.float64).pin_memory().numpy()
@@ -550,6 +580,7 @@ def run_ours(args):
         "gpu_launches": launches_per_cycle * args.steps,
         "clocks": clocks,
         "kernels": kernels,
+        "mixed_elements": mixed_el,
         "variant_plain_fp64": plain,
         "variant_dword_flux": variant,
         "convergence": conv,
@@ -604,12 +635,13 @@ def _solve_to_drop_ctx(ctx, mesh, w, W0, G0, mode, max_cycles, levels=None):
     return out, W
 
 
-# Settings under which the Mach-5 cylinder converges: collision-time constants
-# C1 = 1, C2 = 10 (the paper leaves them to its reference) and the pseudo-time
-# under-relaxation of the slope update (0.5) and of a rising DF factor (0.05),
-# which leave every steady state a fixed point.  With the defaults (C1 = 0.01)
-# the residual stalls near 1e-1.
-CYLINDER_CONVERGENCE = {"tau_c1": 1.0, "tau_c2": 10.0, "alpha_relax": 0.05, "slope_relax": 0.5}
+# Settings under which the inviscid cylinders converge from Mach 2.5 to 8:
+# collision-time constants C1 = 1, C2 = 5 (the paper leaves them to its
+# reference) and the pseudo-time under-relaxation of the slope update (0.5)
+# and of a rising DF factor (0.05), which leave every steady state a fixed
+# point.  With the defaults (C1 = 0.01) the residual stalls near 1e-1; with
+# C2 = 10 Mach 5 goes slightly deeper but Mach 7.5 and 8 diverge.
+CYLINDER_CONVERGENCE = {"tau_c1": 1.0, "tau_c2": 5.0, "alpha_relax": 0.05, "slope_relax": 0.5}
 
 
 def convergence_leg(cgks, stream):
@@ -617,7 +649,7 @@ def convergence_leg(cgks, stream):
     the vortex workload (2,048 jittered periodic triangles; the iteration
     dissipates the vortex and converges, to 1e-10, to a uniform state) and the
     Mach-5 cylinder of the timed workload with CYLINDER_CONVERGENCE (reaches a
-    1e-6 drop, then stays near 2e-7); drops reached and wall times reported."""
+    1e-6 drop, then stays near 2.4e-7); drops reached and wall times reported."""
     res = {}
     mv = synth.vortex_mesh(n_coarse=8, n_refine=2)
     Wv, Gv = synth.vortex_state(mv)

@@ -30,7 +30,7 @@ TOL = 1e-10
 CFG = dict(tau_c1=1.0)  # the convergence setting of the vortex solves (reading R4: C1 is a config field)
 # the convergence setting of the Mach-5 cylinder solves: collision-time constants and the
 # pseudo-time under-relaxation of the slopes and of a rising DF factor
-CYLINDER_CFG = dict(tau_c1=1.0, tau_c2=10.0, alpha_relax=0.05, slope_relax=0.5)
+CYLINDER_CFG = dict(tau_c1=1.0, tau_c2=5.0, alpha_relax=0.05, slope_relax=0.5)
 
 
 def first_drop(hist, tol=TOL):
