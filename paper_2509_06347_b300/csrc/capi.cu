@@ -90,6 +90,7 @@ struct LevelDev {
   int* iperm = nullptr;  // new -> original
   double* vol = nullptr;
   double *W = nullptr, *W0 = nullptr, *alpha = nullptr, *R = nullptr, *P = nullptr, *Rstar = nullptr;
+  double* Wb = nullptr;  // the state's second buffer: coarse smoothing steps alternate W -> Wb -> W
   double* ones = nullptr;   // DF = 1 everywhere (prolongation ablation)
   double* relax = nullptr;  // the constant that stands for DF in LU-SGS when df_relax != 1
   FaceSet faces{};
@@ -168,6 +169,7 @@ struct MlpState {
   int impl = 0;
   int* tc_err = nullptr;  // set by the tcgen05 kernel if a bounded wait gave up
   bool tc_attr = false;   // dynamic shared-memory size set for the tcgen05 kernel
+  int tc_blocks = 0;      // resident CTAs of the (persistent) tcgen05 kernel on the device
   // work buffers (rows = work_rows)
   float *Z1 = nullptr, *Z2 = nullptr, *P = nullptr, *dP = nullptr, *part = nullptr, *loss = nullptr;
   __nv_bfloat16 *A1 = nullptr, *A2 = nullptr, *dPb = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
@@ -319,6 +321,7 @@ void alloc_level_state(MeshDev& M, LevelDev& L, const cgks_config& cfg) {
   auto& P = M.pool;
   const int nv = M.nv;
   L.W = dalloc<double>(P, (size_t)L.n * nv);
+  L.Wb = dalloc<double>(P, (size_t)L.n * nv);
   L.W0 = dalloc<double>(P, (size_t)L.n * nv);
   L.alpha = dalloc<double>(P, L.n);
   L.ones = upload(P, std::vector<double>(L.n, 1.0));
@@ -555,7 +558,13 @@ void fine_residual(cgks_t* h, MeshDev& M, bool slopes_update, bool want_diag, bo
 // c0_done: the forward step of colour 0 already ran inside the kernel that
 // built R and D (fine_residual / coarse_prep with fuse_c0)
 template <int DIM, typename T>
-void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool c0_done = false) {
+// Wcur / Wnext (both null: the level's W, updated in place by a final
+// update launch): the state is read from Wcur and the guarded updates are
+// written to Wnext by the launches that finalise each colour's increments.
+void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool c0_done = false, double* Wcur = nullptr,
+            double* Wnext = nullptr) {
+  const bool fused = Wnext != nullptr;
+  double* W = fused ? Wcur : L.W;
   const double* alpha = h->cfg.df_relax == 1 ? L.alpha : L.relax;
   T* dWs = sizeof(T) == 8 ? (T*)L.dWs64 : (T*)L.dWs32;
   T* dW = sizeof(T) == 8 ? (T*)L.dW64 : (T*)L.dW32;
@@ -565,7 +574,7 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool c0_done =
     if (hi > lo)
     {
       const int b = fit_block(h, hi - lo, M.blk[B_SWEEP]);
-      k_sweep<DIM, T, 0><<<blocks_for(hi - lo, b), b, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
+      k_sweep<DIM, T, 0><<<blocks_for(hi - lo, b), b, 0, h->stream>>>(L.topo, lo, hi, W, L.R, Pf, alpha, L.D,
                                                                      L.rface, h->cfg.gamma, dWs, dW);
     }
   }
@@ -574,8 +583,8 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool c0_done =
     if (hi > lo)
     {
       const int b = fit_block(h, hi - lo, M.blk[B_SWEEP]);
-      k_sweep<DIM, T, 2><<<blocks_for(hi - lo, b), b, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
-                                                                     L.rface, h->cfg.gamma, dWs, dW);
+      k_sweep<DIM, T, 2><<<blocks_for(hi - lo, b), b, 0, h->stream>>>(
+          L.topo, lo, hi, W, L.R, Pf, alpha, L.D, L.rface, h->cfg.gamma, dWs, dW, Wnext, M.cnt);
     }
   }
   for (int c = nc - 2; c >= 0; --c) {
@@ -583,13 +592,23 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool c0_done =
     if (hi > lo)
     {
       const int b = fit_block(h, hi - lo, M.blk[B_SWEEP]);
-      k_sweep<DIM, T, 1><<<blocks_for(hi - lo, b), b, 0, h->stream>>>(L.topo, lo, hi, L.W, L.R, Pf, alpha, L.D,
-                                                                     L.rface, h->cfg.gamma, dWs, dW);
+      k_sweep<DIM, T, 1><<<blocks_for(hi - lo, b), b, 0, h->stream>>>(
+          L.topo, lo, hi, W, L.R, Pf, alpha, L.D, L.rface, h->cfg.gamma, dWs, dW, Wnext, M.cnt);
     }
   }
   const bool fine = &L == &M.lev[0];
   const bool masked = fine && !M.lgrp.empty();
   const int bu = fit_block(h, L.n, M.blk[B_UPDATE]);
+  if (fused) {
+    // every colour's update was written by its finalising launch, except a
+    // single colour's, which the colour-0 forward step finalised
+    if (c0_done && nc == 1) {
+      CK(cudaMemcpyAsync(Wnext, Wcur, (size_t)L.n * M.nv * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      k_update<DIM, T><<<blocks_for(L.n, bu), bu, 0, h->stream>>>(L.n, h->cfg.gamma, Wnext, dW, M.cnt, nullptr,
+                                                                   nullptr);
+    }
+    return;
+  }
   k_update<DIM, T><<<blocks_for(L.n, bu), bu, 0, h->stream>>>(
       L.n, h->cfg.gamma, L.W, dW, M.cnt, masked ? M.lgrp[0] : nullptr, masked ? M.active : nullptr);
 }
@@ -598,17 +617,18 @@ void sweeps(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool c0_done =
 // hold the face fluxes and spectral radii of the current state
 template <int DIM, typename TS = double>
 void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want_diag, bool fuse_c0 = false,
-                 bool faces_ready = false) {
+                 bool faces_ready = false, const double* Wc = nullptr) {
   const PhysParams p = phys(h->cfg, DIM);
   const int bf = fit_block(h, L.faces.nf, M.blk[B_FACE]), bc = fit_block(h, L.n, M.blk[B_CELL]);
+  const double* W = Wc ? Wc : L.W;  // the buffer holding the current state
   if (!faces_ready)
     k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(
-        L.faces, L.W, M.winf, p, L.Fc, want_diag ? L.rface : nullptr);
+        L.faces, W, M.winf, p, L.Fc, want_diag ? L.rface : nullptr);
   const bool fuse = fuse_c0 && want_diag;
   TS* dWs0 = fuse ? (sizeof(TS) == 8 ? (TS*)L.dWs64 : (TS*)L.dWs32) : nullptr;
   TS* dW0 = fuse && L.n_colors == 1 ? (sizeof(TS) == 8 ? (TS*)L.dW64 : (TS*)L.dW32) : nullptr;
   k_coarse_cell<DIM, TS><<<blocks_for(L.n, bc), bc, 0, h->stream>>>(
-      L.topo, L.W, L.Fc, L.rface, Pf, nullptr, h->cfg.df_relax == 1 ? L.alpha : L.relax, h->cfg.gamma, h->cfg.cfl_exp,
+      L.topo, W, L.Fc, L.rface, Pf, nullptr, h->cfg.df_relax == 1 ? L.alpha : L.relax, h->cfg.gamma, h->cfg.cfl_exp,
       h->cfg.cfl_imp, L.R, want_diag ? L.D : nullptr, dWs0, dW0, L.color_off[1]);
 }
 
@@ -656,10 +676,17 @@ void vcycle_coarse(cgks_t* h, MeshDev& M) {
     k_restrict<DIM><<<blocks_for(C.n, br), br, 0, h->stream>>>(C.n, C.ch_off, C.ch_idx, F.vol, C.vol, F.W, F.alpha,
                                                                 F.R, C.W0, C.W, C.alpha, C.Rstar);
     coarse_forcing<DIM>(h, M, C);
-    for (int s = 0; s < h->cfg.n_sweep_coarse; ++s) {
-      coarse_prep<DIM, T>(h, M, C, C.P, true, true, s == 0);
-      sweeps<DIM, T>(h, M, C, nullptr, true);
+    // the smoothing steps alternate the state between C.W and C.Wb (each
+    // colour's update is written by the launch that finalises it); after an
+    // odd number of steps the state is copied back to C.W
+    const int nsw = h->cfg.n_sweep_coarse;
+    for (int s = 0; s < nsw; ++s) {
+      double* Wcur = (s & 1) ? C.Wb : C.W;
+      double* Wnext = (s & 1) ? C.W : C.Wb;
+      coarse_prep<DIM, T>(h, M, C, C.P, true, true, s == 0, Wcur);
+      sweeps<DIM, T>(h, M, C, nullptr, true, Wcur, Wnext);
     }
+    if (nsw & 1) CK(cudaMemcpyAsync(C.W, C.Wb, (size_t)C.n * M.nv * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     if (l + 1 < M.nlev) coarse_prep<DIM>(h, M, C, C.P, false);  // R~ = R(W) + P to restrict
   }
   for (int l = M.nlev - 1; l >= 1; --l) {
@@ -1767,6 +1794,9 @@ void mlp_ensure(cgks_t* h) {
   CK(cudaMemsetAsync(S.tc_err, 0, sizeof(int), h->stream));
   if (!S.tc_attr) {
     CK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_forward_tc, kTcThreads, kTcSmem));
+    S.tc_blocks = std::max(1, occ) * h->sms;
     S.tc_attr = true;
   }
   S.ready = true;
@@ -1817,7 +1847,8 @@ void mlp_forward(cgks_t* h, int64_t rows, const __nv_bfloat16* X, float* P, bool
   const __nv_bfloat16* W = S.theta_bf;
   const int M = (int)rows;
   if (S.impl == 0) {
-    const int nb = (int)((rows + kTcRows - 1) / kTcRows);
+    const int ntiles = (int)((rows + kTcRows - 1) / kTcRows);
+    const int nb = std::min(ntiles, S.tc_blocks);  // persistent: CTAs loop over the tiles
     k_mlp_forward_tc<<<nb, kTcThreads, kTcSmem, h->stream>>>(M, X, W, S.theta, keep ? S.Z1 : nullptr,
                                                             keep ? S.A1 : nullptr, keep ? S.Z2 : nullptr,
                                                             keep ? S.A2 : nullptr, P, S.tc_err);

@@ -991,41 +991,6 @@ __device__ __forceinline__ void offdiag_term(const Topo& Tp, int e, const double
 
 // mode 0: forward (neighbours j < lo); mode 1: backward (j >= hi);
 // mode 2: the top colour, forward then dW = dW*.
-template <int DIM, typename T, int MODE>
-__global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const double* __restrict__ W,
-                                                  const double* __restrict__ R, const double* __restrict__ Pf,
-                                                  const double* __restrict__ alpha, const double* __restrict__ Dg,
-                                                  const double* __restrict__ rface, double gamma,
-                                                  T* __restrict__ dWs, T* __restrict__ dW) {
-  constexpr int NV = DIM + 2;
-  const int c = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= hi) return;
-  T acc[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = 0;
-  const T* src = MODE == 1 ? dW : dWs;
-  for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) {
-    const int j = Tp.nbr[e];
-    if (j < 0) continue;  // ghost increments are zero
-    if (MODE == 1 ? (j < hi) : (j >= lo)) continue;
-    offdiag_term<DIM, T>(Tp, e, W, src, rface, gamma, acc);
-  }
-  const T ha = (T)(0.5 * alpha[c]);
-  const T iD = T(1) / (T)Dg[c];  // as in colour0_forward
-  if (MODE == 1) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) dW[(size_t)c * NV + v] = dWs[(size_t)c * NV + v] - ha * acc[v] * iD;
-  } else {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const double rhs = -(R[(size_t)c * NV + v] + (Pf ? Pf[(size_t)c * NV + v] : 0.0));
-      const T x = ((T)rhs - ha * acc[v]) * iD;
-      dWs[(size_t)c * NV + v] = x;
-      if (MODE == 2) dW[(size_t)c * NV + v] = x;
-    }
-  }
-}
-
 // state update with the positivity guard (reading): halve up to 10 times, else drop
 template <int DIM>
 __device__ __forceinline__ int guarded_add(double gamma, double* W, const double* dW) {
@@ -1045,6 +1010,77 @@ __device__ __forceinline__ int guarded_add(double gamma, double* W, const double
     s *= 0.5;
   }
   return -1;
+}
+
+// the guarded update of cell c into Wout (the state's other buffer), as k_update
+template <int DIM, typename T>
+__device__ __forceinline__ void update_into(int c, double gamma, const double* __restrict__ W, const T* d_c,
+                                            double* __restrict__ Wout, Counters* __restrict__ cnt) {
+  constexpr int NV = DIM + 2;
+  double w[NV], d[NV];
+  bool finite = true;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    w[v] = W[(size_t)c * NV + v];
+    d[v] = (double)d_c[v];
+    finite = finite && isfinite(d[v]);
+  }
+  if (!finite) {
+    atomicAdd(&cnt->nonfinite, 1ull);
+  } else {
+    const int r = guarded_add<DIM>(gamma, w, d);
+    if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
+    if (r < 0) atomicAdd(&cnt->update_zeroed, 1ull);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Wout[(size_t)c * NV + v] = w[v];
+}
+
+// Wout (nullable): the state's other buffer.  Where this launch finalises the
+// increments of its colour (MODE 2: the last colour; MODE 1: backward), it
+// also writes the guarded update W + dW there, so that no separate update
+// launch is needed (the sweeps keep reading W).
+template <int DIM, typename T, int MODE>
+__global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const double* __restrict__ W,
+                                                  const double* __restrict__ R, const double* __restrict__ Pf,
+                                                  const double* __restrict__ alpha, const double* __restrict__ Dg,
+                                                  const double* __restrict__ rface, double gamma,
+                                                  T* __restrict__ dWs, T* __restrict__ dW,
+                                                  double* __restrict__ Wout = nullptr,
+                                                  Counters* __restrict__ cnt = nullptr) {
+  constexpr int NV = DIM + 2;
+  const int c = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= hi) return;
+  T acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0;
+  const T* src = MODE == 1 ? dW : dWs;
+  for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) {
+    const int j = Tp.nbr[e];
+    if (j < 0) continue;  // ghost increments are zero
+    if (MODE == 1 ? (j < hi) : (j >= lo)) continue;
+    offdiag_term<DIM, T>(Tp, e, W, src, rface, gamma, acc);
+  }
+  const T ha = (T)(0.5 * alpha[c]);
+  const T iD = T(1) / (T)Dg[c];  // as in colour0_forward
+  T fin[NV];  // the final increment (MODE 1, 2)
+  if (MODE == 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      fin[v] = dWs[(size_t)c * NV + v] - ha * acc[v] * iD;
+      dW[(size_t)c * NV + v] = fin[v];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double rhs = -(R[(size_t)c * NV + v] + (Pf ? Pf[(size_t)c * NV + v] : 0.0));
+      const T x = ((T)rhs - ha * acc[v]) * iD;
+      dWs[(size_t)c * NV + v] = x;
+      fin[v] = x;
+      if (MODE == 2) dW[(size_t)c * NV + v] = x;
+    }
+  }
+  if (MODE != 0 && Wout) update_into<DIM, T>(c, gamma, W, fin, Wout, cnt);
 }
 
 template <int DIM, typename T>

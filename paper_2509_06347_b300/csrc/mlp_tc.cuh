@@ -125,37 +125,56 @@ __device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_base, uint32_
   tc_commit(mbar);
 }
 
-// Bias + GELU epilogue of one layer for this thread's row: Z (fp32, nullable),
-// A (bf16 global, nullable) and the bf16 activations into the next operand
-// tile (smem, nullable) and into act[64] (registers, rounded to bf16).
-__device__ __forceinline__ void tc_epilogue(uint32_t taddr, const float* bias, int row, bool valid, float* Z,
-                                            __nv_bfloat16* A, unsigned char* next_tile, float* act) {
+// Bias + GELU epilogue of one layer for this thread's row (tensor-memory lane
+// = row of the tile): Z (fp32, nullable) and A (bf16, nullable) rows in global
+// memory, the bf16 activations into the next operand tile (smem, nullable),
+// 8 at a time as 16-byte stores, and into act[64] (rounded to bf16).
+__device__ __forceinline__ void tc_epilogue(uint32_t taddr, const float* bias, int r, int64_t row, bool valid,
+                                            float* Z, __nv_bfloat16* A, unsigned char* next_tile, float* act) {
 #pragma unroll
   for (int c0 = 0; c0 < kH; c0 += 16) {
     float v[16];
     tc_ld16(taddr + (uint32_t)c0, v);
+    __align__(16) __nv_bfloat16 a[16];
+    float z[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      const float z = v[i] + bias[c0 + i];
-      const __nv_bfloat16 a = __float2bfloat16(gelu(z));
-      act[c0 + i] = __bfloat162float(a);
-      if (valid && Z) Z[(size_t)row * kH + c0 + i] = z;
-      if (valid && A) A[(size_t)row * kH + c0 + i] = a;
-      if (next_tile)
-        *reinterpret_cast<__nv_bfloat16*>(next_tile + tc_core_off(row & (kTcRows - 1), c0 + i, kTcRows)) = a;
+      z[i] = v[i] + bias[c0 + i];
+      a[i] = __float2bfloat16(gelu(z[i]));
+      act[c0 + i] = __bfloat162float(a[i]);
+    }
+    if (valid && Z) {
+      float4* zo = reinterpret_cast<float4*>(Z + row * kH + c0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) zo[i] = make_float4(z[4 * i], z[4 * i + 1], z[4 * i + 2], z[4 * i + 3]);
+    }
+    const uint4* ap = reinterpret_cast<const uint4*>(a);
+    if (valid && A) {
+      uint4* ao = reinterpret_cast<uint4*>(A + row * kH + c0);
+      ao[0] = ap[0];
+      ao[1] = ap[1];
+    }
+    if (next_tile) {
+      *reinterpret_cast<uint4*>(next_tile + tc_core_off(r, c0, kTcRows)) = ap[0];
+      *reinterpret_cast<uint4*>(next_tile + tc_core_off(r, c0 + 8, kTcRows)) = ap[1];
     }
   }
 }
 
-// X bf16 [M][76]; Wbf the bf16 parameter copy, theta the fp32 masters (biases);
-// outputs (each nullable except P): Z1, Z2 fp32 [M][64], A1, A2 bf16 [M][64],
-// P fp32 [M][4].  err (device int) is set to 1 if an mbarrier wait gives up.
+// Persistent: each CTA stages the weights once, then takes 128-row tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...  X bf16 [M][76] (rows of 152
+// bytes, read as 8-byte words that never straddle a row); Wbf the bf16
+// parameter copy, theta the fp32 masters (biases); outputs (each nullable
+// except P): Z1, Z2 fp32 [M][64], A1, A2 bf16 [M][64], P fp32 [M][4].  err
+// (device int) is set to 1 if an mbarrier wait gives up.
 __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(int M, const __nv_bfloat16* __restrict__ X,
                                                                const __nv_bfloat16* __restrict__ Wbf,
                                                                const float* __restrict__ theta,
                                                                float* __restrict__ Z1, __nv_bfloat16* __restrict__ A1,
                                                                float* __restrict__ Z2, __nv_bfloat16* __restrict__ A2,
                                                                float* __restrict__ P, int* __restrict__ err) {
+  static_assert(kIn % 4 == 0 && kTcK1 - kIn == 4, "rows of 4-element words, one word of padding");
+  constexpr int kW = kIn / 4;  // 8-byte words per row
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA1 = smem + kTcOffA1;
   unsigned char* sB1 = smem + kTcOffB1;
@@ -165,8 +184,8 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(int M, const __nv
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kTcOffBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcOffBar + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int row0 = blockIdx.x * kTcRows;
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  const int ntiles = (M + kTcRows - 1) / kTcRows;
+  const uint2 zero2 = make_uint2(0u, 0u);
 
   // tensor memory: one accumulator of 64 columns, allocated by warp 0
   if (warp == 0) {
@@ -179,22 +198,17 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(int M, const __nv
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // operands: the X tile (zero rows past M, zero columns 68..79), W1, W2,
-  // biases and layer 3 into shared memory
-  for (int e = tid; e < kTcRows * kTcK1; e += kTcThreads) {
-    const int r = e / kTcK1, k = e - r * kTcK1;
-    __nv_bfloat16 v = zero;
-    if (k < kIn && row0 + r < M) v = X[(size_t)(row0 + r) * kIn + k];
-    *reinterpret_cast<__nv_bfloat16*>(sA1 + tc_core_off(r, k, kTcRows)) = v;
+  // weights once per CTA: W1 [64][76] as 8-byte words (+ one zero word of
+  // K padding per row), W2 [64][64] as 16-byte words; biases and layer 3
+  for (int j = tid; j < kH * (kW + 1); j += kTcThreads) {
+    const int n = j / (kW + 1), q = j - n * (kW + 1);
+    const uint2 v = q < kW ? reinterpret_cast<const uint2*>(Wbf + oW1 + n * kIn)[q] : zero2;
+    *reinterpret_cast<uint2*>(sB1 + tc_core_off(n, 4 * q, kH)) = v;
   }
-  for (int e = tid; e < kH * kTcK1; e += kTcThreads) {
-    const int n = e / kTcK1, k = e - n * kTcK1;
-    const __nv_bfloat16 v = k < kIn ? Wbf[oW1 + n * kIn + k] : zero;
-    *reinterpret_cast<__nv_bfloat16*>(sB1 + tc_core_off(n, k, kH)) = v;
-  }
-  for (int e = tid; e < kH * kH; e += kTcThreads) {
-    const int n = e / kH, k = e - n * kH;
-    *reinterpret_cast<__nv_bfloat16*>(sB2 + tc_core_off(n, k, kH)) = Wbf[oW2 + n * kH + k];
+  for (int j = tid; j < kH * (kH / 8); j += kTcThreads) {
+    const int n = j / (kH / 8), q = j - n * (kH / 8);
+    *reinterpret_cast<uint4*>(sB2 + tc_core_off(n, 8 * q, kH)) =
+        reinterpret_cast<const uint4*>(Wbf + oW2 + n * kH)[q];
   }
   for (int e = tid; e < 2 * kH + kOut * kH + kOut; e += kTcThreads) {
     float v;
@@ -204,7 +218,9 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(int M, const __nv
     else v = theta[ob3 + e - 2 * kH - kOut * kH];
     sF[e] = v;
   }
-  fence_async_smem();  // the operand stores must be visible to the tensor cores
+  // the K padding word of every input row stays zero for all tiles
+  for (int r = tid; r < kTcRows; r += kTcThreads)
+    *reinterpret_cast<uint2*>(sA1 + tc_core_off(r, kIn, kTcRows)) = zero2;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -212,45 +228,57 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(int M, const __nv
   const uint32_t mb = smem_u32(mbar);
   const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
   const int r = tid;                                            // row within the tile
-  const int row = row0 + r;
-  const bool valid = row < M;
   float act[kH];
-  bool ok = true;
-
-  // layer 1: D = X W1^T (K = 80)
-  if (tid == 0) tc_layer(tmem, smem_u32(sA1), smem_u32(sB1), kTcK1, mb);
-  ok = tc_wait(mb, 0);
-  uint32_t pending = 0;  // parity of an MMA batch still to be waited for on the error path
-  if (__syncthreads_and(ok)) {
+  uint32_t phase = 0;    // completed MMA batches (mbarrier phases)
+  uint32_t pending = 0;  // 1 + parity of a batch still in flight after a failed wait
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = (int64_t)tile * kTcRows;
+    // the input tile: 8-byte words, consecutive threads on consecutive words
+    for (int j = tid; j < kTcRows * kW; j += kTcThreads) {
+      const int rr = j / kW, q = j - rr * kW;
+      const int64_t g = row0 + rr;
+      const uint2 v = g < M ? reinterpret_cast<const uint2*>(X + g * kIn)[q] : zero2;
+      *reinterpret_cast<uint2*>(sA1 + tc_core_off(rr, 4 * q, kTcRows)) = v;
+    }
+    fence_async_smem();  // the operand stores must be visible to the tensor cores
+    tc_fence_before();
+    __syncthreads();
     tc_fence_after();
-    // Z1, A1 and the layer-2 operand tile (rows past M are computed and not stored)
-    tc_epilogue(taddr, sF, row, valid, Z1, A1, sA2, act);
+    const int64_t row = row0 + r;
+    const bool valid = row < M;
+    // layer 1: D = X W1^T (K = 80)
+    if (tid == 0) tc_layer(tmem, smem_u32(sA1), smem_u32(sB1), kTcK1, mb);
+    if (!__syncthreads_and(tc_wait(mb, phase & 1u))) { pending = 1 + (phase & 1u); break; }
+    ++phase;
+    tc_fence_after();
+    tc_epilogue(taddr, sF, r, row, valid, Z1, A1, sA2, act);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     // layer 2: D = A1 W2^T (K = 64), into the same tensor-memory columns
     if (tid == 0) tc_layer(tmem, smem_u32(sA2), smem_u32(sB2), kH, mb);
-    ok = tc_wait(mb, 1);
-    if (__syncthreads_and(ok)) {
-      tc_fence_after();
-      tc_epilogue(taddr, sF + kH, row, valid, Z2, A2, nullptr, act);
-      // layer 3 on the CUDA cores from the bf16 activations, FP32 sums in k order
-      if (valid) {
+    if (!__syncthreads_and(tc_wait(mb, phase & 1u))) { pending = 1 + (phase & 1u); break; }
+    ++phase;
+    tc_fence_after();
+    tc_epilogue(taddr, sF + kH, r, row, valid, Z2, A2, nullptr, act);
+    // layer 3 on the CUDA cores from the bf16 activations, FP32 sums in k order
+    if (valid) {
+      float o[kOut];
 #pragma unroll
-        for (int o = 0; o < kOut; ++o) {
-          float s = 0.f;
-          const float* w3 = sF + 2 * kH + o * kH;
+      for (int c = 0; c < kOut; ++c) {
+        float s = 0.f;
+        const float* w3 = sF + 2 * kH + c * kH;
 #pragma unroll
-          for (int k = 0; k < kH; ++k) s = fmaf(act[k], w3[k], s);
-          P[(size_t)row * kOut + o] = s + sF[2 * kH + kOut * kH + o];
-        }
+        for (int k = 0; k < kH; ++k) s = fmaf(act[k], w3[k], s);
+        o[c] = s + sF[2 * kH + kOut * kH + c];
       }
-    } else {
-      pending = 2;  // layer 2's batch (parity 1)
+      *reinterpret_cast<float4*>(P + row * kOut) = make_float4(o[0], o[1], o[2], o[3]);
     }
-  } else {
-    pending = 1;  // layer 1's batch (parity 0)
+    // every lane's tensor-memory reads and the tiles are done before the next tile
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
   }
   if (pending) {
     // an mbarrier wait gave up: record it, and wait (bounded) for the MMAs in
