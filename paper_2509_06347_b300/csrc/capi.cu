@@ -513,8 +513,8 @@ void launch_flux(cgks_t* h, MeshDev& M, bool point = true, bool radius = true) {
     if constexpr (DIM == 3) {
       if (M.H.fine.mixed) kern = point ? k_flux<3, true, double, 1> : k_flux<3, false, double, 1>;
     }
-    kern<<<resident_blocks(h, kern, bs, nb), bs, 0, h->stream>>>(M.fine, M.coef, L.dte, M.winf, P, P.gamma, M.Fface, M.Wface, M.aface,
-                                              L.W, radius ? L.rface : nullptr);
+    kern<<<resident_blocks(h, kern, bs, nb), bs, 0, h->stream>>>(
+        M.fine, M.coef, L.dte, M.winf, P, P.gamma, M.Fface, M.Wface, M.aface, L.W, radius ? L.rface : nullptr);
   }
 }
 

@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "physics.cuh"
 
@@ -121,7 +122,7 @@ __device__ __forceinline__ S eval_poly(const S* c, const S* X) {
   for (int q = 0; q < D::NQ; ++q) {
     int a, b;
     quad_pq<DIM>(q, a, b);
-    s += c[1 + DIM + q] * X[a] * X[b];
+    s += c[1 + DIM + q] * (X[a] * X[b]);  // the monomial is shared by every variable at X
   }
   return s;
 }
@@ -450,8 +451,20 @@ template <int DIM, typename S>
 __device__ __forceinline__ void eval_grad(const S* c, const S* x, S& W, S* g) {
   using D = Dims<DIM>;
   S cc[D::NC];
+  if constexpr (std::is_same<S, double>::value && D::NC % 2 == 0) {
+    // 16-byte loads: every variable's coefficient row starts on a 16-byte
+    // boundary (rows of NV * NC doubles, NC even, from 256-byte aligned buffers)
+    const double2* c2 = reinterpret_cast<const double2*>(c);
 #pragma unroll
-  for (int k = 0; k < D::NC; ++k) cc[k] = c[k];
+    for (int k = 0; k < D::NC / 2; ++k) {
+      const double2 t = __ldg(c2 + k);
+      cc[2 * k] = t.x;
+      cc[2 * k + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < D::NC; ++k) cc[k] = c[k];
+  }
   W = eval_poly<DIM, S>(cc, x);
   grad_poly<DIM, S>(cc, x, g);
 }

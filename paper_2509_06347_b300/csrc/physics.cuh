@@ -171,26 +171,30 @@ __device__ __forceinline__ void psi_mom(const Mom<DIM, S>& m, S* out) {
   }
 }
 
-// Solve <psi (a . psi)> = b for a (b normalised by density): explicit inverse
-// of the Maxwellian moment matrix.
+// Solve <psi (a . psi)> = sc b for a (sc b normalised by density): explicit
+// inverse of the Maxwellian moment matrix.  The scale sc (1 / rho, or -1 / rho
+// for the time slopes) enters through the per-side factors 2 lambda and
+// 4 lambda^2 / N, so b itself is never scaled.
 template <int DIM, typename S>
-__device__ __forceinline__ void slope_solve(const Prim<DIM, S>& p, const PhysT<S>& P, const S* b, S* a) {
-  S q2 = S(0.0), ub = S(0.0);
+__device__ __forceinline__ void slope_solve(const Prim<DIM, S>& p, const PhysT<S>& P, const S* b, S sc, S* a) {
+  S q2 = S(0.0), ub = S(0.0), bd[DIM];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     q2 += p.U[d] * p.U[d];
-    ub += p.U[d] * (b[1 + d] - p.U[d] * b[0]);
+    bd[d] = b[1 + d] - p.U[d] * b[0];
+    ub += p.U[d] * bd[d];
   }
   const S e = q2 + P.N * p.h;
-  const S aE = (P.fourOverN * p.lam * p.lam) * (S(2.0) * b[DIM + 1] - e * b[0] - S(2.0) * ub);
+  const S aE = ((P.fourOverN * p.lam * p.lam) * sc) * (S(2.0) * b[DIM + 1] - e * b[0] - S(2.0) * ub);
+  const S tl = (S(2.0) * p.lam) * sc;
   S s = S(0.0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    a[1 + d] = S(2.0) * p.lam * (b[1 + d] - p.U[d] * b[0]) - p.U[d] * aE;
+    a[1 + d] = tl * bd[d] - p.U[d] * aE;
     s += p.U[d] * a[1 + d];
   }
   a[DIM + 1] = aE;
-  a[0] = b[0] - s - S(0.5) * aE * e;
+  a[0] = sc * b[0] - s - S(0.5) * aE * e;
 }
 
 // The part of the distribution that multiplies a Maxwellian in the flux and
@@ -251,14 +255,19 @@ __device__ __forceinline__ void poly_psi_mom_2d(const Mom<2, S>& m, const Poly<2
     F1[k] = d1 + m.xi2 * D3[k];
     if (k == 0) { D0a = d0; D1a = d1; E0a = e0; }
   }
-  // <u^(A0+k) v^b P>; mv[0] = 1
+  // <u^(A0+k) v^b P>; mv[0] = 1.  Macc adds it to acc (one chain of
+  // multiply-adds, no separate sum)
   auto M = [&](int k, int b) { return mv[b] * F0[k] + mv[b + 1] * F1[k] + mv[b + 2] * D2[k] + mv[b + 3] * D3[k]; };
+  auto Macc = [&](S acc, int k, int b) {
+    return acc + mv[b] * F0[k] + mv[b + 1] * F1[k] + mv[b + 2] * D2[k] + mv[b + 3] * D3[k];
+  };
   out[0] = M(0, 0);
   out[1] = M(1, 0);
   out[2] = M(0, 1);
-  const S mxi = m.xi2 * (D0a * mv[0] + D1a * mv[1] + D2[0] * mv[2] + D3[0] * mv[3]) +
-                m.xi4 * (E0a * mv[0] + D3[0] * mv[1]);
-  out[3] = S(0.5) * (M(2, 0) + M(0, 2) + mxi);
+  const S sv = D0a * mv[0] + D1a * mv[1] + D2[0] * mv[2] + D3[0] * mv[3];
+  const S se = E0a * mv[0] + D3[0] * mv[1];
+  const S sE = Macc(M(2, 0), 0, 2) + m.xi2 * sv + m.xi4 * se;
+  out[3] = S(0.5) * sE;
 }
 
 // 3-D form of <u^A0 psi P>, grouped by the powers (j, k) of v and w:
@@ -296,6 +305,12 @@ __device__ __forceinline__ void poly_psi_mom_3d(const Mom<3, S>& m, const Poly<3
     if (k == 0) { D00a = d00; D10a = d10; D01a = d01; E00a = e00; }
   }
   // <u^(A0+k) v^b w^c P>, summed by powers of w; mv[0] = mw[0] = 1
+  auto Macc = [&](S acc, int k, int b, int c) {
+    const Grp& q = g[k];
+    return acc + mw[c] * (mv[b] * q.F00 + mv[b + 1] * q.F10 + mv[b + 2] * q.D20 + mv[b + 3] * q.Q1) +
+           mw[c + 1] * (mv[b] * q.F01 + mv[b + 1] * q.D11 + mv[b + 2] * q.Q2) +
+           mw[c + 2] * (mv[b] * q.D02 + mv[b + 1] * q.Q1) + mw[c + 3] * (mv[b] * q.Q2);
+  };
   auto M = [&](int k, int b, int c) {
     const Grp& q = g[k];
     return mw[c] * (mv[b] * q.F00 + mv[b + 1] * q.F10 + mv[b + 2] * q.D20 + mv[b + 3] * q.Q1) +
@@ -309,8 +324,9 @@ __device__ __forceinline__ void poly_psi_mom_3d(const Mom<3, S>& m, const Poly<3
   const Grp& q = g[0];
   const S sv = (D00a + mv[1] * D10a + mv[2] * q.D20 + mv[3] * q.Q1) +
                mw[1] * (D01a + mv[1] * q.D11 + mv[2] * q.Q2) + mw[2] * (q.D02 + mv[1] * q.Q1) + mw[3] * q.Q2;
-  const S mxi = m.xi2 * sv + m.xi4 * (E00a + mv[1] * q.Q1 + mw[1] * q.Q2);
-  out[4] = S(0.5) * (M(2, 0, 0) + M(0, 2, 0) + M(0, 0, 2) + mxi);
+  const S se = E00a + mv[1] * q.Q1 + mw[1] * q.Q2;
+  const S sE = Macc(Macc(M(2, 0, 0), 0, 2, 0), 0, 0, 2) + m.xi2 * sv + m.xi4 * se;
+  out[4] = S(0.5) * sE;
 }
 
 // out = <u^A0 psi P>
@@ -327,7 +343,10 @@ __device__ __forceinline__ void poly_psi_mom(const Mom<DIM, S>& m, const Poly<DI
 // local axes: for a Maxwellian g(W(x)), int u_d psi dg/dx_d = d/dx_d F_d(W), so
 // this equals <psi (a.u)> of the full-space Maxwellian (times rho) without
 // forming the velocity moments.  ir = 1 / W[0], which every caller already holds.
-template <int DIM, typename S>
+// Only the first ND directions are summed (the others are taken as zero).
+// Every accumulation is written as acc + a b + c d, which FP64 code issues as
+// fused multiply-adds into the accumulator.
+template <int DIM, typename S, int ND = DIM>
 __device__ __forceinline__ void euler_flux_divergence(S gamma, const S* W, S ir, const S (*dW)[DIM + 2], S* out) {
   constexpr int NV = DIM + 2;
   S u[DIM], q2 = S(0.0);
@@ -336,12 +355,11 @@ __device__ __forceinline__ void euler_flux_divergence(S gamma, const S* W, S ir,
     u[i] = W[1 + i] * ir;
     q2 += u[i] * u[i];
   }
-  const S p = (gamma - S(1.0)) * (W[NV - 1] - S(0.5) * W[0] * q2);
+  const S gm1 = gamma - S(1.0), hq2 = S(0.5) * q2;
+  const S p = gm1 * (W[NV - 1] - W[0] * hq2);
   const S H = (W[NV - 1] + p) * ir;  // total enthalpy
 #pragma unroll
-  for (int v = 0; v < NV; ++v) out[v] = S(0.0);
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
+  for (int d = 0; d < ND; ++d) {
     const S* g = dW[d];
     // derivatives of primitive quantities along this direction
     S du[DIM], udu = S(0.0);
@@ -350,13 +368,14 @@ __device__ __forceinline__ void euler_flux_divergence(S gamma, const S* W, S ir,
       du[i] = (g[1 + i] - u[i] * g[0]) * ir;
       udu += u[i] * du[i];
     }
-    const S dp = (gamma - S(1.0)) * (g[NV - 1] - S(0.5) * g[0] * q2 - W[0] * udu);
-    out[0] += g[1 + d];
+    const S dp = gm1 * (g[NV - 1] - g[0] * hq2 - W[0] * udu);
+    out[0] = d == 0 ? g[1] : out[0] + g[1 + d];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) out[1 + i] += g[1 + d] * u[i] + W[1 + d] * du[i];
+    for (int i = 0; i < DIM; ++i)
+      out[1 + i] = d == 0 ? g[1 + d] * u[i] + W[1 + d] * du[i] : out[1 + i] + g[1 + d] * u[i] + W[1 + d] * du[i];
     out[1 + d] += dp;
     const S dH = (g[NV - 1] + dp - H * g[0]) * ir;
-    out[NV - 1] += g[1 + d] * H + W[1 + d] * dH;
+    out[NV - 1] = d == 0 ? g[1 + d] * H + W[1 + d] * dH : out[NV - 1] + g[1 + d] * H + W[1 + d] * dH;
   }
 }
 
@@ -370,7 +389,7 @@ __device__ __forceinline__ void euler_flux_divergence(S gamma, const S* W, S ir,
 //   Q_d^i   = rho U_0 U_d U_i + p (U_0 delta_di + U_d delta_0i + U_i delta_0d)
 //   Q_d^E   = U_0 U_d (rho |U|^2 + (D + 4 + K) p) / 2
 //             + delta_0d (p |U|^2 + (D + 2 + K) p theta) / 2.
-// ir = 1 / W[0].
+// ir = 1 / W[0].  Accumulations as in euler_flux_divergence.
 template <int DIM, typename S>
 __device__ __forceinline__ void second_moment_divergence(S gamma, S K, const S* W, S ir, const S (*dW)[DIM + 2],
                                                          S* out) {
@@ -381,12 +400,12 @@ __device__ __forceinline__ void second_moment_divergence(S gamma, S K, const S* 
     U[i] = W[1 + i] * ir;
     q2 += U[i] * U[i];
   }
-  const S p = (gamma - S(1.0)) * (W[NV - 1] - S(0.5) * W[0] * q2);
+  const S gm1 = gamma - S(1.0), hq2 = S(0.5) * q2;
+  const S p = gm1 * (W[NV - 1] - W[0] * hq2);
   const S th = p * ir;
   const S cA = S(double(DIM + 4)) + K, cB = S(double(DIM + 2)) + K;
-  const S A = W[0] * q2 + cA * p;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) out[v] = S(0.0);
+  const S hcA = S(0.5) * cA, hcB = S(0.5) * cB;
+  const S hA = W[0] * hq2 + hcA * p;  // (rho |U|^2 + cA p) / 2
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const S* g = dW[d];
@@ -396,24 +415,26 @@ __device__ __forceinline__ void second_moment_divergence(S gamma, S K, const S* 
       du[i] = (g[1 + i] - U[i] * g[0]) * ir;
       udu += U[i] * du[i];
     }
-    const S dp = (gamma - S(1.0)) * (g[NV - 1] - S(0.5) * g[0] * q2 - W[0] * udu);
+    const S dp = gm1 * (g[NV - 1] - g[0] * hq2 - W[0] * udu);
     const S u0d = U[0] * U[d];
     const S du0d = du[0] * U[d] + U[0] * du[d];  // d(U_0 U_d)
-    out[0] += g[0] * u0d + W[0] * du0d;
-    if (d == 0) out[0] += dp;
+    out[0] = (d == 0 ? dp : out[0]) + g[0] * u0d + W[0] * du0d;
+    // d(rho U_0 U_d U_i) = (g0 u0d + rho du0d) U_i + rho u0d du_i
+    const S gw = g[0] * u0d + W[0] * du0d, wu = W[0] * u0d;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-      S t = g[0] * u0d * U[i] + W[0] * (du0d * U[i] + u0d * du[i]);
-      if (i == d) t += dp * U[0] + p * du[0];
-      if (i == 0) t += dp * U[d] + p * du[d];
-      if (d == 0) t += dp * U[i] + p * du[i];
-      out[1 + i] += t;
+      S t = d == 0 ? gw * U[i] + wu * du[i] : out[1 + i] + gw * U[i] + wu * du[i];
+      if (i == d) t = t + dp * U[0] + p * du[0];
+      if (i == 0) t = t + dp * U[d] + p * du[d];
+      if (d == 0) t = t + dp * U[i] + p * du[i];
+      out[1 + i] = t;
     }
-    const S dA = g[0] * q2 + S(2.0) * W[0] * udu + cA * dp;
-    out[NV - 1] += S(0.5) * (du0d * A + u0d * dA);
+    // d(A) / 2 with A = rho |U|^2 + cA p
+    const S hdA = g[0] * hq2 + W[0] * udu + hcA * dp;
+    out[NV - 1] = d == 0 ? du0d * hA + u0d * hdA : out[NV - 1] + du0d * hA + u0d * hdA;
     if (d == 0) {
       const S dth = (dp - th * g[0]) * ir;
-      out[NV - 1] += S(0.5) * (dp * q2 + S(2.0) * p * udu + cB * (dp * th + p * dth));
+      out[NV - 1] = out[NV - 1] + dp * hq2 + p * udu + hcB * (dp * th + p * dth);
     }
   }
 }
@@ -427,7 +448,7 @@ __device__ __forceinline__ void euler_flux_jvp_normal(S gamma, const S* W, S ir,
   for (int d = 0; d < DIM; ++d)
 #pragma unroll
     for (int i = 0; i < NV; ++i) g[d][i] = d == 0 ? v[i] : S(0.0);
-  euler_flux_divergence<DIM, S>(gamma, W, ir, g, out);
+  euler_flux_divergence<DIM, S, 1>(gamma, W, ir, g, out);
 }
 
 // Out-of-line variants for the double-word flux.  Its code, fully inlined, is
@@ -440,13 +461,13 @@ template <>
 struct OutOfLine<dword> { static constexpr bool value = true; };
 
 template <int DIM, typename S>
-__device__ __noinline__ void slope_solve_ool(const Prim<DIM, S>& p, const PhysT<S>& P, const S* b, S* a) {
-  slope_solve<DIM, S>(p, P, b, a);
+__device__ __noinline__ void slope_solve_ool(const Prim<DIM, S>& p, const PhysT<S>& P, const S* b, S sc, S* a) {
+  slope_solve<DIM, S>(p, P, b, sc, a);
 }
 template <int DIM, typename S>
-__device__ __forceinline__ void slope_solve_c(const Prim<DIM, S>& p, const PhysT<S>& P, const S* b, S* a) {
-  if constexpr (OutOfLine<S>::value) slope_solve_ool<DIM, S>(p, P, b, a);
-  else slope_solve<DIM, S>(p, P, b, a);
+__device__ __forceinline__ void slope_solve_c(const Prim<DIM, S>& p, const PhysT<S>& P, const S* b, S sc, S* a) {
+  if constexpr (OutOfLine<S>::value) slope_solve_ool<DIM, S>(p, P, b, sc, a);
+  else slope_solve<DIM, S>(p, P, b, sc, a);
 }
 template <int DIM, typename S>
 __device__ __noinline__ void euler_flux_divergence_ool(S gamma, const S* W, S ir, const S (*dW)[DIM + 2], S* out) {
@@ -560,16 +581,11 @@ __device__ S gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2], co
   }
   // spatial slopes of the two kinetic Maxwellians (Eq. co); the interface
   // Maxwellian's slopes enter only through closed-form moments below
-  S al[DIM][NV], ar[DIM][NV], b[NV];
+  S al[DIM][NV], ar[DIM][NV];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const S il = pl.irho, irr = pr.irho;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) b[i] = Gl[d][i] * il;
-    slope_solve_c<DIM, S>(pl, P, b, al[d]);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) b[i] = Gr[d][i] * irr;
-    slope_solve_c<DIM, S>(pr, P, b, ar[d]);
+    slope_solve_c<DIM, S>(pl, P, Gl[d], pl.irho, al[d]);
+    slope_solve_c<DIM, S>(pr, P, Gr[d], pr.irho, ar[d]);
   }
   // time slopes from <A + a.u> = 0, with <psi (a.u)> of a full-space
   // Maxwellian given by the Euler-flux divergence of its slopes
@@ -577,34 +593,28 @@ __device__ S gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2], co
   {
     S s[NV];
     euler_flux_divergence_c<DIM, S>(P.gamma, Wl, pl.irho, Gl, s);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) s[i] *= -pl.irho;
-    slope_solve_c<DIM, S>(pl, P, s, Al);
+    slope_solve_c<DIM, S>(pl, P, s, -pl.irho, Al);
     euler_flux_divergence_c<DIM, S>(P.gamma, Wr, pr.irho, Gr, s);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) s[i] *= -pr.irho;
-    slope_solve_c<DIM, S>(pr, P, s, Ar);
+    slope_solve_c<DIM, S>(pr, P, s, -pr.irho, Ar);
   }
-  // interface Maxwellian with the mean slopes: <psi (a_c.u)> = Euler-flux
-  // divergence; its time slope gives <psi (A_c.psi)> = W_t = -<psi (a_c.u)>
-  // and <u psi (A_c.psi)> = J_n W_t; <u psi (a_c.u)> is the divergence of the
-  // second moments; <u psi> is the Euler flux
-  S PAc[NV], UAc[NV], QAc[NV], Fc[NV];
+  // interface Maxwellian with the mean slopes g_c = (G_l + G_r) / 2: with the
+  // Euler-flux divergence D(g) (linear in g), rho_c <psi (a_c.u)> = D(g_c);
+  // its time slope gives rho_c <psi (A_c.psi)> = -D(g_c) and
+  // rho_c <u psi (A_c.psi)> = -J_n D(g_c) (J_n the Jacobian of the Euler flux
+  // through the normal); rho_c <u psi (a_c.u)> is the
+  // divergence of the second moments Q(g_c); <u psi> is the Euler flux.  They
+  // are formed here from the sum G_l + G_r = 2 g_c, and the factor 1/2 joins
+  // the time integrals below.
+  S PAc[NV], UAc[NV], QAc[NV], Fc[NV];  // D(2 g_c), J_n D(2 g_c), Q(2 g_c)
   {
-    S gc[DIM][NV];
+    S gs[DIM][NV];
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
-      for (int i = 0; i < NV; ++i) gc[d][i] = S(0.5) * (Gl[d][i] + Gr[d][i]);
-    euler_flux_divergence_c<DIM, S>(P.gamma, Wc, irc, gc, PAc);
-    second_moment_divergence_c<DIM, S>(P.gamma, K, Wc, irc, gc, QAc);
-    S wt[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      PAc[i] *= irc;
-      wt[i] = -PAc[i];
-    }
-    euler_flux_jvp_normal<DIM, S>(P.gamma, Wc, irc, wt, UAc);
+      for (int i = 0; i < NV; ++i) gs[d][i] = Gl[d][i] + Gr[d][i];
+    euler_flux_divergence_c<DIM, S>(P.gamma, Wc, irc, gs, PAc);
+    second_moment_divergence_c<DIM, S>(P.gamma, K, Wc, irc, gs, QAc);
+    euler_flux_jvp_normal<DIM, S>(P.gamma, Wc, irc, PAc, UAc);
     // Euler flux of W^c through the local normal
     const S un = Wc[1] * irc;
 #pragma unroll
@@ -639,11 +649,13 @@ __device__ S gks_flux(const PhysT<S>& P, const S* Wl, const S (*Gl)[DIM + 2], co
   const S C1 = S(1.0) - e, C2 = (dt + tau) * e - tau, C3 = dt - tau + tau * e;
   // --- equilibrium part (g^c, full space): T1 <u psi> + T2 <u psi (a_c . u)>
   // + T3 <u psi (A_c . psi)>; point value C1 <psi> + (C2 - C3) <psi (A_c . psi)>
+  // (times rho_c; the slope terms from the doubled-slope quantities above)
   S fx[NV], wx[NV];
+  const S hT2 = S(0.5) * T2, hT3 = S(0.5) * T3, hC23 = S(0.5) * (C2 - C3);
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    F[i] = T1 * Fc[i] + T2 * QAc[i] + T3 * Wc[0] * UAc[i];
-    Wt[i] = POINT ? C1 * Wc[i] + (C2 - C3) * Wc[0] * PAc[i] : S(0.0);
+    F[i] = T1 * Fc[i] + hT2 * QAc[i] - hT3 * UAc[i];
+    Wt[i] = POINT ? C1 * Wc[i] + hC23 * PAc[i] : S(0.0);
   }
   // --- kinetic part (g^l on u > 0, g^r on u < 0)
 #pragma unroll
