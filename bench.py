@@ -37,20 +37,21 @@ WORKLOAD = "cylinder_mach5_65536tri_3level"
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 # FP64 flops per Gauss point of the gas-kinetic flux kernel k_flux<dim,1>
 # (flux and point values) as the current formulation performs them (grouped
-# moment sums, closed-form equilibrium terms, table-driven exp and erfc), from
-# ncu's counters on this workload ((2 x DFMA + DADD + DMUL) / Gauss points):
-# achieved = these flops x Gauss points / event time.  The direct formulation
+# moment sums, closed-form equilibrium terms, table-driven exp and erfc,
+# multiply-add chains into the accumulators), from ncu's counters
+# ((2 x DFMA + DADD + DMUL) / Gauss points; 2-D on this workload, 3-D on the
+# 16 x 16 x 16 sphere shell): achieved = these flops x Gauss points / event time.  The direct formulation
 # (one moment product per slope vector, library exp and erfc) took the second
 # figures; its rate is reported beside, for comparison with earlier builds.
 FLUX_FLOP_PER_GP_2D = 1824.7
 FLUX_DIRECT_FLOP_PER_GP_2D = 2947.1
-FLUX_FLOP_PER_GP_3D = 3507.4
+FLUX_FLOP_PER_GP_3D = 3339.5
 FLUX_DIRECT_FLOP_PER_GP_3D = 5301.1
 # DRAM bytes (read + write) of one k_flux<2,1> launch on this workload, and per
 # face of k_flux<3,1> on the 16 x 16 x 16 sphere shell (297,984 faces), scaled
 # to the full shell by its number of faces; ncu, cold-cache replay.
-FLUX_DRAM_BYTES_PER_LAUNCH = 24797952
-FLUX_DRAM_BYTES_PER_FACE_3D = 487.2
+FLUX_DRAM_BYTES_PER_LAUNCH = 22689536
+FLUX_DRAM_BYTES_PER_FACE_3D = 437.7
 
 
 def parse():
@@ -571,7 +572,7 @@ def run_ours(args):
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_source": "FP64 FMA-chain probe of this library on this GPU (cgks_fma_probe)",
                      "flop_per_gp": flop_per_gp, "gauss_points": n_gp,
-                     "fp64_pipe_busy_ncu": 0.855 if dim == 2 else 0.902,
+                     "fp64_pipe_busy_ncu": 0.858 if dim == 2 else 0.924,
                      "direct_formulation_flop_per_gp": direct_per_gp,
                      "direct_formulation_equivalent_tflops": direct_per_gp * n_gp / t_flux / 1e12,
                      "ms_per_launch": t_flux * 1e3},
