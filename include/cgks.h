@@ -106,6 +106,13 @@ typedef struct cgks_config {
                                 alpha_relax (prod of the Gauss-point factors - DF); 1 takes
                                 the product (Sec 3.3).  Same fixed points for any value in
                                 (0, 1] (1) */
+  int learned_scale;         /* learned correction: 0 the network's inputs and target are
+                                in free-stream units; 1 its 24 residual-type inputs and its
+                                target are further divided by the cell's defect scale, its
+                                dt_imp times the RMS over the variables of the last residual
+                                norms of its mesh (group), so the network sees the defect
+                                relative to the stage of the solve and its correction scales
+                                with the residual (0) */
 } cgks_config;
 
 typedef struct cgks_ctx cgks_t;
@@ -469,14 +476,19 @@ int cgks_mlp_collect(cgks_t* h, int mesh_id, int n_cycles, int mode);
  * residual summed over the cell's level-1 parent and over its level-2
  * grandparent (the restriction of Sec 5.2), each times dt_imp
  * (|Omega_I| / |Omega|)^(1/2) / |Omega_I| and scaled like W (zero on meshes
- * of fewer than 3 levels).  R, dt_imp and DF come from a residual evaluation
- * at the current state (as cgks_residual; the state is not changed).  Needs
+ * of fewer than 3 levels).  With learned_scale 1 the 24 residual-type values
+ * are further divided by the cell's defect scale (see cgks_config).  R,
+ * dt_imp and DF come from a residual evaluation at the current state (as
+ * cgks_residual; the state is not changed; with learned_scale 1 the
+ * evaluation also sets the norms cgks_residual_norms returns).  Needs
  * cgks_mlp_set_params. */
 int cgks_mlp_features(cgks_t* h, int mesh_id, uint16_t* X_out);
 
 /* Learned-cycle statistics of the last cgks_vcycle(..., CGKS_LEARNED, ...):
- * out[6] = learned cycles, plain cycles, judge cycles, stall fallbacks,
- * network disabled (0/1), last judge relative RMS error (-1 if none).
+ * out[10] = learned cycles, plain cycles, judge cycles, stall fallbacks,
+ * network disabled (0/1), last judge relative RMS error (-1 if none), then
+ * that judge's relative RMS error per conserved variable (rho, rho u, rho v,
+ * E; -1 if none), each in free-stream units.
  * Policy: every 20th cycle (0, 20, 40, ...) is a plain "judge" cycle that also measures the
  * network's error against the plain correction over gated cells (disabled
  * above 0.5); a drop below 1 % over 5 learned cycles, or growth above 1.5x

@@ -55,7 +55,7 @@ class Config(C.Structure):
                 ("df_prolong", C.c_int), ("df_gate", C.c_double), ("learned_judge_every", C.c_int),
                 ("learned_max_error", C.c_double), ("flux_precision", C.c_int),
                 ("relax_beta", C.c_double), ("mu", C.c_double), ("slope_relax", C.c_double),
-                ("alpha_relax", C.c_double)]
+                ("alpha_relax", C.c_double), ("learned_scale", C.c_int)]
 
 
 _lib = None
@@ -420,10 +420,11 @@ class Context:
         return (bits.astype(np.uint32) << 16).view(np.float32)
 
     def cgks_learned_stats(self, mesh_id: int):
-        out = np.zeros(6)
+        out = np.zeros(10)
         self._check(self._L.cgks_learned_stats(self.h, mesh_id, _ptr(out)))
         return dict(learned=int(out[0]), plain=int(out[1]), judge=int(out[2]), fallbacks=int(out[3]),
-                    disabled=bool(out[4]), judge_error=float(out[5]))
+                    disabled=bool(out[4]), judge_error=float(out[5]),
+                    judge_error_per_variable=[float(x) for x in out[6:10]])
 
     def cgks_run_stage(self, mesh_id: int, stage: int):
         self._check(self._L.cgks_run_stage(self.h, mesh_id, stage))

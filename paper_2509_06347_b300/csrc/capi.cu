@@ -129,10 +129,12 @@ struct MeshDev {
   std::vector<std::unique_ptr<DBuf>> lpool;
   __nv_bfloat16* X = nullptr;
   float *Pl = nullptr, *Yl = nullptr;
+  float* Sl = nullptr;  // per-cell defect scale of the inputs and target (learned_scale 1)
   double *Wsave = nullptr, *judge_part = nullptr, *judge_out = nullptr;
   double *Rp1 = nullptr, *Rp2 = nullptr;  // restricted fine residual on levels 1 and 2 (network inputs)
   // learned-cycle policy statistics
-  double lstats[6] = {0, 0, 0, 0, 0, -1};  // learned, plain, judge, fallbacks, disabled, last judge error
+  // learned, plain, judge, fallbacks, disabled, last judge error, then that error per variable
+  double lstats[10] = {0, 0, 0, 0, 0, -1, -1, -1, -1, -1};
   // batched members (groups of cells with their own free stream)
   int n_groups = 1;
   std::vector<std::unique_ptr<DBuf>> gpool;
@@ -822,7 +824,7 @@ int run_learned(cgks_t* h, MeshDev& M, int n_cycles, double* norms_out, int* cyc
   CK(cudaMemcpyAsync(&start, M.cycle, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   for (double& x : M.lstats) x = 0;
-  M.lstats[5] = -1;
+  for (int i = 5; i < 10; ++i) M.lstats[i] = -1;
   bool disabled = false;
   int fallback = 0, done = 0, status = CGKS_OK;
   std::vector<double> rho;      // RMS density residual per cycle
@@ -833,11 +835,11 @@ int run_learned(cgks_t* h, MeshDev& M, int n_cycles, double* norms_out, int* cyc
     const bool judge = !disabled && fallback == 0 && je_every > 0 && k % je_every == 0;  // cycles 0, J, 2J, ...
     const bool use_net = !disabled && fallback == 0 && !judge;
     CK(cudaGraphLaunch(judge ? gj : (use_net ? gl : gp), h->stream));
-    double r = 0.0, je[2] = {0, 0};
+    double r = 0.0, je[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int idx = start + k;
     if (idx < M.max_hist)
       CK(cudaMemcpyAsync(&r, M.hist + (size_t)idx * 2 * nv, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    if (judge) CK(cudaMemcpyAsync(je, M.judge_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (judge) CK(cudaMemcpyAsync(je, M.judge_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     done++;
     rho.push_back(r);
@@ -846,8 +848,10 @@ int run_learned(cgks_t* h, MeshDev& M, int n_cycles, double* norms_out, int* cyc
     M.lstats[use_net ? 0 : 1] += 1;
     if (judge) {
       M.lstats[2] += 1;
-      const double err = je[1] > 0 ? std::sqrt(je[0] / je[1]) : 0.0;
+      const double e = je[0] + je[1] + je[2] + je[3], t = je[4] + je[5] + je[6] + je[7];
+      const double err = t > 0 ? std::sqrt(e / t) : 0.0;
       M.lstats[5] = err;
+      for (int v = 0; v < 4; ++v) M.lstats[6 + v] = je[4 + v] > 0 ? std::sqrt(je[v] / je[4 + v]) : 0.0;
       if (err > h->cfg.learned_max_error) disabled = true;
     }
     if (fallback > 0) fallback--;
@@ -919,6 +923,7 @@ int cgks_default_config(cgks_config* c) {
   c->mu = 0.0;
   c->slope_relax = 1.0;
   c->alpha_relax = 1.0;
+  c->learned_scale = 0;
   return CGKS_OK;
 }
 
@@ -940,7 +945,8 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
       !(h->cfg.cfl_imp > 0.0 && h->cfg.cfl_imp < 1e300) || !(h->cfg.cfl_exp > 0.0 && h->cfg.cfl_exp < 1e300) ||
       !(h->cfg.weno_eps > 0.0 && h->cfg.weno_eps < 1e300) ||
       !(h->cfg.slope_relax > 0.0 && h->cfg.slope_relax <= 1.0) ||
-      !(h->cfg.alpha_relax > 0.0 && h->cfg.alpha_relax <= 1.0)) {
+      !(h->cfg.alpha_relax > 0.0 && h->cfg.alpha_relax <= 1.0) ||
+      (h->cfg.learned_scale != 0 && h->cfg.learned_scale != 1)) {
     delete h;
     return CGKS_ERR_ARG;
   }
@@ -1906,8 +1912,9 @@ void ensure_learned(cgks_t* h, MeshDev& M) {
     M.Pl = dalloc<float>(M.lpool, n * kOut);
     M.Yl = dalloc<float>(M.lpool, n * kOut);
     M.Wsave = dalloc<double>(M.lpool, n * M.nv);
-    M.judge_part = dalloc<double>(M.lpool, 2 * blocks_for(n));
-    M.judge_out = dalloc<double>(M.lpool, 2);
+    M.Sl = dalloc<float>(M.lpool, n);
+    M.judge_part = dalloc<double>(M.lpool, 8 * blocks_for(n));
+    M.judge_out = dalloc<double>(M.lpool, 8);
     if (M.nlev >= 3) {
       M.Rp1 = dalloc<double>(M.lpool, (size_t)M.lev[1].n * 4);
       M.Rp2 = dalloc<double>(M.lpool, (size_t)M.lev[2].n * 4);
@@ -1930,7 +1937,8 @@ void features(cgks_t* h, MeshDev& M) {
   k_features2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(
       M.fine, L.W, M.G, L.R, L.dti, L.alpha, M.winf, h->cfg.gamma, coarse ? L.parent : nullptr,
       coarse ? M.lev[1].parent : nullptr, M.Rp1, M.Rp2, coarse ? M.lev[1].vol : nullptr,
-      coarse ? M.lev[2].vol : nullptr, M.X);
+      coarse ? M.lev[2].vol : nullptr, M.lgrp.empty() ? M.last_norm : M.last_g, M.X,
+      h->cfg.learned_scale ? M.Sl : nullptr);
 }
 
 template <typename T>
@@ -1943,15 +1951,15 @@ void enqueue_learned(cgks_t* h, MeshDev& M, bool judge) {
   if (!judge) {
     k_apply_learned2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, M.Pl, L.alpha, h->cfg.df_gate, grp, M.winf,
                                                                  M.lgrp.empty() ? nullptr : M.active, h->cfg.gamma,
-                                                                 L.W, M.cnt);
+                                                                 h->cfg.learned_scale ? M.Sl : nullptr, L.W, M.cnt);
     return;
   }
   CK(cudaMemcpyAsync(M.Wsave, L.W, (size_t)L.n * M.nv * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   vcycle_coarse<2, T>(h, M);
   const int nb = (int)blocks_for(L.n);
   k_judge2<<<nb, kBlock, 0, h->stream>>>(L.n, M.Pl, L.W, M.Wsave, L.alpha, h->cfg.df_gate, grp, M.winf, h->cfg.gamma,
-                                         M.judge_part);
-  k_judge_final<<<1, 1, 0, h->stream>>>(M.judge_part, nb, M.judge_out);
+                                         h->cfg.learned_scale ? M.Sl : nullptr, M.judge_part);
+  k_judge_final<<<1, 32, 0, h->stream>>>(M.judge_part, nb, M.judge_out);
 }
 
 void enqueue_kind(cgks_t* h, MeshDev& M, int kind, int prec) {
@@ -1982,8 +1990,9 @@ int cgks_mlp_features(cgks_t* h, int mesh_id, uint16_t* X_out) {
     if (!X_out) throw ArgError("null output");
     ensure_learned(h, M);
     LevelDev& L = M.lev[0];
-    // residual, time steps and DF at the current state (slopes unchanged)
-    fine_residual<2>(h, M, false, false, false, false, nullptr, nullptr);
+    // residual, time steps and DF at the current state (slopes unchanged);
+    // with learned_scale 1 also its norms, which set the inputs' scale
+    fine_residual<2>(h, M, false, false, h->cfg.learned_scale != 0, false, nullptr, nullptr);
     features(h, M);
     std::vector<uint16_t> tmp((size_t)L.n * kIn);
     CK(cudaMemcpyAsync(tmp.data(), M.X, tmp.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost, h->stream));
@@ -2011,7 +2020,8 @@ int cgks_mlp_collect(cgks_t* h, int mesh_id, int n_cycles, int mode) {
       CK(cudaMemcpyAsync(M.Wsave, L.W, (size_t)L.n * M.nv * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
       if (mode == CGKS_MIXED) vcycle_coarse<2, float>(h, M);
       else vcycle_coarse<2, double>(h, M);
-      k_target2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, L.W, M.Wsave, grp, M.winf, h->cfg.gamma, M.Yl);
+      k_target2<<<blocks_for(L.n), kBlock, 0, h->stream>>>(L.n, L.W, M.Wsave, grp, M.winf, h->cfg.gamma,
+                                                           h->cfg.learned_scale ? M.Sl : nullptr, M.Yl);
       CK(cudaGetLastError());
       const int rc = cgks_mlp_dataset_append(h, L.n, (const uint16_t*)M.X, M.Yl);
       if (rc != CGKS_OK) return rc;
@@ -2024,7 +2034,7 @@ int cgks_learned_stats(cgks_t* h, int mesh_id, double* out) {
   return guarded(h, [&]() -> int {
     MeshDev& M = get_mesh(h, mesh_id);
     if (!out) throw ArgError("null output");
-    for (int i = 0; i < 6; ++i) out[i] = M.lstats[i];
+    for (int i = 0; i < 10; ++i) out[i] = M.lstats[i];
     return CGKS_OK;
   });
 }

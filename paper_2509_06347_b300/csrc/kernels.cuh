@@ -1401,7 +1401,12 @@ __global__ void k_sum_children(int nc, const int* __restrict__ ch_off, const int
 // the volumes of those levels (all null on a mesh of fewer than 3 levels: the
 // 8 inputs are then zero).  Each coarse residual enters as an increment: times
 // the cell's implicit time step scaled by the length ratio to the coarse
-// cell, sqrt(V_I / V_c), over V_I.
+// cell, sqrt(V_I / V_c), over V_I.  With S non-null the 24 residual-type
+// inputs are further divided by the cell's defect scale s (its implicit time
+// step times the size of the residual over the whole mesh, from the norms
+// gnorm [groups][4][rms, max]), stored in S: the network then sees the
+// defect relative to the current stage of the solve, and its output is
+// multiplied by s (a correction proportional to the size of the defect).
 __global__ void __launch_bounds__(kBlock) k_features2(DevFine M, const double* __restrict__ W,
                                                       const double* __restrict__ G, const double* __restrict__ R,
                                                       const double* __restrict__ dti, const double* __restrict__ alpha,
@@ -1409,13 +1414,15 @@ __global__ void __launch_bounds__(kBlock) k_features2(DevFine M, const double* _
                                                       const int* __restrict__ parent1, const int* __restrict__ parent2,
                                                       const double* __restrict__ R1, const double* __restrict__ R2,
                                                       const double* __restrict__ vol1, const double* __restrict__ vol2,
-                                                      __nv_bfloat16* __restrict__ X) {
+                                                      const double* __restrict__ gnorm, __nv_bfloat16* __restrict__ X,
+                                                      float* __restrict__ S) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= M.n) return;
   const double* wi = winf + 4 * (M.grp ? M.grp[c] : 0);
   double sc[4];
   fs_scales(wi, gamma, sc);
   __nv_bfloat16* out = X + (size_t)c * kFeat;
+  double inv_s = 1.0;
   {
     double f1[4] = {0.0, 0.0, 0.0, 0.0}, f2[4] = {0.0, 0.0, 0.0, 0.0};
     if (parent1 && parent2) {
@@ -1428,10 +1435,26 @@ __global__ void __launch_bounds__(kBlock) k_features2(DevFine M, const double* _
         f2[v] = R2[(size_t)J * 4 + v] * k2 / sc[v];
       }
     }
+    if (S) {
+      // defect scale of the cell: its implicit time step times the RMS over
+      // the variables of the mesh's (group's) last residual norms, RMS of
+      // R_v / |Omega| over the cells, in free-stream units
+      const double* q = gnorm + 8 * (M.grp ? M.grp[c] : 0);
+      double ss = 0.0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const double t = q[2 * v] / sc[v];
+        ss += t * t;
+      }
+      double s = dti[c] * sqrt(0.25 * ss);
+      if (!(s > 0.0)) s = 1.0;
+      inv_s = 1.0 / s;
+      S[c] = (float)s;
+    }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      out[68 + v] = __float2bfloat16((float)f1[v]);
-      out[72 + v] = __float2bfloat16((float)f2[v]);
+      out[68 + v] = __float2bfloat16((float)(f1[v] * inv_s));
+      out[72 + v] = __float2bfloat16((float)(f2[v] * inv_s));
     }
   }
   double Wc[4], gc[4][2];
@@ -1442,7 +1465,7 @@ __global__ void __launch_bounds__(kBlock) k_features2(DevFine M, const double* _
     for (int d = 0; d < 2; ++d) gc[v][d] = G[((size_t)c * 4 + v) * 2 + d];
   }
   const double hc = sqrt(M.vol[c]);
-  cell_features(Wc, gc, dti[c] / M.vol[c], R + (size_t)c * 4, alpha[c], hc, sc, out);
+  cell_features(Wc, gc, dti[c] / M.vol[c] * inv_s, R + (size_t)c * 4, alpha[c], hc, sc, out);
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     const int j = M.cnbr[(size_t)c * 3 + m];
@@ -1455,7 +1478,7 @@ __global__ void __launch_bounds__(kBlock) k_features2(DevFine M, const double* _
 #pragma unroll
         for (int d = 0; d < 2; ++d) gj[v][d] = G[((size_t)j * 4 + v) * 2 + d];
       }
-      cell_features(Wj, gj, dti[j] / M.vol[j], R + (size_t)j * 4, alpha[j], sqrt(M.vol[j]), sc, o);
+      cell_features(Wj, gj, dti[j] / M.vol[j] * inv_s, R + (size_t)j * 4, alpha[j], sqrt(M.vol[j]), sc, o);
     } else {
       const int f = M.cface[(size_t)c * 3 + m];
       const double sd = M.cside[(size_t)c * 3 + m];
@@ -1468,16 +1491,19 @@ __global__ void __launch_bounds__(kBlock) k_features2(DevFine M, const double* _
   }
 }
 
-// training target: the applied fine correction, scaled like W
+// training target: the applied fine correction, scaled like W (and divided by
+// the defect scale S where given)
 __global__ void k_target2(int n, const double* __restrict__ W, const double* __restrict__ Wsave,
                           const int* __restrict__ grp, const double* __restrict__ winf, double gamma,
-                          float* __restrict__ Y) {
+                          const float* __restrict__ S, float* __restrict__ Y) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   double sc[4];
   fs_scales(winf + 4 * (grp ? grp[c] : 0), gamma, sc);
+  const double is = S ? 1.0 / (double)S[c] : 1.0;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) Y[(size_t)c * 4 + v] = (float)((W[(size_t)c * 4 + v] - Wsave[(size_t)c * 4 + v]) / sc[v]);
+  for (int v = 0; v < 4; ++v)
+    Y[(size_t)c * 4 + v] = (float)((W[(size_t)c * 4 + v] - Wsave[(size_t)c * 4 + v]) / sc[v] * is);
 }
 
 // learned correction applied where the DF factor is at least the gate
@@ -1485,17 +1511,19 @@ __global__ void __launch_bounds__(kBlock) k_apply_learned2(int n, const float* _
                                                            const double* __restrict__ alpha, double gate,
                                                            const int* __restrict__ grp, const double* __restrict__ winf,
                                                            const int* __restrict__ active, double gamma,
-                                                           double* __restrict__ W, Counters* __restrict__ cnt) {
+                                                           const float* __restrict__ S, double* __restrict__ W,
+                                                           Counters* __restrict__ cnt) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   if (active && !active[grp[c]]) return;
   if (!(alpha[c] >= gate)) return;
   double sc[4], w[4], d[4];
   fs_scales(winf + 4 * (grp ? grp[c] : 0), gamma, sc);
+  const double s = S ? (double)S[c] : 1.0;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     w[v] = W[(size_t)c * 4 + v];
-    d[v] = (double)P[(size_t)c * 4 + v] * sc[v];
+    d[v] = (double)P[(size_t)c * 4 + v] * s * sc[v];
   }
   const int r = guarded_add<2>(gamma, w, d);
   if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
@@ -1504,49 +1532,51 @@ __global__ void __launch_bounds__(kBlock) k_apply_learned2(int n, const float* _
   for (int v = 0; v < 4; ++v) W[(size_t)c * 4 + v] = w[v];
 }
 
-// judge: squared error of the prediction against the applied plain correction
-// and squared size of that correction, over gated cells (per-block partials)
+// judge: per variable, the squared error of the prediction against the
+// applied plain correction and the squared size of that correction, over gated
+// cells (free-stream units; per-block partials, 8 per block)
 __global__ void __launch_bounds__(kBlock) k_judge2(int n, const float* __restrict__ P, const double* __restrict__ W,
                                                    const double* __restrict__ Wsave, const double* __restrict__ alpha,
                                                    double gate, const int* __restrict__ grp,
                                                    const double* __restrict__ winf, double gamma,
-                                                   double* __restrict__ part) {
-  __shared__ double se[kBlock], sr[kBlock];
+                                                   const float* __restrict__ S, double* __restrict__ part) {
+  __shared__ double sw[kBlock / 32][8];
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  double e = 0.0, r = 0.0;
+  double q[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (c < n && alpha[c] >= gate) {
     double sc[4];
     fs_scales(winf + 4 * (grp ? grp[c] : 0), gamma, sc);
+    const double s = S ? (double)S[c] : 1.0;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const double t = (W[(size_t)c * 4 + v] - Wsave[(size_t)c * 4 + v]) / sc[v];
-      const double d = (double)P[(size_t)c * 4 + v] - t;
-      e += d * d;
-      r += t * t;
+      const double d = (double)P[(size_t)c * 4 + v] * s - t;
+      q[v] = d * d;
+      q[4 + v] = t * t;
     }
   }
-  se[threadIdx.x] = e;
-  sr[threadIdx.x] = r;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    for (int o = 16; o > 0; o >>= 1) q[k] += __shfl_down_sync(0xffffffffu, q[k], o);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sw[wp][k] = q[k];
   __syncthreads();
-  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-    if (threadIdx.x < st) {
-      se[threadIdx.x] += se[threadIdx.x + st];
-      sr[threadIdx.x] += sr[threadIdx.x + st];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = se[0];
-    part[2 * blockIdx.x + 1] = sr[0];
+  if (threadIdx.x < 8) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sw[w][threadIdx.x];
+    part[8 * (size_t)blockIdx.x + threadIdx.x] = a;
   }
 }
 
+// out[0..3] squared errors, out[4..7] squared corrections, per variable
+// (blocks summed in order)
 __global__ void k_judge_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double e = 0.0, r = 0.0;
-  for (int b = 0; b < nb; ++b) { e += part[2 * b]; r += part[2 * b + 1]; }
-  out[0] = e;
-  out[1] = r;
+  if (blockIdx.x != 0 || threadIdx.x >= 8) return;
+  double a = 0.0;
+  for (int b = 0; b < nb; ++b) a += part[8 * (size_t)b + threadIdx.x];
+  out[threadIdx.x] = a;
 }
 
 // FMA-throughput probe: CH independent chains per thread

@@ -5,8 +5,11 @@ free stream (rho, rho c, rho c, rho c^2); then the three face neighbours in
 stored face order (face k opposite vertex k), with wall (mirror) and far-field
 (free stream on inflow, copy on outflow) ghosts across boundary faces; then
 the fine residual summed over the cell's parent and grandparent, times
-dt_imp (|Omega_I| / |Omega|)^(1/2) / |Omega_I|, scaled like W.  The GPU rounds
-to bfloat16, so the bound is 2^-8 relative."""
+dt_imp (|Omega_I| / |Omega|)^(1/2) / |Omega_I|, scaled like W.  With
+learned_scale = 1 the 24 residual-type inputs are further divided by the cell's
+dt_imp times the RMS over the variables of the mesh's residual norms (RMS over
+cells of R_v / |Omega|, free-stream units).  The GPU rounds to bfloat16, so the
+bound is 2^-8 relative."""
 import numpy as np
 import pytest
 
@@ -41,12 +44,18 @@ def _ghost(tag, w, n, W, G):
     return W.copy(), G.copy()
 
 
-def test_features_match_numpy(cg):
+# the residual-type inputs: the residual increments of the cell and of its three
+# neighbours, then the parent's and the grandparent's defects
+RES_COLS = np.r_[12:16, 29:33, 46:50, 63:67, 68:76]
+
+
+@pytest.mark.parametrize("learned_scale", [0, 1])
+def test_features_match_numpy(cg, learned_scale):
     m = tp.MESHES["cylinder"]
     rng = np.random.default_rng(21)
     W, G, w = tp.state_for("cylinder", m, rng)
     n = len(W)
-    ctx = cg.Context()
+    ctx = cg.Context(learned_scale=learned_scale)
     try:
         ctx.cgks_mlp_set_params(synth.mlp_init_params())
         ctx.setup(1, m, w, W, G)
@@ -107,6 +116,11 @@ def test_features_match_numpy(cg):
     I, J = p1, p2[p1]
     E[:, 68:72] = R1[I] * (dti * np.sqrt(V1[I] / V) / V1[I])[:, None] / sc
     E[:, 72:76] = R2[J] * (dti * np.sqrt(V2[J] / V) / V2[J])[:, None] / sc
+    if learned_scale:
+        rms = np.sqrt(np.mean((R / V[:, None]) ** 2, axis=0)) / sc
+        s = dti * np.sqrt(np.mean(rms ** 2))
+        assert np.all(s > 0)
+        E[:, RES_COLS] /= s[:, None]
     err = np.abs(X - E)
     bound = 2.0 ** -8 * np.abs(E) + 1e-30
     assert np.all(err <= bound), (np.unravel_index(np.argmax(err - bound), err.shape), np.max(err / (np.abs(E) + 1e-30)))

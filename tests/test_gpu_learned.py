@@ -88,6 +88,47 @@ def test_open_gate_adds_the_prediction(cg):
     np.testing.assert_allclose(Wl - W1, np.tile(d * sc, (len(W1), 1)), rtol=1e-2, atol=1e-7)
 
 
+def test_open_gate_scales_with_the_residual_norm(cg):
+    """learned_scale = 1: the prediction is multiplied by the cell's defect
+    scale as well, dt_imp at the smoothed state times the RMS over the
+    variables of the cycle's fine residual norms in free-stream units."""
+    d = np.array([1e-3, 2e-3, -1e-3, 3e-3])
+    th = constant_net(d)
+    m = mesh()
+    w = synth.freestream(3.0)
+    W0 = synth.uniform_state(m, w)
+    n = len(W0)
+    ctx = cg.Context(cg.default_config(df_gate=-1.0, learned_judge_every=0, learned_scale=1))
+    ctx.cgks_mlp_set_params(th)
+    ctx.setup(1, m, w, W0)
+    norms = np.zeros((1, 4, 2))
+    assert ctx.cgks_vcycle([1], 1, cg.LEARNED, norms, check=False) == 0
+    Wl = np.zeros_like(W0)
+    ctx.cgks_get_state(1, Wl)
+    ctx.close()
+    _, W1, _, _ = run(cg, 3.0, 1, cg.MIXED, levels=1)
+    c1 = cg.Context()
+    c1.setup(1, m, w, W1)
+    dte, dti = np.zeros(n), np.zeros(n)
+    c1.cgks_reconstruct(1, None, dte, dti)
+    c1.close()
+    sc = np.array([w[0], w[0], w[0], w[0]])  # rho = 1, c = 1
+    sigma = np.sqrt(np.mean((norms[0, :, 0] / sc) ** 2))
+    s = (Wl - W1) / (d * sc)
+    np.testing.assert_allclose(s, np.tile((dti * sigma)[:, None], (1, 4)), rtol=1e-4)
+
+
+def test_per_variable_judge_errors_bracket_the_total(cg):
+    """The judge's error over all variables is the correction-weighted mean of
+    the per-variable squared errors, so it lies between their extremes."""
+    th = constant_net(np.array([0.5, -0.5, 0.5, 2.0]))
+    for ls in (0, 1):
+        rc, _, _, st = run(cg, 3.0, 2, cg.LEARNED, theta=th, learned_scale=ls)
+        pv = np.array(st["judge_error_per_variable"])
+        assert rc == 0 and st["judge"] == 1 and np.all(pv >= 0)
+        assert pv.min() * (1 - 1e-12) <= st["judge_error"] <= pv.max() * (1 + 1e-12)
+
+
 def test_bad_network_is_disabled_by_the_judge(cg):
     """A network predicting nonsense fails the first judge cycle and the run
     then follows the plain V-cycle exactly."""
