@@ -13,7 +13,7 @@ cylinder solve.
   state, which has an exactly zero residual for any velocity.  MIXED and FP64
   take different paths there and stop at slightly different uniform states,
   so their difference is itself uniform; the test checks both facts.
-* The Mach-5 cylinder of 65,536 cells (config 2's workload) reaches a 1e-10
+* The Mach-5 cylinder of 65,536 cells (the benchmark's workload) reaches a 1e-10
   drop in FP64 and in MIXED with the convergence settings, MIXED within 1 %
   of FP64's cycle count, and its converged state gives the stagnation-point
   wall pressure of the Rayleigh pitot formula (32.65 free-stream pressures at
@@ -123,7 +123,7 @@ def test_mixed_converged_state_against_oracle(solves):
 
 @pytest.fixture(scope="module")
 def cylinder():
-    """Config 2's workload solved from the free stream to a 1e-10 drop, FP64
+    """The 65,536-cell Mach-5 cylinder solved from the free stream to a 1e-10 drop, FP64
     and MIXED (about 11,300 cycles each)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
