@@ -22,6 +22,47 @@ namespace cgks {
 
 constexpr int kBlock = 256;
 
+// Row access.  The N values of one cell or face are contiguous, and every
+// array is its own cudaMalloc allocation (256-byte aligned), so a row of four
+// doubles (2-D states, residuals, face fluxes) starts on a 16-byte boundary
+// and moves as two 16-byte vectors, a row of eight doubles (2-D slopes) as
+// four, and a row of four floats (FP32 increments) as one.  Rows of five
+// (3-D) stay scalar.
+template <int N, typename T>
+__device__ __forceinline__ void ld_row(const T* __restrict__ p, size_t i, T* x) {
+  if constexpr (sizeof(T) == 8 && (N == 4 || N == 8)) {
+    const double2* q = reinterpret_cast<const double2*>(p) + i * (N / 2);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const double2 a = q[k];
+      x[2 * k] = a.x;
+      x[2 * k + 1] = a.y;
+    }
+  } else if constexpr (sizeof(T) == 4 && N == 4) {
+    const float4 a = reinterpret_cast<const float4*>(p)[i];
+    x[0] = a.x;
+    x[1] = a.y;
+    x[2] = a.z;
+    x[3] = a.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) x[k] = p[i * N + k];
+  }
+}
+template <int N, typename T>
+__device__ __forceinline__ void st_row(T* __restrict__ p, size_t i, const T* x) {
+  if constexpr (sizeof(T) == 8 && (N == 4 || N == 8)) {
+    double2* q = reinterpret_cast<double2*>(p) + i * (N / 2);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) q[k] = make_double2(x[2 * k], x[2 * k + 1]);
+  } else if constexpr (sizeof(T) == 4 && N == 4) {
+    reinterpret_cast<float4*>(p)[i] = make_float4(x[0], x[1], x[2], x[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) p[i * N + k] = x[k];
+  }
+}
+
 // VAR = 0: simplices (triangles, tetrahedra), every cell with dim + 1 faces
 // and every face with the same Gauss points; VAR = 1: 3-D mixed elements
 // (tetrahedra, pyramids, prisms, hexahedra), up to 6 faces per cell and 3
@@ -750,13 +791,16 @@ __device__ __forceinline__ void colour0_forward(int c, const double* __restrict_
                                                 T* __restrict__ dWs, T* __restrict__ dW) {
   const T ha = (T)(0.5 * alpha);
   const T iD = T(1) / (T)D;  // in the sweep precision: an FP32 reciprocal in the mixed mode
+  double rc[NV];
+  T x[NV];
+  ld_row<NV>(R, c, rc);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const double rhs = -(R[(size_t)c * NV + v] + 0.0);
-    const T x = ((T)rhs - ha * (T)0) * iD;
-    dWs[(size_t)c * NV + v] = x;
-    if (dW) dW[(size_t)c * NV + v] = x;
+    const double rhs = -(rc[v] + 0.0);
+    x[v] = ((T)rhs - ha * (T)0) * iD;
   }
+  st_row<NV>(dWs, c, x);
+  if (dW) st_row<NV>(dW, c, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -795,15 +839,16 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
       if (VAR && m >= nf) break;
       const int f = M.cface[(size_t)c * NFC + m];
       const double s = M.cside[(size_t)c * NFC + m];
-      double nn[DIM];
+      double nn[DIM], ff[NV], wf[NV];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) nn[d] = s * M.fn[(size_t)f * DIM + d];
+      ld_row<NV>(Fface, f, ff);
+      ld_row<NV>(Wface, f, wf);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        r[v] += s * Fface[(size_t)f * NV + v];
-        const double wv = Wface[(size_t)f * NV + v];
+        r[v] += s * ff[v];
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) gn[v][d] += wv * nn[d];
+        for (int d = 0; d < DIM; ++d) gn[v][d] += wf[v] * nn[d];
       }
       a *= aface[f];
     }
@@ -812,26 +857,27 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevFine M, Topo T, const doub
     // stored DF: the product itself, or, where it rises, under-relaxed towards
     // it (a fall takes effect at once; same fixed points)
     const double as = (om_alpha < 1.0 && a > alpha[c]) ? alpha[c] + om_alpha * (a - alpha[c]) : a;
+    st_row<NV>(R, c, r);
+    double qc[2 * NV], gv[NV * DIM], go[NV * DIM];
+    if (Gout && live && om_slope < 1.0) ld_row<NV * DIM>(Gout, c, go);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      R[(size_t)c * NV + v] = r[v];
       const double q = r[v] * iV;
       rl2[v] = q * q;
       rmax[v] = fabs(q);
-      if (qcell) {
-        qcell[(size_t)c * 2 * NV + 2 * v] = q * q;
-        qcell[(size_t)c * 2 * NV + 2 * v + 1] = fabs(q);
-      }
+      qc[2 * v] = q * q;
+      qc[2 * v + 1] = fabs(q);
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const double g = gn[v][d] * iV;
-        if (gradnew_out) gradnew_out[((size_t)c * NV + v) * DIM + d] = g;
-        if (Gout && live) {  // slope update with DF, replaced or under-relaxed
-          const size_t i = ((size_t)c * NV + v) * DIM + d;
-          Gout[i] = om_slope < 1.0 ? Gout[i] + om_slope * (as * g - Gout[i]) : as * g;
-        }
+        gv[v * DIM + d] = g;
+        // slope update with DF, replaced or under-relaxed
+        go[v * DIM + d] = om_slope < 1.0 ? go[v * DIM + d] + om_slope * (as * g - go[v * DIM + d]) : as * g;
       }
     }
+    if (qcell) st_row<2 * NV>(qcell, c, qc);
+    if (gradnew_out) st_row<NV * DIM>(gradnew_out, c, gv);
+    if (Gout && live) st_row<NV * DIM>(Gout, c, go);
     if (live) alpha[c] = as;
     // LU-SGS diagonal with DF, or with the constant of the fixed-factor schemes (relax_fixed >= 0)
     if (Dg) {
@@ -979,11 +1025,11 @@ __device__ __forceinline__ void offdiag_term(const Topo& Tp, int e, const double
   T nn[DIM], Wj[NV], dj[NV], dF[NV];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) nn[d] = (T)Tp.nrm[(size_t)e * DIM + d];
+  double wj[NV];
+  ld_row<NV>(W, j, wj);
+  ld_row<NV>(dWsrc, j, dj);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    Wj[v] = (T)W[(size_t)j * NV + v];
-    dj[v] = dWsrc[(size_t)j * NV + v];
-  }
+  for (int v = 0; v < NV; ++v) Wj[v] = (T)wj[v];
   const T r = (T)rface[Tp.face[e]];
   if constexpr (sizeof(T) == 8) {
     // plain difference of Euler fluxes in FP64
@@ -1032,9 +1078,9 @@ __device__ __forceinline__ void update_into(int c, double gamma, const double* _
   constexpr int NV = DIM + 2;
   double w[NV], d[NV];
   bool finite = true;
+  ld_row<NV>(W, c, w);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    w[v] = W[(size_t)c * NV + v];
     d[v] = (double)d_c[v];
     finite = finite && isfinite(d[v]);
   }
@@ -1045,8 +1091,7 @@ __device__ __forceinline__ void update_into(int c, double gamma, const double* _
     if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
     if (r < 0) atomicAdd(&cnt->update_zeroed, 1ull);
   }
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Wout[(size_t)c * NV + v] = w[v];
+  st_row<NV>(Wout, c, w);
 }
 
 // Wout (nullable): the state's other buffer.  Where this launch finalises the
@@ -1078,20 +1123,22 @@ __global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const
   const T iD = T(1) / (T)Dg[c];  // as in colour0_forward
   T fin[NV];  // the final increment (MODE 1, 2)
   if (MODE == 1) {
+    T ds[NV];
+    ld_row<NV>(dWs, c, ds);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      fin[v] = dWs[(size_t)c * NV + v] - ha * acc[v] * iD;
-      dW[(size_t)c * NV + v] = fin[v];
-    }
+    for (int v = 0; v < NV; ++v) fin[v] = ds[v] - ha * acc[v] * iD;
+    st_row<NV>(dW, c, fin);
   } else {
+    double rc[NV], pc[NV];
+    ld_row<NV>(R, c, rc);
+    if (Pf) ld_row<NV>(Pf, c, pc);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double rhs = -(R[(size_t)c * NV + v] + (Pf ? Pf[(size_t)c * NV + v] : 0.0));
-      const T x = ((T)rhs - ha * acc[v]) * iD;
-      dWs[(size_t)c * NV + v] = x;
-      fin[v] = x;
-      if (MODE == 2) dW[(size_t)c * NV + v] = x;
+      const double rhs = -(rc[v] + (Pf ? pc[v] : 0.0));
+      fin[v] = ((T)rhs - ha * acc[v]) * iD;
     }
+    st_row<NV>(dWs, c, fin);
+    if (MODE == 2) st_row<NV>(dW, c, fin);
   }
   if (MODE != 0 && Wout) update_into<DIM, T>(c, gamma, W, fin, Wout, cnt);
 }
@@ -1105,11 +1152,13 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, double gamma, double* 
   if (c >= n) return;
   if (active && !active[grp[c]]) return;
   double w[NV], d[NV];
+  T dc[NV];
   bool finite = true;
+  ld_row<NV>(W, c, w);
+  ld_row<NV>(dW, c, dc);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    w[v] = W[(size_t)c * NV + v];
-    d[v] = (double)dW[(size_t)c * NV + v];
+    d[v] = (double)dc[v];
     finite = finite && isfinite(d[v]);
   }
   if (!finite) {
@@ -1119,8 +1168,7 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, double gamma, double* 
   const int r = guarded_add<DIM>(gamma, w, d);
   if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
   if (r < 0) atomicAdd(&cnt->update_zeroed, 1ull);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) W[(size_t)c * NV + v] = w[v];
+  st_row<NV>(W, c, w);
 }
 
 // explicit local-time-step update W -= dt_exp R / V (Eq. smo, fine smoother option)
@@ -1162,11 +1210,9 @@ __global__ void __launch_bounds__(kBlock) k_face_kfvs(FaceSet Fs, const double* 
   double n[DIM], WL[NV], WR[NV];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) n[d] = Fs.fn[(size_t)f * DIM + d];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) WL[v] = W[(size_t)L * NV + v];
+  ld_row<NV>(W, L, WL);
   if (R >= 0) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) WR[v] = W[(size_t)R * NV + v];
+    ld_row<NV>(W, R, WR);
   } else {
     ghost_state<DIM>(Fs.ftag[f], winf + NV * (Fs.grp ? Fs.grp[L] : 0), n, WL, WR, P.gamma);
   }
@@ -1179,7 +1225,8 @@ __global__ void __launch_bounds__(kBlock) k_face_kfvs(FaceSet Fs, const double* 
     to_global<DIM>(fr, Fl, Fg);
     const double S = Fs.fS[f];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fout[(size_t)f * NV + v] = S * Fg[v];
+    for (int v = 0; v < NV; ++v) Fg[v] *= S;
+    st_row<NV>(Fout, f, Fg);
   }
   if (rout) rout[f] = spectral_radius<DIM, double>(P.gamma, WL, WR, n);
 }
@@ -1205,18 +1252,22 @@ __global__ void __launch_bounds__(kBlock) k_coarse_cell(Topo Tp, const double* _
   for (int e = Tp.off[c]; e < Tp.off[c + 1]; ++e) {
     const int f = Tp.face[e];
     const double sd = Tp.side[e];
+    double ff[NV];
+    ld_row<NV>(Fface, f, ff);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) r[v] += sd * Fface[(size_t)f * NV + v];
+    for (int v = 0; v < NV; ++v) r[v] += sd * ff[v];
   }
+  {
+    double o[NV], q[NV];
+    if (Rstar) ld_row<NV>(Rstar, c, q);
+    else if (Pf) ld_row<NV>(Pf, c, q);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    if (Rstar) out[(size_t)c * NV + v] = Rstar[(size_t)c * NV + v] - r[v];
-    else out[(size_t)c * NV + v] = r[v] + (Pf ? Pf[(size_t)c * NV + v] : 0.0);
+    for (int v = 0; v < NV; ++v) o[v] = Rstar ? q[v] - r[v] : r[v] + (Pf ? q[v] : 0.0);
+    st_row<NV>(out, c, o);
   }
   if (Dg) {
     double Wi[NV], ke = 0.0;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Wi[v] = W[(size_t)c * NV + v];
+    ld_row<NV>(W, c, Wi);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) ke += Wi[1 + d] * Wi[1 + d];
     const double ir = 1.0 / Wi[0];
@@ -1253,21 +1304,22 @@ __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int* __restri
   for (int k = ch_off[I]; k < ch_off[I + 1]; ++k) {
     const int i = ch_idx[k];
     const double V = vol_f[i];
+    double wi[NV], ri[NV];
+    ld_row<NV>(Wf, i, wi);
+    ld_row<NV>(Rf, i, ri);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      w[v] += V * Wf[(size_t)i * NV + v];
-      r[v] += Rf[(size_t)i * NV + v];
+      w[v] += V * wi[v];
+      r[v] += ri[v];
     }
     a = fmin(a, af[i]);
   }
   const double iV = 1.0 / vol_c[I];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const double x = w[v] * iV;
-    W0[(size_t)I * NV + v] = x;
-    Wc[(size_t)I * NV + v] = x;
-    Rstar[(size_t)I * NV + v] = r[v];
-  }
+  for (int v = 0; v < NV; ++v) w[v] *= iV;
+  st_row<NV>(W0, I, w);
+  st_row<NV>(Wc, I, w);
+  st_row<NV>(Rstar, I, r);
   ac[I] = a;
 }
 
@@ -1285,18 +1337,17 @@ __global__ void __launch_bounds__(kBlock) k_prolong(int nf, const int* __restric
   if (i >= nf) return;
   if (active && !active[grp[i]]) return;
   const int I = parent[i];
-  double w[NV], d[NV];
+  double w[NV], d[NV], wc[NV], wc0[NV];
   const double a = af[i];
+  ld_row<NV>(Wf, i, w);
+  ld_row<NV>(Wc, I, wc);
+  ld_row<NV>(Wc0, I, wc0);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    w[v] = Wf[(size_t)i * NV + v];
-    d[v] = a * (Wc[(size_t)I * NV + v] - Wc0[(size_t)I * NV + v]);
-  }
+  for (int v = 0; v < NV; ++v) d[v] = a * (wc[v] - wc0[v]);
   const int r = guarded_add<DIM>(gamma, w, d);
   if (r > 0) atomicAdd(&cnt->update_halved, 1ull);
   if (r < 0) atomicAdd(&cnt->update_zeroed, 1ull);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Wf[(size_t)i * NV + v] = w[v];
+  st_row<NV>(Wf, i, w);
 }
 
 // ---------------------------------------------------------------------------
