@@ -32,12 +32,16 @@ def test_default_config_values():
     assert cfg.gamma == 1.4 and cfg.cfl_imp == 10.0 and cfg.cfl_exp == 0.5
     assert cfg.n_sweep_coarse == 6 and cfg.n_pre == 1 and cfg.n_post == 0
     assert cfg.tol == 1e-10
+    assert cfg.weno_gamma_high == 0.95 and cfg.slope_relax == 1.0 and cfg.alpha_relax == 1.0
+    assert cfg.learned_scale == 0
 
 
 @pytest.mark.parametrize("kw", [dict(tau_c1=0.0), dict(tau_c1=float("nan")), dict(tau_c2=-1.0), dict(mu=-1.0),
                                 dict(gamma=1.0), dict(df_relax=3), dict(df_relax=2, relax_beta=1.5),
                                 dict(n_pre=2), dict(n_sweep_coarse=0), dict(flux_precision=2),
-                                dict(cfl_imp=0.0), dict(cfl_exp=-0.5), dict(weno_eps=0.0)])
+                                dict(cfl_imp=0.0), dict(cfl_exp=-0.5), dict(weno_eps=0.0),
+                                dict(slope_relax=0.0), dict(alpha_relax=1.5), dict(weno_gamma_high=0.0),
+                                dict(learned_scale=2)])
 def test_invalid_config_rejected_before_any_device_call(kw):
     """cgks_create checks the configuration before it touches the device, so
     every rejection holds on a host without a GPU."""
