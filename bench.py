@@ -857,7 +857,9 @@ def learned_leg(cgks, stream, collect_at=(0, 20, 80), collect_cycles=2, train_st
     inputs and the applied coarse corrections of collect_cycles plain cycles are
     appended (states from the start of the solve and from further on).  The
     network is trained on the GPU, then, at each held-out Mach number on the
-    65,536-cell cylinder: (1) after each number of plain cycles in judge_after,
+    65,536-cell cylinder: (0) the held-out Mach 5.5 also runs FP64, MIXED and
+    LEARNED to a 1e-10 drop with CYLINDER_CONVERGENCE_MACH5; (1) after each
+    number of plain cycles in judge_after,
     judge_cycles learned cycles whose judge never disables the network give its
     relative RMS error against the plain correction every 20 cycles, overall
     and per variable (held-out data); (2) FP64, MIXED and LEARNED (with the
@@ -968,6 +970,25 @@ def learned_leg(cgks, stream, collect_at=(0, 20, 80), collect_cycles=2, train_st
             res["wall_ratio_fp64_over_learned"] = res["fp64"][key] / res["learned"][key]
             res["wall_ratio_fp64_over_mixed"] = res["fp64"][key] / res["mixed"][key]
         out[f"mach_{mach}"] = res
+    # the held-out Mach 5.5 to a 1e-10 drop, with the settings of the Mach-5
+    # convergence runs: FP64, MIXED and LEARNED (judge and fallback on)
+    w = synth.freestream(5.5)
+    W = synth.uniform_state(mesh, w)
+    cfg10 = dict(CYLINDER_CONVERGENCE_MACH5, learned_scale=learned_scale)
+    res = {"mach": 5.5, "config": cfg10}
+    for name, mode in (("fp64", cgks.PLAIN_FP64), ("mixed", cgks.MIXED), ("learned", cgks.LEARNED)):
+        c = cgks.Context(stream=stream.cuda_stream, **cfg10)
+        c.cgks_mlp_set_params(theta)
+        r, _ = _solve_to_drop_ctx(c, mesh, w, W, None, mode, 14000)
+        if mode == cgks.LEARNED:
+            r["learned_stats"] = c.cgks_learned_stats(1)
+        c.close()
+        res[name] = {k: v for k, v in r.items() if k in ("rc", "cycles", "wall_s", "final_drop", "learned_stats")
+                     or k.endswith("1e-10") or k.endswith("1e-6")}
+    for name in ("mixed", "learned"):
+        if "wall_s_to_1e-10" in res["fp64"] and "wall_s_to_1e-10" in res[name]:
+            res[f"wall_ratio_fp64_over_{name}_to_1e-10"] = res["fp64"]["wall_s_to_1e-10"] / res[name]["wall_s_to_1e-10"]
+    out["mach_5.5_to_1e-10"] = res
     return out
 
 
