@@ -113,6 +113,13 @@ typedef struct cgks_config {
                                 norms of its mesh (group), so the network sees the defect
                                 relative to the stage of the solve and its correction scales
                                 with the residual (0) */
+  int coarse_cluster_max_cells; /* a coarse level of two colours and at most this many cells
+                                runs each smoothing step's cell residual, colour-0 forward
+                                step and both sweep phases in one thread-block cluster (16
+                                blocks where the device allows, else 8), with cluster
+                                barriers between the phases instead of kernel boundaries;
+                                bit-identical results, but slower on the 4,096- and
+                                16,384-cell levels measured; 0 never (0) */
 } cgks_config;
 
 typedef struct cgks_ctx cgks_t;

@@ -55,7 +55,8 @@ class Config(C.Structure):
                 ("df_prolong", C.c_int), ("df_gate", C.c_double), ("learned_judge_every", C.c_int),
                 ("learned_max_error", C.c_double), ("flux_precision", C.c_int),
                 ("relax_beta", C.c_double), ("mu", C.c_double), ("slope_relax", C.c_double),
-                ("alpha_relax", C.c_double), ("learned_scale", C.c_int)]
+                ("alpha_relax", C.c_double), ("learned_scale", C.c_int),
+                ("coarse_cluster_max_cells", C.c_int)]
 
 
 _lib = None

@@ -200,6 +200,7 @@ struct cgks_ctx {
   int sms = 148;                                      // SM count of the device (set at creation)
   int device = 0;                                     // device current at creation; all work runs there
   double* noalloc_scratch = nullptr;                  // device address of the no-allocation scratch array
+  int cluster_cs[2] = {0, 0};  // blocks per cluster of the 2-D coarse-step cluster kernel [FP64, FP32]; 0: none
   // pinned host buffer for the small per-chunk reads of cgks_vcycle
   double* pin = nullptr;
   size_t pin_cap = 0;
@@ -634,6 +635,67 @@ void coarse_prep(cgks_t* h, MeshDev& M, LevelDev& L, const double* Pf, bool want
       h->cfg.cfl_imp, L.R, want_diag ? L.D : nullptr, dWs0, dW0, L.color_off[1]);
 }
 
+// One smoothing step of a two-colour coarse level of at most
+// cfg.coarse_cluster_max_cells cells: the face fluxes (unless faces_ready),
+// then k_coarse_step_cluster in one thread-block cluster.  Returns false,
+// launching nothing, where the level does not qualify.
+template <int DIM, typename T>
+bool coarse_step_cluster(cgks_t* h, MeshDev& M, LevelDev& L, bool faces_ready, double* Wcur, double* Wnext) {
+  const int cs = h->cluster_cs[sizeof(T) == 8 ? 0 : 1];
+  if (DIM != 2 || cs < 1 || L.n_colors != 2 || L.n > h->cfg.coarse_cluster_max_cells || L.n < 1) return false;
+  const PhysParams p = phys(h->cfg, DIM);
+  if (!faces_ready) {
+    const int bf = fit_block(h, L.faces.nf, M.blk[B_FACE]);
+    k_face_kfvs<DIM><<<blocks_for(L.faces.nf, bf), bf, 0, h->stream>>>(L.faces, Wcur, M.winf, p, L.Fc, L.rface);
+    CK(cudaGetLastError());
+  }
+  T* dWs = sizeof(T) == 8 ? (T*)L.dWs64 : (T*)L.dWs32;
+  T* dW = sizeof(T) == 8 ? (T*)L.dW64 : (T*)L.dW32;
+  const double* alpha = h->cfg.df_relax == 1 ? L.alpha : L.relax;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(cs, 1, 1);
+  lc.blockDim = dim3(kClusterBlock, 1, 1);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = h->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  CK(cudaLaunchKernelEx(&lc, k_coarse_step_cluster<DIM, T>, L.topo, (const double*)Wcur, (const double*)L.Fc,
+                        (const double*)L.rface, (const double*)L.P, alpha, h->cfg.gamma, h->cfg.cfl_exp,
+                        h->cfg.cfl_imp, L.R, L.D, dWs, dW, L.color_off[1], Wnext, M.cnt));
+  return true;
+}
+
+// blocks per cluster that the coarse-step cluster kernel can run with (16 where
+// the device allows that non-portable size, else 8; 0 if neither)
+template <typename T>
+int coarse_cluster_size() {
+  auto kern = k_coarse_step_cluster<2, T>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    (void)cudaGetLastError();
+  }
+  for (int cs : {16, 8}) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cs, 1, 1);
+    lc.blockDim = dim3(kClusterBlock, 1, 1);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &lc) == cudaSuccess && nc >= 1) return cs;
+    (void)cudaGetLastError();
+  }
+  return 0;
+}
+
 // FAS forcing P = R* - R(W0) on a coarse level.  The restriction sets W = W0,
 // so the face fluxes and spectral radii computed here also serve the first
 // smoothing step (coarse_prep with faces_ready).
@@ -685,8 +747,10 @@ void vcycle_coarse(cgks_t* h, MeshDev& M) {
     for (int s = 0; s < nsw; ++s) {
       double* Wcur = (s & 1) ? C.Wb : C.W;
       double* Wnext = (s & 1) ? C.W : C.Wb;
-      coarse_prep<DIM, T>(h, M, C, C.P, true, true, s == 0, Wcur);
-      sweeps<DIM, T>(h, M, C, nullptr, true, Wcur, Wnext);
+      if (!coarse_step_cluster<DIM, T>(h, M, C, s == 0, Wcur, Wnext)) {
+        coarse_prep<DIM, T>(h, M, C, C.P, true, true, s == 0, Wcur);
+        sweeps<DIM, T>(h, M, C, nullptr, true, Wcur, Wnext);
+      }
     }
     if (nsw & 1) CK(cudaMemcpyAsync(C.W, C.Wb, (size_t)C.n * M.nv * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     if (l + 1 < M.nlev) coarse_prep<DIM>(h, M, C, C.P, false);  // R~ = R(W) + P to restrict
@@ -924,6 +988,7 @@ int cgks_default_config(cgks_config* c) {
   c->slope_relax = 1.0;
   c->alpha_relax = 1.0;
   c->learned_scale = 0;
+  c->coarse_cluster_max_cells = 0;
   return CGKS_OK;
 }
 
@@ -946,7 +1011,7 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
       !(h->cfg.weno_eps > 0.0 && h->cfg.weno_eps < 1e300) ||
       !(h->cfg.slope_relax > 0.0 && h->cfg.slope_relax <= 1.0) ||
       !(h->cfg.alpha_relax > 0.0 && h->cfg.alpha_relax <= 1.0) ||
-      (h->cfg.learned_scale != 0 && h->cfg.learned_scale != 1)) {
+      (h->cfg.learned_scale != 0 && h->cfg.learned_scale != 1) || h->cfg.coarse_cluster_max_cells < 0) {
     delete h;
     return CGKS_ERR_ARG;
   }
@@ -956,6 +1021,9 @@ int cgks_create(cgks_t** out, const cgks_config* cfg, void* stream) {
       h->device = dev;
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
         h->sms = sms;
+      // the coarse-step cluster kernel's cluster size on this device
+      h->cluster_cs[0] = cgks::coarse_cluster_size<double>();
+      h->cluster_cs[1] = cgks::coarse_cluster_size<float>();
     }
   }
   if (stream) {

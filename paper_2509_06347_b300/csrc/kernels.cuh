@@ -21,6 +21,14 @@
 namespace cgks {
 
 constexpr int kBlock = 256;
+constexpr int kClusterBlock = 512;  // threads per block of the cluster kernels
+
+// all threads of the thread-block cluster: arrive with release and wait with
+// acquire semantics at cluster scope (the PTX defaults), so that the global
+// writes of every block before the barrier are visible to every block after it
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 // Row access.  The N values of one cell or face are contiguous, and every
 // array is its own cudaMalloc allocation (256-byte aligned), so a row of four
@@ -1098,17 +1106,15 @@ __device__ __forceinline__ void update_into(int c, double gamma, const double* _
 // increments of its colour (MODE 2: the last colour; MODE 1: backward), it
 // also writes the guarded update W + dW there, so that no separate update
 // launch is needed (the sweeps keep reading W).
+// the LU-SGS step of cell c of the colour [lo, hi) (k_sweep's per-cell work)
 template <int DIM, typename T, int MODE>
-__global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const double* __restrict__ W,
-                                                  const double* __restrict__ R, const double* __restrict__ Pf,
-                                                  const double* __restrict__ alpha, const double* __restrict__ Dg,
-                                                  const double* __restrict__ rface, double gamma,
-                                                  T* __restrict__ dWs, T* __restrict__ dW,
-                                                  double* __restrict__ Wout = nullptr,
-                                                  Counters* __restrict__ cnt = nullptr) {
+__device__ __forceinline__ void sweep_cell(const Topo& Tp, int c, int lo, int hi, const double* __restrict__ W,
+                                           const double* __restrict__ R, const double* __restrict__ Pf,
+                                           const double* __restrict__ alpha, const double* __restrict__ Dg,
+                                           const double* __restrict__ rface, double gamma, T* __restrict__ dWs,
+                                           T* __restrict__ dW, double* __restrict__ Wout,
+                                           Counters* __restrict__ cnt) {
   constexpr int NV = DIM + 2;
-  const int c = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= hi) return;
   T acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0;
@@ -1141,6 +1147,19 @@ __global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const
     if (MODE == 2) st_row<NV>(dW, c, fin);
   }
   if (MODE != 0 && Wout) update_into<DIM, T>(c, gamma, W, fin, Wout, cnt);
+}
+
+template <int DIM, typename T, int MODE>
+__global__ void __launch_bounds__(kBlock) k_sweep(Topo Tp, int lo, int hi, const double* __restrict__ W,
+                                                  const double* __restrict__ R, const double* __restrict__ Pf,
+                                                  const double* __restrict__ alpha, const double* __restrict__ Dg,
+                                                  const double* __restrict__ rface, double gamma,
+                                                  T* __restrict__ dWs, T* __restrict__ dW,
+                                                  double* __restrict__ Wout = nullptr,
+                                                  Counters* __restrict__ cnt = nullptr) {
+  const int c = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= hi) return;
+  sweep_cell<DIM, T, MODE>(Tp, c, lo, hi, W, R, Pf, alpha, Dg, rface, gamma, dWs, dW, Wout, cnt);
 }
 
 template <int DIM, typename T>
@@ -1233,19 +1252,14 @@ __global__ void __launch_bounds__(kBlock) k_face_kfvs(FaceSet Fs, const double* 
 
 // ... then per cell: R~ = sum_f +-S F + P (or, with Rstar, the forcing
 // P = R* - R), local time steps and the DF-relaxed LU-SGS diagonal.
-template <int DIM, typename T = double>
-__global__ void __launch_bounds__(kBlock) k_coarse_cell(Topo Tp, const double* __restrict__ W,
-                                                        const double* __restrict__ Fface,
-                                                        const double* __restrict__ rface,
-                                                        const double* __restrict__ Pf,
-                                                        const double* __restrict__ Rstar,
-                                                        const double* __restrict__ alpha, double gamma,
-                                                        double cfl_exp, double cfl_imp, double* __restrict__ out,
-                                                        double* __restrict__ Dg, T* __restrict__ dWs0,
-                                                        T* __restrict__ dW0, int c0_end) {
+template <int DIM, typename T>
+__device__ __forceinline__ void coarse_cell(const Topo& Tp, int c, const double* __restrict__ W,
+                                            const double* __restrict__ Fface, const double* __restrict__ rface,
+                                            const double* __restrict__ Pf, const double* __restrict__ Rstar,
+                                            const double* __restrict__ alpha, double gamma, double cfl_exp,
+                                            double cfl_imp, double* __restrict__ out, double* __restrict__ Dg,
+                                            T* __restrict__ dWs0, T* __restrict__ dW0, int c0_end) {
   constexpr int NV = DIM + 2;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= Tp.n) return;
   double r[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) r[v] = 0.0;
@@ -1283,6 +1297,47 @@ __global__ void __launch_bounds__(kBlock) k_coarse_cell(Topo Tp, const double* _
     Dg[c] = D;
     if (dWs0 && c < c0_end) colour0_forward<NV, T>(c, out, alpha[c], D, dWs0, dW0);
   }
+}
+
+template <int DIM, typename T = double>
+__global__ void __launch_bounds__(kBlock) k_coarse_cell(Topo Tp, const double* __restrict__ W,
+                                                        const double* __restrict__ Fface,
+                                                        const double* __restrict__ rface,
+                                                        const double* __restrict__ Pf,
+                                                        const double* __restrict__ Rstar,
+                                                        const double* __restrict__ alpha, double gamma,
+                                                        double cfl_exp, double cfl_imp, double* __restrict__ out,
+                                                        double* __restrict__ Dg, T* __restrict__ dWs0,
+                                                        T* __restrict__ dW0, int c0_end) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Tp.n) return;
+  coarse_cell<DIM, T>(Tp, c, W, Fface, rface, Pf, Rstar, alpha, gamma, cfl_exp, cfl_imp, out, Dg, dWs0, dW0, c0_end);
+}
+
+// One smoothing step of a small two-colour coarse level after its face fluxes
+// (k_face_kfvs): R~ and D of every cell with the forward step of colour 0
+// (k_coarse_cell), then colour 1 forward and backward with its guarded update
+// (k_sweep mode 2), then colour 0 backward with its update (k_sweep mode 1).
+// One thread-block cluster runs the three phases, separated by cluster
+// barriers (release / acquire at cluster scope) instead of kernel boundaries;
+// every cell does exactly the work, in the same order, of the three kernels.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(kClusterBlock) k_coarse_step_cluster(
+    Topo Tp, const double* __restrict__ W, const double* __restrict__ Fface, const double* __restrict__ rface,
+    const double* __restrict__ Pf, const double* __restrict__ alpha, double gamma, double cfl_exp, double cfl_imp,
+    double* __restrict__ R, double* __restrict__ Dg, T* __restrict__ dWs, T* __restrict__ dW, int c1,
+    double* __restrict__ Wout, Counters* __restrict__ cnt) {
+  const int n = Tp.n;
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int c = t0; c < n; c += stride)
+    coarse_cell<DIM, T>(Tp, c, W, Fface, rface, Pf, nullptr, alpha, gamma, cfl_exp, cfl_imp, R, Dg, dWs, nullptr, c1);
+  cluster_barrier();
+  for (int c = c1 + t0; c < n; c += stride)
+    sweep_cell<DIM, T, 2>(Tp, c, c1, n, W, R, nullptr, alpha, Dg, rface, gamma, dWs, dW, Wout, cnt);
+  cluster_barrier();
+  for (int c = t0; c < c1; c += stride)
+    sweep_cell<DIM, T, 1>(Tp, c, 0, c1, W, R, nullptr, alpha, Dg, rface, gamma, dWs, dW, Wout, cnt);
 }
 
 // ---------------------------------------------------------------------------

@@ -100,3 +100,30 @@ def test_autotune_keeps_results(cg):
         res.append(W)
         ctx.close()
     np.testing.assert_array_equal(res[0], res[1])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_coarse_cluster_step_keeps_results(cg, mode):
+    """The coarse smoothing step in one thread-block cluster (cell residual,
+    colour-0 forward step and both sweep phases separated by cluster barriers)
+    does each cell's work of the three kernels it replaces: states and norms
+    after ten cycles are bit-identical with it on both coarse levels, on level
+    2 only and off, and it takes fewer launches per cycle."""
+    m = synth.cylinder_mesh(32, 16, 1.05 ** 2, n_refine=2)  # 16,384 / 4,096 / 1,024 cells
+    w = synth.freestream(3.0)
+    W0 = synth.uniform_state(m, w)
+    res, launches = [], []
+    for mc in (0, 2000, 5000):
+        ctx = cg.Context(coarse_cluster_max_cells=mc)
+        ctx.setup(9, m, w, W0)
+        norms = np.zeros((10, 4, 2))
+        ctx.cgks_vcycle([9], 10, mode, norms)
+        W = np.zeros_like(W0)
+        ctx.cgks_get_state(9, W)
+        res.append((W, norms))
+        launches.append(ctx.cgks_launch_count(9, mode))
+        ctx.close()
+    for W, norms in res[1:]:
+        np.testing.assert_array_equal(W, res[0][0])
+        np.testing.assert_array_equal(norms, res[0][1])
+    assert launches[0] > launches[1] > launches[2]
