@@ -390,9 +390,13 @@ int cgks_set_groups(cgks_t* h, int mesh_id, int n_groups, const int32_t* group_o
  * V-cycles of a grouped mesh: up to n_cycles cycles; every cfg.check_every
  * cycles each member whose RMS density residual has dropped by cfg.tol from
  * its first recorded cycle is frozen (its state no longer changes) and its
- * cycle count stored in cycles_to_tol [n_groups] (-1 if not reached); stops
- * when every member is frozen.  norms_out (host, nullable)
- * [n_cycles][n_groups][nv][2] as in cgks_vcycle; *cycles_done (nullable).
+ * cycle count stored in cycles_to_tol [n_groups] (-1 if not reached).  A
+ * member whose residual becomes non-finite or grows by cfg.diverge_factor is
+ * frozen as well, with cycles_to_tol -2; the members share no faces, so the
+ * others continue unaffected.  Stops when every member is frozen.  Returns
+ * CGKS_ERR_DIVERGED (after the run) if any member diverged, else CGKS_OK.
+ * norms_out (host, nullable) [n_cycles][n_groups][nv][2] as in cgks_vcycle;
+ * *cycles_done (nullable).
  */
 int cgks_vcycle_groups(cgks_t* h, int mesh_id, int n_cycles, int mode, double* norms_out, int* cycles_to_tol,
                        int* cycles_done);

@@ -1731,15 +1731,20 @@ int cgks_vcycle_groups(cgks_t* h, int mesh_id, int n_cycles, int mode, double* n
         for (int q = 0; q < G; ++q) {
           const double r = hist[((size_t)k * G + q) * 2 * nv];
           if (first[q] < 0) first[q] = r;
-          if (!std::isfinite(r) || (first[q] > 0 && r > h->cfg.diverge_factor * first[q])) status = CGKS_ERR_DIVERGED;
-          if (conv[q] < 0 && act[q] && first[q] > 0 && r <= h->cfg.tol * first[q]) {
+          if (!act[q]) continue;
+          if (!std::isfinite(r) || (first[q] > 0 && r > h->cfg.diverge_factor * first[q])) {
+            // diverged: freeze this member and carry on with the others
+            status = CGKS_ERR_DIVERGED;
+            conv[q] = -2;
+            act[q] = 0;
+          } else if (conv[q] < 0 && first[q] > 0 && r <= h->cfg.tol * first[q]) {
             conv[q] = k - start + 1;
             act[q] = 0;  // converged: freeze this member
           }
         }
       done += chunk;
       CK(cudaMemcpyAsync(M.active, act.data(), G * sizeof(int), cudaMemcpyHostToDevice, h->stream));
-      if (status != CGKS_OK || std::all_of(act.begin(), act.end(), [](int a) { return a == 0; })) break;
+      if (std::all_of(act.begin(), act.end(), [](int a) { return a == 0; })) break;
     }
     std::fill(act.begin(), act.end(), 1);
     CK(cudaMemcpyAsync(M.active, act.data(), G * sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -1752,7 +1757,11 @@ int cgks_vcycle_groups(cgks_t* h, int mesh_id, int n_cycles, int mode, double* n
         }
     if (cycles_to_tol) std::memcpy(cycles_to_tol, conv.data(), G * sizeof(int));
     if (cycles_done) *cycles_done = done;
-    if (status != CGKS_OK) h->err = "a batch member diverged";
+    if (status != CGKS_OK) {
+      h->err = "batch members diverged (frozen, the others ran on):";
+      for (int q = 0; q < G; ++q)
+        if (conv[q] == -2) h->err += " " + std::to_string(q);
+    }
     return status;
   });
 }

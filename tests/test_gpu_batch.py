@@ -81,6 +81,48 @@ def test_converged_members_are_frozen(cg):
     ctx.close()
 
 
+def test_diverged_member_is_frozen_and_others_run_on(cg):
+    """A member whose residual grows past diverge_factor is frozen and
+    reported (cycles_to_tol -2, status DIVERGED) while the others run to the
+    end unaffected: they share no faces with it.  The factor is set between
+    the members' largest residual growths of a reference run, so that some
+    members cross it and some do not."""
+    union, grp, winf, W0 = synth.batch_cylinders(SPECS)
+    ncyc = 40
+    G = len(SPECS)
+
+    def run(factor):
+        ctx = cg.Context(cg.default_config(tol=1e-30, check_every=1, diverge_factor=factor))
+        ctx.setup(8, union, winf[0], W0)
+        ctx.cgks_set_groups(8, grp, winf)
+        norms = np.zeros((ncyc, G, 4, 2))
+        conv, done, rc = ctx.cgks_vcycle_groups(8, ncyc, 0, norms, check=False)
+        W = np.zeros_like(W0)
+        ctx.cgks_get_state(8, W)
+        ctx.close()
+        return conv, done, rc, norms, W
+
+    conv0, done0, rc0, norms0, W0ref = run(1e6)
+    assert rc0 == 0 and done0 == ncyc and np.all(conv0 == -1)
+    growth = norms0[:, :, 0, 0].max(axis=0) / norms0[0, :, 0, 0]
+    factor = float(np.median(growth))
+    conv, done, rc, norms, W = run(factor)
+    hit = conv == -2
+    print(f"\nresidual growth per member {np.round(growth, 4)}, factor {factor:.4f}, frozen as diverged: {hit}")
+    assert hit.any() and (~hit).any()
+    assert rc == -4 and done == ncyc  # CGKS_ERR_DIVERGED
+    for q in range(G):
+        rows = grp == q
+        if hit[q]:
+            # frozen: from the cycle after the one that crossed the factor on,
+            # the state and so its residual no longer change
+            k = int(np.argmax(norms[:, q, 0, 0] > factor * norms[0, q, 0, 0]))
+            assert np.all(norms[k + 1:, q, 0, 0] == norms[k + 1, q, 0, 0])
+        else:
+            np.testing.assert_array_equal(W[rows], W0ref[rows])
+            np.testing.assert_array_equal(norms[:, q], norms0[:, q])
+
+
 def test_autotune_keeps_results(cg):
     """Block sizes change only the launch shape: the state after three cycles
     is bit-identical with and without autotuning."""
