@@ -462,7 +462,9 @@ int cgks_mlp_select(cgks_t* h, int impl);
  * grad (device fp32 [9348]); loss (host, nullable). */
 int cgks_mlp_grad(cgks_t* h, int64_t n, const uint16_t* X, const float* Y, float* grad, float* loss);
 /* Training set held by the library: append rows (host or device pointers),
- * query its size, clear it. */
+ * query its size, clear it.  An appended row with a non-finite input or
+ * target (collected from a diverging mesh) is kept but takes no part in
+ * training: its inputs are zeroed and it adds neither loss nor gradient. */
 int cgks_mlp_dataset_append(cgks_t* h, int64_t n, const uint16_t* X, const float* Y);
 int cgks_mlp_dataset_size(cgks_t* h, int64_t* n);
 int cgks_mlp_dataset_clear(cgks_t* h);

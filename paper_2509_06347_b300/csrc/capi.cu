@@ -2203,6 +2203,9 @@ int cgks_mlp_dataset_append(cgks_t* h, int64_t n, const uint16_t* X, const float
     }
     CK(cudaMemcpyAsync(S.X + S.rows * kIn, X, n * kIn * sizeof(__nv_bfloat16), cudaMemcpyDefault, h->stream));
     CK(cudaMemcpyAsync(S.Y + S.rows * kOut, Y, n * kOut * sizeof(float), cudaMemcpyDefault, h->stream));
+    // rows with a non-finite input or target (a diverging mesh) take no part in training
+    k_mark_nonfinite_rows<<<blocks_for(n), kBlock, 0, h->stream>>>(n, S.X + S.rows * kIn, S.Y + S.rows * kOut);
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     S.rows += n;
     return CGKS_OK;

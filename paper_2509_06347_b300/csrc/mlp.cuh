@@ -174,7 +174,10 @@ __global__ void k_mse_grad(const float* __restrict__ P, const float* __restrict_
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float e2 = 0.f;
   if (i < n) {
-    const float d = P[i] - Y[i];
+    // a NaN target marks a row excluded from training (k_mark_nonfinite_rows):
+    // it contributes neither loss nor gradient
+    const float y = Y[i];
+    const float d = y == y ? P[i] - y : 0.f;
     e2 = d * d;
     const float gdp = 2.f * d * scale;
     dP[i] = gdp;
@@ -221,6 +224,20 @@ __global__ void k_adam(int n, const float* __restrict__ g, float* __restrict__ t
 __global__ void k_f32_to_bf16(int n, const float* __restrict__ x, __nv_bfloat16* __restrict__ y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = __float2bfloat16(x[i]);
+}
+
+// rows [0, n) of an appended block: a row with a non-finite input or target
+// gets zero inputs (a finite forward pass) and NaN targets (no loss, no
+// gradient in k_mse_grad)
+__global__ void k_mark_nonfinite_rows(int64_t n, __nv_bfloat16* __restrict__ X, float* __restrict__ Y) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  bool ok = true;
+  for (int c = 0; c < kIn; ++c) ok = ok && isfinite(__bfloat162float(X[r * kIn + c]));
+  for (int c = 0; c < kOut; ++c) ok = ok && isfinite(Y[r * kOut + c]);
+  if (ok) return;
+  for (int c = 0; c < kIn; ++c) X[r * kIn + c] = __float2bfloat16(0.f);
+  for (int c = 0; c < kOut; ++c) Y[r * kOut + c] = __int_as_float(0x7fc00000);
 }
 
 // gather rows (mini-batch) of the training set

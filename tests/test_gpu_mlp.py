@@ -120,3 +120,40 @@ def test_training_reduces_loss(ctx):
     assert losses[-20:].mean() < 0.1 * losses[:5].mean()
     th = ctx.cgks_mlp_get_params()
     assert th.shape == (9348,) and np.all(np.isfinite(th))
+
+
+def test_nonfinite_rows_take_no_part_in_training(ctx):
+    """Rows collected from a diverging mesh carry non-finite inputs or targets.
+    Appended to the training set they add neither loss nor gradient, so
+    training on a set with such rows stays finite and still fits; and a NaN
+    target excludes its row from the gradient: the gradient equals the one
+    without that row, times (n - 1) / n for the mean's count, up to the BF16
+    rounding of the output gradient (whose scale differs by that factor)."""
+    rng = np.random.default_rng(8)
+    n = 512
+    X = rng.standard_normal((n, 76)).astype(np.float32)
+    A = rng.standard_normal((76, 4)) / 8.0
+    Y = np.tanh(X @ A).astype(np.float32)
+    ctx.cgks_mlp_set_params(mlp.init_params(9))
+    # the gradient with one NaN target against the gradient without that row
+    Yn = Y.copy()
+    Yn[7] = np.nan
+    g1 = torch.zeros(9348, dtype=torch.float32, device="cuda")
+    g2 = torch.zeros(9348, dtype=torch.float32, device="cuda")
+    ctx.cgks_mlp_grad(bf16_dev(X), torch.tensor(Yn, device="cuda"), g1)
+    keep = np.arange(n) != 7
+    ctx.cgks_mlp_grad(bf16_dev(X[keep]), torch.tensor(Y[keep], device="cuda"), g2)
+    a, b = g1.cpu().numpy(), g2.cpu().numpy() * (n - 1) / n
+    assert np.all(np.isfinite(a))
+    assert np.max(np.abs(a - b)) <= 2e-3 * np.max(np.abs(b))
+    # training on a set with rows of NaN inputs and infinite targets
+    Xp, Yp = X.copy(), Y.copy()
+    Xp[3, 5] = np.nan
+    Yp[11, 2] = np.inf
+    ctx.cgks_mlp_dataset_clear()
+    ctx.cgks_mlp_dataset_append(bf16_dev(Xp), torch.tensor(Yp, device="cuda"))
+    ctx.cgks_mlp_set_params(mlp.init_params(9))
+    losses = ctx.cgks_mlp_train(200, 256, 2e-3, seed=3)
+    assert np.all(np.isfinite(losses))
+    assert losses[-20:].mean() < 0.5 * losses[:5].mean()
+    assert np.all(np.isfinite(ctx.cgks_mlp_get_params()))
