@@ -51,7 +51,7 @@ FLUX_DIRECT_FLOP_PER_GP_3D = 5301.1
 # face of k_flux<3,1> on the 16 x 16 x 16 sphere shell (297,984 faces), scaled
 # to the full shell by its number of faces; ncu, cold-cache replay.
 FLUX_DRAM_BYTES_PER_LAUNCH = 22689536
-FLUX_DRAM_BYTES_PER_FACE_3D = 437.7
+FLUX_DRAM_BYTES_PER_FACE_3D = 469.5
 
 
 def parse():
