@@ -615,10 +615,11 @@ def _solve_to_drop(cgks, mesh, w, W0, G0, mode, max_cycles, stream, levels=None,
 
 def _solve_to_drop_ctx(ctx, mesh, w, W0, G0, mode, max_cycles, levels=None):
     import torch
+    nv = W0.shape[1]  # the norms buffer holds nv variables (2-D 4, 3-D 5)
     ctx.setup(1, mesh, w, W0, G0, levels=levels)
-    ctx.cgks_vcycle([1], 1, mode, np.zeros((1, 4, 2)))
+    ctx.cgks_vcycle([1], 1, mode, np.zeros((1, nv, 2)))
     ctx.cgks_init_state(1, W0, G0)
-    norms = np.zeros((max_cycles, 4, 2))
+    norms = np.zeros((max_cycles, nv, 2))
     done = np.zeros(1, np.int32)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
